@@ -1,0 +1,391 @@
+"""Benchmark of the SFMM gravity solver on one GB300 (or N, one rank each).
+
+A step is one pass of the whole hot path over one particle set: the tree
+build (bounding box, Morton keys, sort, radix tree, centres, sizes) and the
+gravity (moments, per-leaf walk with M2L/L2L/L2P, softened P2P, reductions),
+with inputs resident in HBM.  Default workload: Plummer sphere, N = 10^6,
+theta = 0.5, expansion order p = 2, leaf size 16.  The headline value is the
+FP32 form's particles/s; the FP64 form and theta = 0.3 / 0.7 are measured
+too and reported beside it.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank solves its own particle set (seed + rank): weak
+scaling with no data-path collective; the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/sec & interactions/sec of SFMM gravity, FP32 vs FP64 form on 1 GB300"
+WORKLOAD = dict(name="plummer_1e6", n=1_000_000, seed=1002, theta=0.5, order=2, leaf_size=16)
+FLOPS_PER_PAIR = 20      # far-field pair: dx 3, r^2 5, rsqrt 1, m r^-3 3, acc 6, pot 2 (FMA = 2)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _kernel_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2602_05804_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, src_hash):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("source_sha") == src_hash:
+            return e["dram_bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def _cpu_baseline(pos, m, h, w, budget_s=20.0):
+    """The FP64 oracle as it stands, on the host cores: full tree build, then
+    the per-leaf walk on a seeded sample of leaves (per-leaf independence,
+    Algorithm 1), scaled to the whole particle set."""
+    import oracle
+
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    t = oracle.Tree(pos, m, h, w["leaf_size"], p=w["order"])
+    t_build = time.perf_counter() - t0
+    order = np.random.default_rng(7).permutation(t.nleaves).astype(np.int32)
+    nsel = 64
+    t_walk, nl_done, np_done = 0.0, 0, 0
+    while True:
+        sel = order[nl_done:nl_done + nsel]
+        t0 = time.perf_counter()
+        t.sfmm(w["theta"], leaf_sample=sel)
+        dt = time.perf_counter() - t0
+        t_walk += dt
+        nl_done += nsel
+        np_done += int(t.count[t.leaves[sel]].sum())
+        if t_walk > budget_s or nl_done >= t.nleaves:
+            break
+        nsel = int(min(t.nleaves - nl_done, max(nsel, nsel * min(8.0, (budget_s - t_walk) / max(dt, 1e-3)))))
+    t_full = t_build + t_walk * (t.n / max(np_done, 1))
+    return {"value": t.n / t_full, "unit": "particles/s", "cores": threads, "kind": "oracle",
+            "sample": "full FP64 oracle tree build (%.1f s) + Algorithms 1-2 on %d of %d leaves (%d particles, "
+                      "%.1f s), scaled by particles" % (t_build, nl_done, t.nleaves, np_done, t_walk)}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import workloads
+
+    w = WORKLOAD
+    pos, m, h = workloads.plummer(w["n"], w["seed"])
+    times = []
+    base = None
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        base = _cpu_baseline(pos, m, h, w, budget_s=3.0 if it >= args.warmup else 1.0)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = base["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * w["n"] / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Plummer sphere)",
+            "config": {"workload": w["name"], "n": w["n"], "theta": w["theta"], "order": w["order"],
+                       "leaf_size": w["leaf_size"], "form": "oracle FP64 (CPU)"},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _flush(buf):
+    buf.add_(1)
+
+
+def time_steps(torch, solver, pos_d, m_d, h_d, acc, pot, w, theta, steps, warmup, flush):
+    """Per-step device time (CUDA events on the solver's stream), L2 flushed
+    between steps outside the events."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    from paper_2602_05804_gb300 import sfmm
+
+    n = m_d.shape[0]
+    for _ in range(warmup):
+        sfmm.sfmm_build(solver.ctx, n, pos_d, m_d, h_d, w["leaf_size"])
+        sfmm.sfmm_gravity(solver.ctx, theta, w["order"], acc, pot)
+    stage = {"ms_build": 0.0, "ms_moments": 0.0, "ms_walk": 0.0, "ms_p2p": 0.0, "ms_reduce": 0.0}
+    launches0 = solver.stats()["kernel_launches"]
+    for k in range(steps):
+        _flush(flush)
+        ev[k][0].record(solver.stream)
+        sfmm.sfmm_build(solver.ctx, n, pos_d, m_d, h_d, w["leaf_size"])
+        sfmm.sfmm_gravity(solver.ctx, theta, w["order"], acc, pot)
+        ev[k][1].record(solver.stream)
+        st = solver.stats()
+        for key in stage:
+            stage[key] += st[key]
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    st = solver.stats()
+    st["kernel_launches_per_step"] = (st["kernel_launches"] - launches0) / steps
+    for key in stage:
+        st[key] = stage[key] / steps
+    return ms, st
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import workloads
+    from paper_2602_05804_gb300 import sfmm
+
+    w = WORKLOAD
+    pos, m, h = workloads.plummer(w["n"], w["seed"] + rank)
+    dev = torch.device("cuda", local)
+    pos_d = torch.from_numpy(pos).to(dev)
+    m_d = torch.from_numpy(m).to(dev)
+    h_d = torch.from_numpy(h).to(dev)
+    acc = torch.empty((w["n"], 3), dtype=torch.float64, device=dev)
+    pot = torch.empty(w["n"], dtype=torch.float64, device=dev)
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    s32 = sfmm.Solver(local, "fp32", profile=1)
+    s64 = sfmm.Solver(local, "fp64", profile=1)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # headline: FP32 form, theta = 0.5, whole step, max over ranks
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        ms32, st32 = time_steps(torch, s32, pos_d, m_d, h_d, acc, pot, w, w["theta"], args.steps, args.warmup, flush)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    step_ms = float(np.mean(ms32))
+    if dist is not None:
+        tt = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms = float(tt.item())
+    value = ws * w["n"] / (step_ms * 1e-3)
+    inter = st32["p2p_pairs"] + st32["m2l_unique"]
+
+    if args.only == "fp32":
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
+                              "ms_per_step": step_ms, "stage_ms": {k: st32[k] for k in ("ms_build", "ms_moments",
+                                                                                         "ms_walk", "ms_p2p")},
+                              "partial": "headline FP32 step only"}))
+        s32.close()
+        s64.close()
+        return 0
+    # FP64 form (same workload, fewer steps: it is ~50x slower)
+    k64 = max(1, min(args.steps, 3))
+    ms64, st64 = time_steps(torch, s64, pos_d, m_d, h_d, acc, pot, w, w["theta"], k64, 1, flush)
+    fp64_ms = float(np.mean(ms64))
+    # theta sweep of the FP32 form
+    sweep = {}
+    for th in (0.3, 0.7):
+        ms_t, st_t = time_steps(torch, s32, pos_d, m_d, h_d, acc, pot, w, th, max(1, min(args.steps, 3)), 1, flush)
+        sweep[str(th)] = {"particles_per_s": w["n"] / (np.mean(ms_t) * 1e-3),
+                          "interactions_per_s": (st_t["p2p_pairs"] + st_t["m2l_unique"]) / (np.mean(ms_t) * 1e-3),
+                          "ms_per_step": float(np.mean(ms_t)), "m2l": st_t["m2l"], "p2p_pairs": st_t["p2p_pairs"]}
+
+    # e2e through the C ABI with HOST buffers (pinned), copies inside the region
+    pos_h = torch.from_numpy(pos).pin_memory()
+    m_h = torch.from_numpy(m).pin_memory()
+    h_h = torch.from_numpy(h).pin_memory()
+    acc_h = torch.empty((w["n"], 3), dtype=torch.float64).pin_memory()
+    pot_h = torch.empty(w["n"], dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        s32.solve_host(pos_h, m_h, h_h, w["leaf_size"], w["theta"], w["order"], acc_h, pot_h)
+    ke = max(1, min(args.steps, 5))
+    barrier()
+    e2e_s = 0.0
+    for _ in range(ke):
+        _flush(flush)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s32.solve_host(pos_h, m_h, h_h, w["leaf_size"], w["theta"], w["order"], acc_h, pot_h)  # syncs
+        e2e_s += time.perf_counter() - t1
+    e2e_ms = 1e3 * e2e_s / ke
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    # roofline of the dominant kernel
+    peaks, peak_kind = _peaks()
+    clocks = clk.summary()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, unit counts x max clock
+    shares = {"walk": st32["ms_walk"], "p2p": st32["ms_p2p"], "build": st32["ms_build"],
+              "moments": st32["ms_moments"]}
+    if st32["ms_p2p"] >= st32["ms_walk"]:
+        kname, kms = "k_p2p<FP32>", st32["ms_p2p"]
+        achieved = st32["p2p_pairs"] * FLOPS_PER_PAIR / (kms * 1e-3) / 1e12
+        src = _kernel_hash("p2p.cu")
+    else:
+        kname, kms = "k_walk<2,FP32>", st32["ms_walk"]
+        achieved = st32["m2l"] * 136 / (kms * 1e-3) / 1e12
+        src = _kernel_hash("walk.cu", "expansion_gen.cuh")
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": _traffic(kname, src),
+            "peak_source": "FP32 FMA units: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock, %s peaks file)"
+                           % (sm_max, peak_kind),
+            "ms_per_launch": kms, "stage_ms": shares}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Plummer sphere, one per rank)",
+        "config": {"workload": w["name"], "n": w["n"], "theta": w["theta"], "order": w["order"],
+                   "leaf_size": w["leaf_size"], "form": "FP32 (FP64 centres, decisions, reductions)",
+                   "l2": "flushed between timed steps (512 MB write outside the events)"},
+        "interactions_per_s": ws * inter / (step_ms * 1e-3),
+        "counts": {"m2l_replicated": st32["m2l"], "m2l_unique": st32["m2l_unique"],
+                   "p2p_pairs": st32["p2p_pairs"], "p2p_leaf_pairs": st32["p2p_leaves"],
+                   "mac_fallbacks": st32["mac_fallbacks"], "nleaves": st32["nleaves"]},
+        "fp64_form": {"particles_per_s": ws * w["n"] / (fp64_ms * 1e-3), "ms_per_step": fp64_ms,
+                      "speedup_fp32_over_fp64": fp64_ms / step_ms,
+                      "stage_ms": {"walk": st64["ms_walk"], "p2p": st64["ms_p2p"], "build": st64["ms_build"]}},
+        "momentum_residual": {"fp32": float(np.linalg.norm(st32["momentum"]) / st32["abs_momentum"]),
+                              "fp64": float(np.linalg.norm(st64["momentum"]) / st64["abs_momentum"])},
+        "theta_sweep_fp32": sweep,
+        "e2e": {"value": ws * w["n"] / (e2e_ms * 1e-3), "unit": "particles/s",
+                "h2d_bytes_per_step": int(w["n"] * 40), "d2h_bytes_per_step": int(w["n"] * 32)},
+        "gpu_launches": int(st32["kernel_launches_per_step"] * args.steps),
+        "roofline": roof,
+        "clocks": clocks,
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(pos, m, h, w)
+    if rank == 0:
+        print(json.dumps(line))
+    s32.close()
+    s64.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="particle count (default: the workload's 10^6)")
+    ap.add_argument("--only", default="all", choices=["all", "fp32"],
+                    help="fp32: time the headline FP32 step only (for profiler launch lists)")
+    args = ap.parse_args()
+    if args.n:
+        WORKLOAD["n"] = int(args.n)
+        WORKLOAD["name"] = "plummer_%d" % args.n
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

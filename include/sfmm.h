@@ -1,0 +1,198 @@
+/*
+ * sfmm.h -- C ABI of the GB300 (sm_103a) symmetric fast multipole gravity
+ * solver with adaptive kernel softening.
+ *
+ * The method is the momentum-conserving symmetric Cartesian fast multipole
+ * method (SFMM) of Bernard, David-Cleris, Price & Lau, "Momentum-conserving
+ * self-gravity in the Phantom SPH code" (arXiv 2602.05804):
+ *   - the softened gravitational acceleration and potential of N particles
+ *     (Sect. 2, Eqs. directsum and softdirectsum) are computed with
+ *   - a binary tree whose nodes carry Cartesian mass moments (Eq. massmom,
+ *     moments translated bottom-up with Eq. massmomtrans, App. A.1),
+ *   - a dual-tree walk replayed per leaf on the leaf's branch of parents
+ *     (Algorithms 1 and 2, Sect. 3) with the opening-angle criterion and the
+ *     softening criterion of Sect. 3,
+ *   - node-node expansions (Eq. dmkdeffmm, Sect. 2.2) translated down the
+ *     branch (Eq. gravmtranslat, App. A.2) and evaluated at the particles,
+ *   - pairwise kernel-softened gravity for every pair inside the kernel.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SFMM_OK (0) or one of the error codes below.  No entry
+ *     point throws, aborts or prints; sfmm_last_error() gives a message.
+ *   - Device pointers are CUDA device (or managed) memory on the context's
+ *     device, owned by the caller; the library never frees them.  "host"
+ *     pointers are ordinary or pinned host memory, owned by the caller.
+ *   - All work is issued on the context's stream.  Calls return after the
+ *     work they issued has completed (each call ends with one stream
+ *     synchronisation to read the device status word), so outputs are ready
+ *     on return.
+ *   - Positions are row-major n x 3 (x, y, z per particle) float64.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef SFMM_H
+#define SFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfmm_ctx sfmm_ctx;
+
+/* Error codes. */
+enum {
+  SFMM_OK = 0,
+  SFMM_EINVAL = 1,      /* bad argument (range, NULL, size) */
+  SFMM_ENOMEM = 2,      /* device allocation failed */
+  SFMM_ECUDA = 3,       /* a CUDA runtime call failed */
+  SFMM_ESTATE = 4,      /* call out of order (e.g. gravity before build) */
+  SFMM_ESTACK = 5,      /* a leaf's branch is deeper than the walk supports */
+  SFMM_ECAPACITY = 6,   /* a work buffer was too small even after regrowing */
+  SFMM_ENONFINITE = 7,  /* non-finite or non-positive input value */
+  SFMM_ENOTIMPL = 8     /* not implemented in this build */
+};
+
+/* Arithmetic forms. */
+enum {
+  SFMM_FP64 = 0,  /* every step in float64 */
+  SFMM_FP32 = 1   /* P2P and M2L in float32 on coordinates relative to node
+                     centres; centres, sizes and the acceptance decisions in
+                     float64; inherited expansion coefficients accumulated in
+                     double-float; reductions in float64 */
+};
+
+/* Statistics of the last build / gravity call. */
+typedef struct sfmm_stats {
+  int64_t n;            /* particles */
+  int64_t nnodes;       /* tree nodes (leaves included) */
+  int64_t nleaves;      /* leaves */
+  int64_t m2l;          /* node-node interactions evaluated, counted once per
+                           leaf whose branch replays them (Algorithm 1) */
+  int64_t m2l_unique;   /* distinct directed node pairs among them */
+  int64_t p2p_leaves;   /* leaf-leaf entries of the neighbour lists */
+  int64_t p2p_pairs;    /* particle-particle evaluations (i != j) */
+  int64_t mac_fallbacks;/* acceptance tests settled by the exact float64 path */
+  double momentum[3];   /* sum_i m_i a_i */
+  double abs_momentum;  /* sum_i sum_d |m_i a_i,d| */
+  double W;             /* 1/2 sum_i m_i Phi_i */
+  double ms_build;      /* device time of the last sfmm_build (profiling on) */
+  double ms_moments;    /* device time of the moment pass of the last gravity */
+  double ms_walk;       /* device time of the walk + M2L + L2L + L2P kernel */
+  double ms_p2p;        /* device time of the near-field kernel */
+  double ms_reduce;     /* device time of the reductions */
+  double ms_gravity;    /* device time of the whole last sfmm_gravity */
+  int64_t kernel_launches; /* CUDA kernels this context has launched so far */
+} sfmm_stats;
+
+/* Create a context on CUDA device `device` in arithmetic form `precision`
+ * (SFMM_FP64 or SFMM_FP32).  `stream` is a cudaStream_t to issue all work on,
+ * or NULL for a stream the context creates and owns.  *out receives the
+ * context (NULL on failure).  Errors: EINVAL (bad device/precision), ECUDA. */
+int sfmm_create(sfmm_ctx** out, int device, int precision, void* stream);
+
+/* Destroy a context and free every buffer it owns.  NULL is a no-op. */
+void sfmm_destroy(sfmm_ctx* ctx);
+
+/* Replace the stream used by later calls (cudaStream_t, NULL = own stream). */
+int sfmm_set_stream(sfmm_ctx* ctx, void* stream);
+
+/* Set an option.  Keys:
+ *   "G"              gravitational constant (default 1, code units as in Sect. 4.2)
+ *   "self_potential" 1 adds each particle's own kernel term G m_i phi(0, h_i)
+ *                    to its potential (the j = i term of Eq. softdirectsum);
+ *                    default 0 (sum over j != i as in Eq. directsum)
+ *   "ring_capacity"  walk frontier entries per warp (power of two, >= 256)
+ *   "list_capacity"  P2P list arena entries (0 = automatic)
+ *   "profile"        1 records per-stage device times into the stats
+ * Errors: EINVAL (unknown key or out-of-range value). */
+int sfmm_set_option(sfmm_ctx* ctx, const char* key, double value);
+
+/* Build the tree (Sect. 3) of n particles: bounding box, 63-bit Morton keys
+ * (21 bits per axis on the cube of the box's largest extent), stable sort by
+ * (key, input index), binary radix tree split at the highest differing bit
+ * of (key, sorted position), leaves of at most leaf_size particles, node
+ * centres of mass, sizes l = max |x_j - s| over the node's particles and
+ * maximum smoothing lengths h_max.
+ *   pos  device, n x 3 float64;  mass device, n float64 (> 0);
+ *   h    device, n float64 smoothing lengths (> 0);  leaf_size in [1, 64].
+ * The inputs are copied into the context and may be freed after the call.
+ * Errors: EINVAL (n < 1, n > 2^31 - 2, leaf_size, NULL), ENONFINITE,
+ * ENOMEM, ECUDA. */
+int sfmm_build(sfmm_ctx* ctx, int64_t n, const double* pos, const double* mass, const double* h,
+               int leaf_size);
+
+/* Gravitational accelerations and potentials of the last built particle set
+ * (Sect. 3, Algorithms 1 and 2): mass moments to order `order` (Eq. massmom,
+ * App. A.1), the per-leaf walk with opening angle `theta`
+ * ((l_t + l_s) / d < theta) and the softening criterion
+ * (open if d < l_t + l_s + 2 max(h_max,t, h_max,s)), node-node expansions
+ * (Eq. dmkdeffmm), their translation down each branch (Eq. gravmtranslat),
+ * evaluation at the particles and pairwise M4-softened gravity over the
+ * neighbour lists.
+ *   theta in [0, 1) (0: every pair pairwise, i.e. the softened direct sum);
+ *   order in [0, 4] (expansion order p; moments to p, coefficients to p + 1);
+ *   acc  device, n x 3 float64, caller (input) order, written;
+ *   pot  device, n float64, caller order, written; may be NULL.
+ * Errors: ESTATE (no build), EINVAL, ESTACK, ECAPACITY, ENOMEM, ECUDA. */
+int sfmm_gravity(sfmm_ctx* ctx, double theta, int order, double* acc, double* pot);
+
+/* Whole solve from HOST buffers: copies the inputs to the device, builds,
+ * runs the gravity and copies the results back, all on the context's stream.
+ * Same arguments and errors as sfmm_build + sfmm_gravity, but every pointer
+ * is a host pointer (pinned memory gives the fastest copies). */
+int sfmm_solve_host(sfmm_ctx* ctx, int64_t n, const double* pos, const double* mass,
+                    const double* h, int leaf_size, double theta, int order, double* acc,
+                    double* pot);
+
+/* Statistics of the last calls (counts, momentum and energy sums; stage
+ * times when the "profile" option is on).  Errors: EINVAL (NULL). */
+int sfmm_get_stats(const sfmm_ctx* ctx, sfmm_stats* out);
+
+/* Sizes of the built tree.  Errors: ESTATE (no build). */
+int sfmm_tree_size(const sfmm_ctx* ctx, int64_t* nnodes, int64_t* nleaves);
+
+/* Copy the built tree to HOST arrays (any pointer may be NULL).  Nodes are in
+ * pre-order (a node's left child is the next node); leaves in tree order.
+ *   perm[n]    sorted position -> input index;   keys[n] Morton keys (sorted)
+ *   first/count/right/parent/depth[nnodes]  (right = -1 and count <= leaf_size
+ *              for leaves; parent = -1 for the root)
+ *   centre[nnodes x 3], size[nnodes], hmax[nnodes], mass[nnodes]
+ *   leaves[nleaves] node index of each leaf.
+ * Errors: ESTATE, ECUDA. */
+int sfmm_tree_export(const sfmm_ctx* ctx, int64_t* perm, uint64_t* keys, int32_t* first,
+                     int32_t* count, int32_t* right, int32_t* parent, int32_t* depth,
+                     double* centre, double* size, double* hmax, double* mass, int32_t* leaves);
+
+/* Compute the scaled mass moments Q_alpha / alpha! of every node to order
+ * `order` (Eq. massmom, translated with Eq. massmomtrans) and copy them to
+ * HOST array Q[nnodes x C(order+3,3)].  mi (may be NULL) receives the
+ * multi-index (a,b,c) of each column, C(order+3,3) x 3 int32.
+ * Errors: ESTATE, EINVAL, ECUDA. */
+int sfmm_moments_export(sfmm_ctx* ctx, int order, double* Q, int32_t* mi);
+
+/* Interaction lists of every leaf for opening angle theta (decisions of
+ * Algorithm 2 only, no arithmetic), into HOST arrays:
+ *   m2l_off[nleaves + 1], p2p_off[nleaves + 1] offsets (always written);
+ *   m2l_level[cap_m2l], m2l_src[cap_m2l]: level k of the branch node and the
+ *     source node of each accepted pair; p2p_src[cap_p2p]: neighbour leaves.
+ * With NULL entry arrays only the offsets are written (sizes query).  Order
+ * of entries within a leaf is unspecified.
+ * Errors: ESTATE, EINVAL (theta), ECAPACITY (caps too small), ECUDA. */
+int sfmm_lists(sfmm_ctx* ctx, double theta, int64_t* m2l_off, int32_t* m2l_level, int32_t* m2l_src,
+               int64_t cap_m2l, int64_t* p2p_off, int32_t* p2p_src, int64_t cap_p2p);
+
+/* Message describing an error code. */
+const char* sfmm_strerror(int code);
+
+/* Last error message recorded by this context (never NULL). */
+const char* sfmm_last_error(const sfmm_ctx* ctx);
+
+/* Library version string. */
+const char* sfmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFMM_H */

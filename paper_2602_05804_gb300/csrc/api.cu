@@ -1,0 +1,445 @@
+// C ABI of the SFMM gravity solver: contexts, argument checks, the build and
+// gravity pipelines, exports for tests, error reporting.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sfmm_internal.cuh"
+
+#define SFMM_VERSION "sfmm-gb300 0.1"
+
+int sfmm_internal_cuda_fail(cudaError_t e, const char*, const char*, int) {
+  return (e == cudaErrorMemoryAllocation) ? SFMM_ENOMEM : SFMM_ECUDA;
+}
+
+int DevBuf::ensure(size_t need) {
+  if (need == 0) need = 16;
+  if (need <= bytes) return SFMM_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+  size_t grow = need + need / 8;
+  if (cudaMalloc(&p, grow) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    return SFMM_ENOMEM;
+  }
+  bytes = grow;
+  return SFMM_OK;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+namespace sfmm {
+
+int set_error(sfmm_ctx* c, int code, const char* msg) {
+  if (c) c->last_error = msg ? msg : sfmm_strerror(code);
+  return code;
+}
+
+// Read (and clear) the device status word: one stream synchronisation.
+int sync_status(sfmm_ctx* c, int* bits) {
+  cudaError_t e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->last_error = cudaGetErrorString(e);
+    return (e == cudaErrorMemoryAllocation) ? SFMM_ENOMEM : SFMM_ECUDA;
+  }
+  *bits = *c->h_status;
+  if (*bits) {
+    e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return SFMM_ECUDA;
+  }
+  return SFMM_OK;
+}
+
+int run_walk_dump_write(sfmm_ctx* c, double theta, const long long* d_off, int* d_level, int* d_src);
+
+}  // namespace sfmm
+
+using namespace sfmm;
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.f;
+  }
+  return ms;
+}
+
+int check_ctx(const sfmm_ctx* c) { return c ? SFMM_OK : SFMM_EINVAL; }
+
+}  // namespace
+
+extern "C" {
+
+const char* sfmm_version(void) { return SFMM_VERSION; }
+
+const char* sfmm_strerror(int code) {
+  switch (code) {
+    case SFMM_OK: return "ok";
+    case SFMM_EINVAL: return "invalid argument";
+    case SFMM_ENOMEM: return "device allocation failed";
+    case SFMM_ECUDA: return "CUDA runtime error";
+    case SFMM_ESTATE: return "call out of order (no tree built)";
+    case SFMM_ESTACK: return "tree branch deeper than the walk supports";
+    case SFMM_ECAPACITY: return "work buffer capacity exceeded";
+    case SFMM_ENONFINITE: return "non-finite or non-positive input";
+    case SFMM_ENOTIMPL: return "not implemented";
+    default: return "unknown error";
+  }
+}
+
+const char* sfmm_last_error(const sfmm_ctx* c) { return c ? c->last_error.c_str() : "no context"; }
+
+int sfmm_create(sfmm_ctx** out, int device, int precision, void* stream) {
+  if (!out) return SFMM_EINVAL;
+  *out = nullptr;
+  if (precision != SFMM_FP64 && precision != SFMM_FP32) return SFMM_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return SFMM_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return SFMM_EINVAL;
+  DeviceGuard g(device);
+  sfmm_ctx* c = new (std::nothrow) sfmm_ctx();
+  if (!c) return SFMM_ENOMEM;
+  c->device = device;
+  c->precision = precision;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return SFMM_ECUDA;
+    }
+    c->owns_stream = true;
+  }
+  bool ok = cudaMalloc(&c->d_status, sizeof(int)) == cudaSuccess &&
+            cudaMallocHost(&c->h_status, sizeof(int)) == cudaSuccess &&
+            cudaMallocHost(&c->h_scalars, 64 * sizeof(double)) == cudaSuccess &&
+            cudaMemset(c->d_status, 0, sizeof(int)) == cudaSuccess;
+  for (int i = 0; ok && i < 8; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    sfmm_destroy(c);
+    return SFMM_ECUDA;
+  }
+  *out = c;
+  return SFMM_OK;
+}
+
+void sfmm_destroy(sfmm_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  DevBuf* bufs[] = {&c->in_pos, &c->in_mass, &c->in_h, &c->out_acc, &c->out_pot, &c->keys_a, &c->keys_b,
+                    &c->idx_a, &c->idx_b, &c->sort_counts, &c->scan_tmp, &c->bbox_part, &c->k_left,
+                    &c->k_right, &c->k_first, &c->k_last, &c->par_int, &c->par_leaf, &c->chain,
+                    &c->pre_int, &c->pre_leaf, &c->misc, &c->px, &c->py, &c->pz, &c->pm, &c->ph,
+                    &c->perm, &c->pnode, &c->prel, &c->ph32, &c->nfirst, &c->ncount, &c->nright,
+                    &c->nparent, &c->ndepth, &c->ncx, &c->ncy, &c->ncz, &c->nsize, &c->nhmax, &c->nmass,
+                    &c->l2bits, &c->flags, &c->geo_hi, &c->geo_lo, &c->leaf_node, &c->isleaf, &c->Qd,
+                    &c->Qf, &c->ring, &c->far, &c->arena, &c->p2p_off, &c->p2p_cnt, &c->counters,
+                    &c->red_part, &c->dump};
+  for (DevBuf* b : bufs) b->release();
+  for (int i = 0; i < 8; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int sfmm_set_stream(sfmm_ctx* c, void* stream) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  DeviceGuard g(c->device);
+  if (c->owns_stream && c->stream) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
+    c->stream = nullptr;
+    c->owns_stream = false;
+  }
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return SFMM_ECUDA;
+    c->owns_stream = true;
+  }
+  return SFMM_OK;
+}
+
+int sfmm_set_option(sfmm_ctx* c, const char* key, double v) {
+  if (check_ctx(c) || !key) return SFMM_EINVAL;
+  if (!std::isfinite(v)) return set_error(c, SFMM_EINVAL, "option value must be finite");
+  if (!strcmp(key, "G")) {
+    c->G = v;
+  } else if (!strcmp(key, "self_potential")) {
+    c->self_potential = (v != 0.0);
+  } else if (!strcmp(key, "ring_capacity")) {
+    int cap = (int)v;
+    if (cap < 256 || cap > (1 << 24) || (cap & (cap - 1))) return set_error(c, SFMM_EINVAL, "ring_capacity: power of two in [256, 2^24]");
+    c->ring_capacity = cap;
+  } else if (!strcmp(key, "list_capacity")) {
+    if (v < 0) return set_error(c, SFMM_EINVAL, "list_capacity must be >= 0");
+    c->list_capacity = (int64_t)v;
+  } else if (!strcmp(key, "profile")) {
+    c->profile = (v != 0.0);
+  } else {
+    return set_error(c, SFMM_EINVAL, "unknown option key");
+  }
+  return SFMM_OK;
+}
+
+int sfmm_build(sfmm_ctx* c, int64_t n, const double* pos, const double* mass, const double* h, int leaf_size) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (n < 1 || n > ((int64_t)1 << 31) - 2) return set_error(c, SFMM_EINVAL, "n must be in [1, 2^31 - 2]");
+  if (!pos || !mass || !h) return set_error(c, SFMM_EINVAL, "NULL input pointer");
+  if (leaf_size < 1 || leaf_size > 64) return set_error(c, SFMM_EINVAL, "leaf_size must be in [1, 64]");
+  DeviceGuard g(c->device);
+  c->built = false;
+  c->moments_order = -1;
+  c->n = n;
+  c->leaf_size = leaf_size;
+  if (c->profile) cudaEventRecord(c->ev[0], c->stream);
+  int rc = build_tree(c, pos, mass, h);
+  if (rc) return set_error(c, rc, "tree build failed");
+  if (c->profile) cudaEventRecord(c->ev[1], c->stream);
+  int bits = 0;
+  if ((rc = sync_status(c, &bits))) return rc;
+  if (bits & (SFMM_ST_NONFINITE | SFMM_ST_NONPOSITIVE))
+    return set_error(c, SFMM_ENONFINITE, "non-finite position/mass/h or non-positive mass/h");
+  if (bits) return set_error(c, SFMM_ECUDA, "internal consistency check of the tree failed");
+  c->built = true;
+  c->stats = sfmm_stats{};
+  c->stats.n = n;
+  c->stats.nnodes = c->nnodes;
+  c->stats.nleaves = c->nleaves;
+  if (c->profile) c->stats.ms_build = elapsed(c->ev[0], c->ev[1]);
+  return SFMM_OK;
+}
+
+int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (!c->built) return set_error(c, SFMM_ESTATE, "sfmm_gravity before sfmm_build");
+  if (!(theta >= 0.0 && theta < 1.0)) return set_error(c, SFMM_EINVAL, "theta must be in [0, 1)");
+  if (order < 0 || order > SFMM_PMAX) return set_error(c, SFMM_EINVAL, "order must be in [0, 4]");
+  if (!acc) return set_error(c, SFMM_EINVAL, "NULL acc");
+  DeviceGuard g(c->device);
+  int rc;
+  cudaStream_t st = c->stream;
+  if (c->profile) cudaEventRecord(c->ev[2], st);
+  if (c->moments_order != order) {
+    if ((rc = compute_moments(c, order))) return set_error(c, rc, "moment pass failed");
+  }
+  if (c->profile) cudaEventRecord(c->ev[3], st);
+  if ((rc = run_walk(c, theta, order, false, 0, 0))) return rc;
+  if (c->profile) cudaEventRecord(c->ev[4], st);
+  if ((rc = run_p2p(c, acc, pot))) return set_error(c, rc, "near-field pass failed");
+  if (c->profile) cudaEventRecord(c->ev[5], st);
+  if ((rc = run_reduce(c, acc, pot))) return set_error(c, rc, "reduction failed");
+  if (c->profile) cudaEventRecord(c->ev[6], st);
+  double* red = c->red_part.as<double>() + 5 * (size_t)c->nleaves;
+  cudaError_t e = cudaMemcpyAsync(c->h_scalars + 16, red, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return set_error(c, SFMM_ECUDA, cudaGetErrorString(e));
+  int bits = 0;
+  if ((rc = sync_status(c, &bits))) return rc;
+  if (bits) return set_error(c, SFMM_ECUDA, "device status error after the near-field pass");
+  const double* r = c->h_scalars + 16;
+  c->stats.momentum[0] = r[0];
+  c->stats.momentum[1] = r[1];
+  c->stats.momentum[2] = r[2];
+  c->stats.abs_momentum = r[3];
+  c->stats.W = 0.5 * r[4];
+  if (c->profile) {
+    c->stats.ms_moments = elapsed(c->ev[2], c->ev[3]);
+    c->stats.ms_walk = elapsed(c->ev[3], c->ev[4]);
+    c->stats.ms_p2p = elapsed(c->ev[4], c->ev[5]);
+    c->stats.ms_reduce = elapsed(c->ev[5], c->ev[6]);
+    c->stats.ms_gravity = elapsed(c->ev[2], c->ev[6]);
+  }
+  return SFMM_OK;
+}
+
+int sfmm_solve_host(sfmm_ctx* c, int64_t n, const double* pos, const double* mass, const double* h, int leaf_size,
+                    double theta, int order, double* acc, double* pot) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (!pos || !mass || !h || !acc) return set_error(c, SFMM_EINVAL, "NULL pointer");
+  if (n < 1 || n > ((int64_t)1 << 31) - 2) return set_error(c, SFMM_EINVAL, "n must be in [1, 2^31 - 2]");
+  if (!(theta >= 0.0 && theta < 1.0)) return set_error(c, SFMM_EINVAL, "theta must be in [0, 1)");
+  if (order < 0 || order > SFMM_PMAX) return set_error(c, SFMM_EINVAL, "order must be in [0, 4]");
+  if (leaf_size < 1 || leaf_size > 64) return set_error(c, SFMM_EINVAL, "leaf_size must be in [1, 64]");
+  DeviceGuard g(c->device);
+  int rc;
+  if ((rc = c->in_pos.ensure(sizeof(double) * 3 * (size_t)n)) || (rc = c->in_mass.ensure(sizeof(double) * n)) ||
+      (rc = c->in_h.ensure(sizeof(double) * n)) || (rc = c->out_acc.ensure(sizeof(double) * 3 * (size_t)n)) ||
+      (rc = c->out_pot.ensure(sizeof(double) * n)))
+    return set_error(c, rc, "staging allocation failed");
+  cudaStream_t st = c->stream;
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->in_pos.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->in_mass.p, mass, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->in_h.p, h, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if ((rc = sfmm_build(c, n, c->in_pos.as<double>(), c->in_mass.as<double>(), c->in_h.as<double>(), leaf_size)))
+    return rc;
+  if ((rc = sfmm_gravity(c, theta, order, c->out_acc.as<double>(), pot ? c->out_pot.as<double>() : nullptr)))
+    return rc;
+  SFMM_CUDA_TRY(cudaMemcpyAsync(acc, c->out_acc.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+  if (pot) SFMM_CUDA_TRY(cudaMemcpyAsync(pot, c->out_pot.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  SFMM_CUDA_TRY(cudaStreamSynchronize(st));
+  return SFMM_OK;
+}
+
+int sfmm_get_stats(const sfmm_ctx* c, sfmm_stats* out) {
+  if (check_ctx(c) || !out) return SFMM_EINVAL;
+  *out = c->stats;
+  out->kernel_launches = c->nlaunch;
+  return SFMM_OK;
+}
+
+int sfmm_tree_size(const sfmm_ctx* c, int64_t* nnodes, int64_t* nleaves) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (!c->built) return SFMM_ESTATE;
+  if (nnodes) *nnodes = c->nnodes;
+  if (nleaves) *nleaves = c->nleaves;
+  return SFMM_OK;
+}
+
+int sfmm_tree_export(const sfmm_ctx* cc, int64_t* perm, uint64_t* keys, int32_t* first, int32_t* count,
+                     int32_t* right, int32_t* parent, int32_t* depth, double* centre, double* size, double* hmax,
+                     double* mass, int32_t* leaves) {
+  sfmm_ctx* c = const_cast<sfmm_ctx*>(cc);
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (!c->built) return SFMM_ESTATE;
+  DeviceGuard g(c->device);
+  const size_t n = (size_t)c->n, nn = (size_t)c->nnodes;
+  cudaStream_t st = c->stream;
+  int rc;
+  if (depth && (rc = compute_depth(c))) return rc;
+  SFMM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (perm) {
+    std::vector<int32_t> tmp(n);
+    SFMM_CUDA_TRY(cudaMemcpy(tmp.data(), c->perm.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) perm[i] = tmp[i];
+  }
+  if (keys) SFMM_CUDA_TRY(cudaMemcpy(keys, c->keys_a.p, n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  if (first) SFMM_CUDA_TRY(cudaMemcpy(first, c->nfirst.p, nn * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (count) SFMM_CUDA_TRY(cudaMemcpy(count, c->ncount.p, nn * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (right) SFMM_CUDA_TRY(cudaMemcpy(right, c->nright.p, nn * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (parent) SFMM_CUDA_TRY(cudaMemcpy(parent, c->nparent.p, nn * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (depth) SFMM_CUDA_TRY(cudaMemcpy(depth, c->ndepth.p, nn * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (centre) {
+    std::vector<double> x(nn), y(nn), z(nn);
+    SFMM_CUDA_TRY(cudaMemcpy(x.data(), c->ncx.p, nn * sizeof(double), cudaMemcpyDeviceToHost));
+    SFMM_CUDA_TRY(cudaMemcpy(y.data(), c->ncy.p, nn * sizeof(double), cudaMemcpyDeviceToHost));
+    SFMM_CUDA_TRY(cudaMemcpy(z.data(), c->ncz.p, nn * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t v = 0; v < nn; ++v) {
+      centre[3 * v] = x[v];
+      centre[3 * v + 1] = y[v];
+      centre[3 * v + 2] = z[v];
+    }
+  }
+  if (size) SFMM_CUDA_TRY(cudaMemcpy(size, c->nsize.p, nn * sizeof(double), cudaMemcpyDeviceToHost));
+  if (hmax) SFMM_CUDA_TRY(cudaMemcpy(hmax, c->nhmax.p, nn * sizeof(double), cudaMemcpyDeviceToHost));
+  if (mass) SFMM_CUDA_TRY(cudaMemcpy(mass, c->nmass.p, nn * sizeof(double), cudaMemcpyDeviceToHost));
+  if (leaves) SFMM_CUDA_TRY(cudaMemcpy(leaves, c->leaf_node.p, (size_t)c->nleaves * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return SFMM_OK;
+}
+
+int sfmm_moments_export(sfmm_ctx* c, int order, double* Q, int32_t* mi) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (!c->built) return SFMM_ESTATE;
+  if (order < 0 || order > SFMM_PMAX) return SFMM_EINVAL;
+  DeviceGuard g(c->device);
+  int rc;
+  if (c->moments_order != order && (rc = compute_moments(c, order))) return rc;
+  const int nq = ncoef(order);
+  SFMM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (Q) SFMM_CUDA_TRY(cudaMemcpy(Q, c->Qd.p, sizeof(double) * (size_t)c->nnodes * nq, cudaMemcpyDeviceToHost));
+  if (mi) {
+    int k = 0;
+    for (int n = 0; n <= order; ++n)
+      for (int a = n; a >= 0; --a)
+        for (int b = n - a; b >= 0; --b) {
+          mi[3 * k] = a;
+          mi[3 * k + 1] = b;
+          mi[3 * k + 2] = n - a - b;
+          ++k;
+        }
+  }
+  return SFMM_OK;
+}
+
+int sfmm_lists(sfmm_ctx* c, double theta, int64_t* m2l_off, int32_t* m2l_level, int32_t* m2l_src, int64_t cap_m2l,
+               int64_t* p2p_off, int32_t* p2p_src, int64_t cap_p2p) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (!c->built) return SFMM_ESTATE;
+  if (!(theta >= 0.0 && theta < 1.0)) return set_error(c, SFMM_EINVAL, "theta must be in [0, 1)");
+  if (!m2l_off || !p2p_off) return set_error(c, SFMM_EINVAL, "NULL offsets");
+  DeviceGuard g(c->device);
+  const int nl = c->nleaves;
+  int rc;
+  if ((rc = run_walk(c, theta, 0, true, 0, 0))) return rc;
+  std::vector<int> cnt(nl), pcnt(nl);
+  std::vector<long long> poff(nl);
+  SFMM_CUDA_TRY(cudaMemcpy(cnt.data(), c->dump.p, sizeof(int) * nl, cudaMemcpyDeviceToHost));
+  m2l_off[0] = 0;
+  for (int q = 0; q < nl; ++q) m2l_off[q + 1] = m2l_off[q] + cnt[q];
+  const int64_t tot = m2l_off[nl];
+  if (m2l_level && m2l_src) {
+    if (cap_m2l < tot) return set_error(c, SFMM_ECAPACITY, "m2l capacity too small");
+    DevBuf off, lev, src;
+    if ((rc = off.ensure(sizeof(long long) * (nl + 1))) || (rc = lev.ensure(sizeof(int) * (size_t)(tot + 1))) ||
+        (rc = src.ensure(sizeof(int) * (size_t)(tot + 1))))
+      return rc;
+    std::vector<long long> offh(nl + 1);
+    for (int q = 0; q <= nl; ++q) offh[q] = m2l_off[q];
+    cudaMemcpy(off.p, offh.data(), sizeof(long long) * (nl + 1), cudaMemcpyHostToDevice);
+    rc = run_walk_dump_write(c, theta, off.as<long long>(), lev.as<int>(), src.as<int>());
+    if (rc == SFMM_OK) {
+      cudaMemcpy(m2l_level, lev.p, sizeof(int) * (size_t)tot, cudaMemcpyDeviceToHost);
+      cudaMemcpy(m2l_src, src.p, sizeof(int) * (size_t)tot, cudaMemcpyDeviceToHost);
+    }
+    off.release();
+    lev.release();
+    src.release();
+    if (rc) return rc;
+  }
+  SFMM_CUDA_TRY(cudaMemcpy(pcnt.data(), c->p2p_cnt.p, sizeof(int) * nl, cudaMemcpyDeviceToHost));
+  SFMM_CUDA_TRY(cudaMemcpy(poff.data(), c->p2p_off.p, sizeof(long long) * nl, cudaMemcpyDeviceToHost));
+  p2p_off[0] = 0;
+  for (int q = 0; q < nl; ++q) p2p_off[q + 1] = p2p_off[q] + pcnt[q];
+  if (p2p_src) {
+    if (cap_p2p < p2p_off[nl]) return set_error(c, SFMM_ECAPACITY, "p2p capacity too small");
+    for (int q = 0; q < nl; ++q)
+      if (pcnt[q])
+        SFMM_CUDA_TRY(cudaMemcpy(p2p_src + p2p_off[q], c->arena.as<int>() + poff[q], sizeof(int) * pcnt[q],
+                                 cudaMemcpyDeviceToHost));
+  }
+  return SFMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// Shared device helpers of the SFMM gravity library (CUDA, sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sfmm.h"
+
+#define SFMM_FULL 0xffffffffu
+#define SFMM_PMAX 4
+#define SFMM_RKERN 2.0
+
+// Device status bits (one int per context, OR-ed by kernels, read once per call).
+#define SFMM_ST_NONFINITE   0x01  // a non-finite position, mass or smoothing length
+#define SFMM_ST_NONPOSITIVE 0x02  // mass <= 0 or h <= 0
+#define SFMM_ST_RING        0x04  // walk frontier ring overflow (capacity)
+#define SFMM_ST_ARENA       0x08  // P2P list arena overflow (capacity)
+#define SFMM_ST_DEPTH       0x10  // branch deeper than SFMM_MAXDEPTH
+#define SFMM_ST_INTERNAL    0x20  // internal consistency check failed
+
+#define SFMM_MAXDEPTH 128
+
+namespace sfmm {
+
+// ---------------------------------------------------------------------------
+// Exact-rounding FP64 helpers: every operation rounded as written, no FMA
+// contraction, so that acceptance decisions match a plain FP64 evaluation of
+// the same expression bit for bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+
+// ---------------------------------------------------------------------------
+// Double-float helpers (Dekker 1971; Knuth's TwoSum): a value carried as an
+// unevaluated sum hi + lo of two floats.
+// ---------------------------------------------------------------------------
+struct dfloat { float hi, lo; };
+
+__device__ __forceinline__ void split_double(double v, float& hi, float& lo) {
+  hi = __double2float_rn(v);
+  lo = __double2float_rn(v - (double)hi);
+}
+
+// TwoSum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+// (hi, lo) + b, renormalised.
+__device__ __forceinline__ dfloat df_add_f(dfloat a, float b) {
+  dfloat s = two_sum(a.hi, b);
+  float lo = __fadd_rn(s.lo, a.lo);
+  return two_sum(s.hi, lo);
+}
+
+// Difference of two double-float centres as a float (|error| ~ 2^-24 |d|).
+__device__ __forceinline__ float df_diff(float ahi, float alo, float bhi, float blo) {
+  return __fadd_rn(__fsub_rn(ahi, bhi), __fsub_rn(alo, blo));
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ void set_status(int* status, int bits) { atomicOr(status, bits); }
+
+// Number of scaled multi-index coefficients with |alpha| <= p.
+__host__ __device__ constexpr int ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+}  // namespace sfmm
+
+// Host-side helpers shared by the .cu files.
+#define SFMM_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return sfmm_internal_cuda_fail(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+int sfmm_internal_cuda_fail(cudaError_t e, const char* expr, const char* file, int line);

@@ -1,0 +1,106 @@
+// Internal declarations of the SFMM gravity library: the context and the
+// stage launchers implemented in tree.cu, moments.cu, walk.cu, p2p.cu.
+#pragma once
+#include <string>
+
+#include "sfmm_common.cuh"
+
+// Device buffer that only grows (freed on destroy).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need);  // SFMM_OK / SFMM_ENOMEM
+  void release();
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct sfmm_ctx {
+  int device = 0;
+  int precision = SFMM_FP64;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  std::string last_error;
+
+  // options
+  double G = 1.0;
+  int self_potential = 0;
+  int ring_capacity = 8192;
+  int64_t list_capacity = 0;
+  int profile = 0;
+
+  // built state
+  bool built = false;
+  int64_t n = 0;
+  int leaf_size = 0;
+  int32_t nnodes = 0, nleaves = 0;
+  int moments_order = -1;  // order of the cached moments (-1: none)
+
+  // inputs staged from host (sfmm_solve_host)
+  DevBuf in_pos, in_mass, in_h;
+  DevBuf out_acc, out_pot;
+
+  // sort / build temporaries
+  DevBuf keys_a, keys_b, idx_a, idx_b, sort_counts, scan_tmp, bbox_part;
+  DevBuf k_left, k_right, k_first, k_last, par_int, par_leaf, chain, pre_int, pre_leaf;
+  DevBuf misc;  // device-side scalars: bbox, counters
+
+  // sorted particles
+  DevBuf px, py, pz, pm, ph;    // float64 SoA
+  DevBuf perm;                  // int32 sorted position -> input index
+  DevBuf pnode;                 // int32 sorted position -> leaf node
+  DevBuf prel;                  // float4 {x - s_leaf, y - s_leaf, z - s_leaf, m}
+  DevBuf ph32;                  // float h
+
+  // nodes (pre-order)
+  DevBuf nfirst, ncount, nright, nparent, ndepth;
+  DevBuf ncx, ncy, ncz, nsize, nhmax, nmass;
+  DevBuf l2bits, flags;
+  DevBuf geo_hi, geo_lo;        // float4 walk records
+  DevBuf leaf_node, isleaf;
+  DevBuf Qd, Qf;                // scaled moments float64 [nn x NQ], float32 [nn x NQS]
+
+  // gravity
+  DevBuf ring, far, arena, p2p_off, p2p_cnt, counters, red_part, dump;
+
+  // status word (device) + pinned host mirror
+  int* d_status = nullptr;
+  int* h_status = nullptr;
+  double* h_scalars = nullptr;  // pinned host scratch
+
+  int64_t nlaunch = 0;  // kernels launched by this context (cumulative)
+  cudaEvent_t ev[8] = {};
+  sfmm_stats stats{};
+};
+
+namespace sfmm {
+
+int set_error(sfmm_ctx* c, int code, const char* msg);
+
+// tree.cu
+int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double* h);
+int compute_depth(sfmm_ctx* c);
+
+// scan (tree.cu): exclusive scan of n uint32 values in place, returns total
+// through `total_dev` (device uint32, may be null)
+int exclusive_scan_u32(sfmm_ctx* c, uint32_t* data, int64_t n, uint32_t* total_dev);
+
+// moments.cu
+int compute_moments(sfmm_ctx* c, int order);
+
+// walk.cu
+int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, int64_t cap_p2p);
+
+// p2p.cu
+int run_p2p(sfmm_ctx* c, double* acc, double* pot);
+int run_reduce(sfmm_ctx* c, const double* acc, const double* pot);
+
+int check_status(sfmm_ctx* c);
+int sync_status(sfmm_ctx* c, int* bits);
+
+inline int num_sms(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  return v > 0 ? v : 1;
+}
+
+}  // namespace sfmm

@@ -1,0 +1,761 @@
+// Tree build of the SFMM solver (Sect. 3): bounding box, Morton keys, radix
+// sort, binary radix tree collapsed to leaves of <= leaf_size particles,
+// pre-order node layout, node centres of mass, maximum smoothing lengths and
+// exact sizes l = max_j |x_j - s| over each node's particles.
+#include <cfloat>
+
+#include "sfmm_internal.cuh"
+
+namespace sfmm {
+
+// ---------------------------------------------------------------------------
+// Block-wide helpers
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(SFMM_FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = (lane < NT / 32) ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(SFMM_FULL, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NT / 32) warp_tot[lane] = w;  // inclusive per-warp totals
+  }
+  __syncthreads();
+  uint32_t base = warp ? warp_tot[warp - 1] : 0u;
+  total = warp_tot[NT / 32 - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of uint32 (three passes: tile sums, scan of sums, rescan)
+// ---------------------------------------------------------------------------
+#define SCAN_NT 512
+#define SCAN_ITEMS 8
+#define SCAN_TILE (SCAN_NT * SCAN_ITEMS)
+
+__global__ void k_scan_tile_sums(const uint32_t* __restrict__ d, int64_t n, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wt[SCAN_NT / 32];
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  uint32_t s = 0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + (int64_t)k * SCAN_NT + threadIdx.x;
+    if (i < n) s += d[i];
+  }
+  uint32_t tot;
+  block_exclusive_scan<SCAN_NT>(s, wt, tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the tile sums (any count, serial chunks).
+__global__ void k_scan_sums(uint32_t* __restrict__ sums, int nt, uint32_t* __restrict__ total_out) {
+  __shared__ uint32_t wt[SCAN_NT / 32];
+  uint32_t carry = 0;
+  for (int base = 0; base < nt; base += SCAN_NT) {
+    int i = base + threadIdx.x;
+    uint32_t v = (i < nt) ? sums[i] : 0u;
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan<SCAN_NT>(v, wt, tot);
+    if (i < nt) sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void k_scan_apply(uint32_t* __restrict__ d, int64_t n, const uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wt[SCAN_NT / 32];
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  uint32_t carry = sums[blockIdx.x];
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + (int64_t)k * SCAN_NT + threadIdx.x;
+    uint32_t v = (i < n) ? d[i] : 0u;
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan<SCAN_NT>(v, wt, tot);
+    if (i < n) d[i] = carry + ex;
+    carry += tot;
+  }
+}
+
+int exclusive_scan_u32(sfmm_ctx* c, uint32_t* data, int64_t n, uint32_t* total_dev) {
+  int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (nt < 1) nt = 1;
+  int rc = c->scan_tmp.ensure(sizeof(uint32_t) * (size_t)nt);
+  if (rc) return rc;
+  uint32_t* sums = c->scan_tmp.as<uint32_t>();
+  k_scan_tile_sums<<<(unsigned)nt, SCAN_NT, 0, c->stream>>>(data, n, sums);
+  ++c->nlaunch;
+  k_scan_sums<<<1, SCAN_NT, 0, c->stream>>>(sums, (int)nt, total_dev);
+  ++c->nlaunch;
+  k_scan_apply<<<(unsigned)nt, SCAN_NT, 0, c->stream>>>(data, n, sums);
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
+  return SFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// S1: bounding box + input validation
+// ---------------------------------------------------------------------------
+#define BB_NT 256
+
+__global__ void k_bbox_partial(const double* __restrict__ pos, const double* __restrict__ mass,
+                               const double* __restrict__ h, int n, double* __restrict__ part,
+                               int* __restrict__ status) {
+  double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double v = pos[3 * (int64_t)i + c];
+      if (!isfinite(v)) bad |= SFMM_ST_NONFINITE;
+      mn[c] = fmin(mn[c], v);
+      mx[c] = fmax(mx[c], v);
+    }
+    double m = mass[i], hh = h[i];
+    if (!isfinite(m) || !isfinite(hh)) bad |= SFMM_ST_NONFINITE;
+    if (!(m > 0.0) || !(hh > 0.0)) bad |= SFMM_ST_NONPOSITIVE;
+  }
+  __shared__ double s[6][BB_NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[c] = fmin(mn[c], __shfl_xor_sync(SFMM_FULL, mn[c], o));
+      mx[c] = fmax(mx[c], __shfl_xor_sync(SFMM_FULL, mx[c], o));
+    }
+    if (lane == 0) { s[c][warp] = mn[c]; s[3 + c][warp] = mx[c]; }
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    int c = threadIdx.x;
+    double v = s[c][0];
+    for (int w = 1; w < BB_NT / 32; ++w) v = (c < 3) ? fmin(v, s[c][w]) : fmax(v, s[c][w]);
+    part[6 * blockIdx.x + c] = v;
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+// bbox[0..2] min, [3..5] max, [6] cube extent E, [7] key scale 2^21 / E (0 if E == 0)
+__global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ bbox) {
+  if (threadIdx.x != 0) return;
+  double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int b = 0; b < nb; ++b)
+    for (int c = 0; c < 3; ++c) {
+      mn[c] = fmin(mn[c], part[6 * b + c]);
+      mx[c] = fmax(mx[c], part[6 * b + 3 + c]);
+    }
+  double E = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    bbox[c] = mn[c];
+    bbox[3 + c] = mx[c];
+    double e = dsub(mx[c], mn[c]);
+    if (e > E) E = e;
+  }
+  bbox[6] = E;
+  bbox[7] = (E > 0.0) ? __ddiv_rn(2097152.0, E) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Morton keys: 21 bits per axis, x highest (bit 3b+2 = x_b, 3b+1 = y_b, 3b = z_b)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+__device__ __forceinline__ uint64_t quantise(double x, double mn, double scale) {
+  double v = floor(dmul(dsub(x, mn), scale));
+  uint64_t k = (v > 0.0) ? (uint64_t)v : 0ull;
+  return k > 2097151ull ? 2097151ull : k;
+}
+
+__global__ void k_morton(const double* __restrict__ pos, int n, const double* __restrict__ bbox,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double scale = bbox[7];
+  uint64_t kx = quantise(pos[3 * (int64_t)i], bbox[0], scale);
+  uint64_t ky = quantise(pos[3 * (int64_t)i + 1], bbox[1], scale);
+  uint64_t kz = quantise(pos[3 * (int64_t)i + 2], bbox[2], scale);
+  keys[i] = (spread3(kx) << 2) | (spread3(ky) << 1) | spread3(kz);
+  idx[i] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// S2: stable LSD radix sort of (key, index), 8-bit digits
+// ---------------------------------------------------------------------------
+#define RS_NT 256
+#define RS_ITEMS 16
+#define RS_TILE (RS_NT * RS_ITEMS)
+#define RS_WARPS (RS_NT / 32)
+
+__global__ void __launch_bounds__(RS_NT) k_rs_hist(const uint64_t* __restrict__ keys, int n, int shift,
+                                                   uint32_t* __restrict__ counts, int ntiles) {
+  __shared__ uint32_t hw[RS_WARPS][256];
+  const int warp = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_NT) (&hw[0][0])[t] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    int64_t i = base + (int64_t)k * RS_NT + threadIdx.x;
+    if (i < n) atomicAdd(&hw[warp][(unsigned)(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += RS_NT) {
+    uint32_t s = 0;
+    for (int w = 0; w < RS_WARPS; ++w) s += hw[w][d];
+    counts[(int64_t)d * ntiles + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(RS_NT) k_rs_scatter(const uint64_t* __restrict__ kin,
+                                                      const uint32_t* __restrict__ vin,
+                                                      uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                      int n, int shift, const uint32_t* __restrict__ offs,
+                                                      int ntiles) {
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wc[RS_WARPS][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < 256; d += RS_NT) run[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_NT) (&wc[0][0])[t] = 0;
+    __syncthreads();
+    int64_t i = base + (int64_t)r * RS_NT + threadIdx.x;
+    bool valid = i < n;
+    uint64_t key = valid ? kin[i] : 0ull;
+    int d = valid ? (int)((key >> shift) & 255u) : 256;
+    unsigned peers = __match_any_sync(SFMM_FULL, d);
+    unsigned rank = __popc(peers & lanemask_lt());
+    bool leader = (__ffs(peers) - 1) == lane;
+    if (valid && leader) wc[warp][d] = __popc(peers);
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      uint32_t s = run[threadIdx.x];
+      for (int w = 0; w < RS_WARPS; ++w) {
+        uint32_t cnt = wc[w][threadIdx.x];
+        wc[w][threadIdx.x] = s;
+        s += cnt;
+      }
+      run[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t dst = wc[warp][d] + rank;
+      kout[dst] = key;
+      vout[dst] = vin[i];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gather the sorted particles (float64 SoA)
+// ---------------------------------------------------------------------------
+__global__ void k_gather(const double* __restrict__ pos, const double* __restrict__ mass,
+                         const double* __restrict__ h, const uint32_t* __restrict__ idx, int n,
+                         double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
+                         double* __restrict__ pm, double* __restrict__ ph, int* __restrict__ perm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t j = idx[i];
+  px[i] = pos[3 * j];
+  py[i] = pos[3 * j + 1];
+  pz[i] = pos[3 * j + 2];
+  pm[i] = mass[j];
+  ph[i] = h[j];
+  perm[i] = (int)j;
+}
+
+// ---------------------------------------------------------------------------
+// S3: binary radix tree over the augmented keys (key, sorted position)
+// (Karras 2012 construction; split at the highest differing bit)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int prefix_len(const uint64_t* __restrict__ keys, int n, int i, int64_t j) {
+  if (j < 0 || j >= n) return -1;
+  uint64_t a = keys[i], b = keys[j];
+  if (a != b) return __clzll((long long)(a ^ b));
+  return 64 + __clz(i ^ (int)j);
+}
+
+// Children encoding: >= 0 internal node index, < 0 leaf (particle) ~index.
+__global__ void k_radix_tree(const uint64_t* __restrict__ keys, int n, int* __restrict__ kl,
+                             int* __restrict__ kr, int* __restrict__ kf, int* __restrict__ kla,
+                             int* __restrict__ par_int, int* __restrict__ par_leaf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int d = (prefix_len(keys, n, i, i + 1) - prefix_len(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = prefix_len(keys, n, i, (int64_t)i - d);
+  int64_t lmax = 2;
+  while (prefix_len(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int64_t l = 0;
+  for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+    if (prefix_len(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  int64_t j = i + l * d;
+  int dnode = prefix_len(keys, n, i, j);
+  int64_t s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (prefix_len(keys, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int gamma = (int)(i + s * d + (d < 0 ? -1 : 0));
+  int first = (int)min((int64_t)i, j), last = (int)max((int64_t)i, j);
+  int left = (first == gamma) ? ~gamma : gamma;
+  int right = (last == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+  kl[i] = left;
+  kr[i] = right;
+  kf[i] = first;
+  kla[i] = last;
+  if (left >= 0) par_int[left] = i; else par_leaf[~left] = i;
+  if (right >= 0) par_int[right] = i; else par_leaf[~right] = i;
+  if (i == 0) par_int[0] = -1;
+}
+
+// Tree nodes of the collapsed tree: the root and every child of a node with
+// more than leaf_size particles.  chain[f] counts the tree nodes whose range
+// starts at f (a nested chain: each is the left child of the previous).
+__global__ void k_mark(int n, int leaf_size, const int* __restrict__ kf, const int* __restrict__ kla,
+                       const int* __restrict__ par_int, const int* __restrict__ par_leaf,
+                       uint32_t* __restrict__ chain) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n - 1) {
+    int p = par_int[i];
+    bool tree = (i == 0) || (kla[p] - kf[p] + 1 > leaf_size);
+    if (tree) atomicAdd(&chain[kf[i]], 1u);
+  }
+  if (i < n) {
+    int p = par_leaf[i];
+    bool tree = (kla[p] - kf[p] + 1 > leaf_size);
+    if (tree) atomicAdd(&chain[i], 1u);
+  }
+}
+
+// Pre-order index = (# tree nodes starting before) + (# tree ancestors
+// starting at the same particle).
+__global__ void k_preorder(int n, int leaf_size, const int* __restrict__ kf, const int* __restrict__ kla,
+                           const int* __restrict__ par_int, const int* __restrict__ par_leaf,
+                           const uint32_t* __restrict__ base, int* __restrict__ pre_int,
+                           int* __restrict__ pre_leaf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n - 1) {
+    int p = par_int[i];
+    bool tree = (i == 0) || (kla[p] - kf[p] + 1 > leaf_size);
+    int v = -1;
+    if (tree) {
+      int f = kf[i], r = 0, u = i;
+      while (u != 0) {
+        int q = par_int[u];
+        if (kf[q] != f) break;
+        ++r;
+        u = q;
+      }
+      v = (int)base[f] + r;
+    }
+    pre_int[i] = v;
+  }
+  if (i < n) {
+    int p = par_leaf[i];
+    bool tree = (kla[p] - kf[p] + 1 > leaf_size);
+    int v = -1;
+    if (tree) {
+      int r = 0, u = p;
+      while (u >= 0 && kf[u] == i) {
+        ++r;
+        u = (u == 0) ? -1 : par_int[u];
+      }
+      v = (int)base[i] + r;
+    }
+    pre_leaf[i] = v;
+  }
+}
+
+__global__ void k_fill_nodes(int n, int leaf_size, const int* __restrict__ kl, const int* __restrict__ kr,
+                             const int* __restrict__ kf, const int* __restrict__ kla,
+                             const int* __restrict__ par_int, const int* __restrict__ par_leaf,
+                             const int* __restrict__ pre_int, const int* __restrict__ pre_leaf,
+                             int* __restrict__ nfirst, int* __restrict__ ncount, int* __restrict__ nright,
+                             int* __restrict__ nparent, uint32_t* __restrict__ isleaf, int* __restrict__ status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n - 1) {
+    int v = pre_int[i];
+    if (v >= 0) {
+      int cnt = kla[i] - kf[i] + 1;
+      nfirst[v] = kf[i];
+      ncount[v] = cnt;
+      nparent[v] = (i == 0) ? -1 : pre_int[par_int[i]];
+      if (cnt <= leaf_size) {
+        nright[v] = -1;
+        isleaf[v] = 1u;
+      } else {
+        int L = kl[i], R = kr[i];
+        int pl = (L >= 0) ? pre_int[L] : pre_leaf[~L];
+        int pr = (R >= 0) ? pre_int[R] : pre_leaf[~R];
+        if (pl != v + 1) atomicOr(status, SFMM_ST_INTERNAL);
+        nright[v] = pr;
+        isleaf[v] = 0u;
+      }
+    }
+  }
+  if (i < n) {
+    int v = pre_leaf[i];
+    if (v >= 0) {
+      nfirst[v] = i;
+      ncount[v] = 1;
+      nright[v] = -1;
+      nparent[v] = pre_int[par_leaf[i]];
+      isleaf[v] = 1u;
+    }
+  }
+}
+
+// isleaf has been exclusive-scanned into leaf indices; record the leaves.
+__global__ void k_leaf_list(int nn, const int* __restrict__ nright, const uint32_t* __restrict__ lidx,
+                            int* __restrict__ leaf_node) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nn) return;
+  if (nright[v] < 0) leaf_node[lidx[v]] = v;
+}
+
+// ---------------------------------------------------------------------------
+// S4 geometry: leaf mass / centre of mass / h_max (one warp per leaf), then
+// bottom-up for internal nodes; particle -> leaf node map.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = dadd(v, __shfl_xor_sync(SFMM_FULL, v, o));
+  return v;
+}
+
+__global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
+                            const int* __restrict__ ncount, const double* __restrict__ px,
+                            const double* __restrict__ py, const double* __restrict__ pz,
+                            const double* __restrict__ pm, const double* __restrict__ ph,
+                            double* __restrict__ ncx, double* __restrict__ ncy, double* __restrict__ ncz,
+                            double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ pnode) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= nleaves) return;
+  int v = leaf_node[w];
+  int f = nfirst[v], cnt = ncount[v];
+  double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, hm = 0.0;
+  for (int k = lane; k < cnt; k += 32) {
+    int i = f + k;
+    double m = pm[i];
+    M = dadd(M, m);
+    sx = dadd(sx, dmul(m, px[i]));
+    sy = dadd(sy, dmul(m, py[i]));
+    sz = dadd(sz, dmul(m, pz[i]));
+    hm = fmax(hm, ph[i]);
+    pnode[i] = v;
+  }
+  M = warp_sum_d(M);
+  sx = warp_sum_d(sx);
+  sy = warp_sum_d(sy);
+  sz = warp_sum_d(sz);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hm = fmax(hm, __shfl_xor_sync(SFMM_FULL, hm, o));
+  if (lane == 0) {
+    nmass[v] = M;
+    ncx[v] = __ddiv_rn(sx, M);
+    ncy[v] = __ddiv_rn(sy, M);
+    ncz[v] = __ddiv_rn(sz, M);
+    nhmax[v] = hm;
+  }
+}
+
+// Bottom-up: the second child to finish computes its parent.
+__global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nparent,
+                         const int* __restrict__ nright, double* ncx, double* ncy, double* ncz, double* nmass,
+                         double* nhmax, int* flags) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nleaves) return;
+  int v = nparent[leaf_node[q]];
+  while (v >= 0) {
+    __threadfence();
+    if (atomicAdd(&flags[v], 1) == 0) return;
+    __threadfence();
+    int L = v + 1, R = nright[v];
+    double mL = __ldcg(&nmass[L]), mR = __ldcg(&nmass[R]);
+    double M = dadd(mL, mR);
+    ncx[v] = __ddiv_rn(dadd(dmul(mL, __ldcg(&ncx[L])), dmul(mR, __ldcg(&ncx[R]))), M);
+    ncy[v] = __ddiv_rn(dadd(dmul(mL, __ldcg(&ncy[L])), dmul(mR, __ldcg(&ncy[R]))), M);
+    ncz[v] = __ddiv_rn(dadd(dmul(mL, __ldcg(&ncz[L])), dmul(mR, __ldcg(&ncz[R]))), M);
+    nmass[v] = M;
+    nhmax[v] = fmax(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
+    v = nparent[v];
+  }
+}
+
+// Exact node sizes: every particle visits its ancestors; lanes at the same
+// node combine their squared distances, one atomic max per group.
+__global__ void k_size(int n, const double* __restrict__ px, const double* __restrict__ py,
+                       const double* __restrict__ pz, const int* __restrict__ pnode,
+                       const int* __restrict__ nparent, const double* __restrict__ ncx,
+                       const double* __restrict__ ncy, const double* __restrict__ ncz,
+                       unsigned long long* __restrict__ l2bits) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int v = (i < n) ? pnode[i] : -1;
+  double x = 0.0, y = 0.0, z = 0.0;
+  if (i < n) {
+    x = px[i];
+    y = py[i];
+    z = pz[i];
+  }
+  while (true) {
+    unsigned act = __ballot_sync(SFMM_FULL, v >= 0);
+    if (act == 0u) break;
+    if (v >= 0) {
+      double dx = dsub(x, ncx[v]), dy = dsub(y, ncy[v]), dz = dsub(z, ncz[v]);
+      double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+      unsigned long long bits = (unsigned long long)__double_as_longlong(d2);
+      unsigned grp = __match_any_sync(act, v);
+      unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+      unsigned mhi = __reduce_max_sync(grp, hi);
+      unsigned mlo = __reduce_max_sync(grp, hi == mhi ? lo : 0u);
+      if ((__ffs(grp) - 1) == lane) atomicMax(&l2bits[v], ((unsigned long long)mhi << 32) | mlo);
+      v = nparent[v];
+    }
+  }
+}
+
+// Final node records and float32 particle data.
+__global__ void k_finalize_nodes(int nn, const unsigned long long* __restrict__ l2bits,
+                                 const double* __restrict__ ncx, const double* __restrict__ ncy,
+                                 const double* __restrict__ ncz, const double* __restrict__ nhmax,
+                                 double* __restrict__ nsize, float4* __restrict__ geo_hi,
+                                 float4* __restrict__ geo_lo) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nn) return;
+  double l = __dsqrt_rn(__longlong_as_double((long long)l2bits[v]));
+  nsize[v] = l;
+  float xh, xl, yh, yl, zh, zl;
+  split_double(ncx[v], xh, xl);
+  split_double(ncy[v], yh, yl);
+  split_double(ncz[v], zh, zl);
+  geo_hi[v] = make_float4(xh, yh, zh, __double2float_rn(l));
+  geo_lo[v] = make_float4(xl, yl, zl, __double2float_rn(nhmax[v]));
+}
+
+__global__ void k_particles_f32(int n, const double* __restrict__ px, const double* __restrict__ py,
+                                const double* __restrict__ pz, const double* __restrict__ pm,
+                                const double* __restrict__ ph, const int* __restrict__ pnode,
+                                const double* __restrict__ ncx, const double* __restrict__ ncy,
+                                const double* __restrict__ ncz, float4* __restrict__ prel,
+                                float* __restrict__ ph32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int v = pnode[i];
+  prel[i] = make_float4(__double2float_rn(dsub(px[i], ncx[v])), __double2float_rn(dsub(py[i], ncy[v])),
+                        __double2float_rn(dsub(pz[i], ncz[v])), __double2float_rn(pm[i]));
+  ph32[i] = __double2float_rn(ph[i]);
+}
+
+__global__ void k_depth(int nn, const int* __restrict__ nparent, int* __restrict__ depth) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nn) return;
+  int d = 0, u = nparent[v];
+  while (u >= 0) {
+    ++d;
+    u = nparent[u];
+  }
+  depth[v] = d;
+}
+
+static inline unsigned nblk(int64_t n, int nt) { return (unsigned)((n + nt - 1) / nt); }
+
+int compute_depth(sfmm_ctx* c) {
+  int rc = c->ndepth.ensure(sizeof(int) * (size_t)c->nnodes);
+  if (rc) return rc;
+  k_depth<<<nblk(c->nnodes, 256), 256, 0, c->stream>>>(c->nnodes, c->nparent.as<int>(), c->ndepth.as<int>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
+  return SFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host orchestration of the build
+// ---------------------------------------------------------------------------
+int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double* h) {
+  const int n = (int)c->n;
+  cudaStream_t st = c->stream;
+  int rc;
+  const size_t nn_max = (size_t)2 * n;
+#define ENS(buf, bytes) \
+  if ((rc = c->buf.ensure(bytes)) != SFMM_OK) return rc;
+  ENS(keys_a, sizeof(uint64_t) * n);
+  ENS(keys_b, sizeof(uint64_t) * n);
+  ENS(idx_a, sizeof(uint32_t) * n);
+  ENS(idx_b, sizeof(uint32_t) * n);
+  ENS(misc, 256);
+  ENS(px, sizeof(double) * n);
+  ENS(py, sizeof(double) * n);
+  ENS(pz, sizeof(double) * n);
+  ENS(pm, sizeof(double) * n);
+  ENS(ph, sizeof(double) * n);
+  ENS(perm, sizeof(int) * n);
+  ENS(pnode, sizeof(int) * n);
+  ENS(prel, sizeof(float4) * n);
+  ENS(ph32, sizeof(float) * n);
+  ENS(k_left, sizeof(int) * n);
+  ENS(k_right, sizeof(int) * n);
+  ENS(k_first, sizeof(int) * n);
+  ENS(k_last, sizeof(int) * n);
+  ENS(par_int, sizeof(int) * n);
+  ENS(par_leaf, sizeof(int) * n);
+  ENS(chain, sizeof(uint32_t) * (n + 1));
+  ENS(pre_int, sizeof(int) * n);
+  ENS(pre_leaf, sizeof(int) * n);
+  ENS(nfirst, sizeof(int) * nn_max);
+  ENS(ncount, sizeof(int) * nn_max);
+  ENS(nright, sizeof(int) * nn_max);
+  ENS(nparent, sizeof(int) * nn_max);
+  ENS(isleaf, sizeof(uint32_t) * (nn_max + 1));
+  ENS(ncx, sizeof(double) * nn_max);
+  ENS(ncy, sizeof(double) * nn_max);
+  ENS(ncz, sizeof(double) * nn_max);
+  ENS(nsize, sizeof(double) * nn_max);
+  ENS(nhmax, sizeof(double) * nn_max);
+  ENS(nmass, sizeof(double) * nn_max);
+  ENS(l2bits, sizeof(unsigned long long) * nn_max);
+  ENS(flags, sizeof(int) * nn_max);
+  ENS(geo_hi, sizeof(float4) * nn_max);
+  ENS(geo_lo, sizeof(float4) * nn_max);
+  ENS(leaf_node, sizeof(int) * nn_max);
+  const int nbb = 2 * num_sms(c->device);
+  ENS(bbox_part, sizeof(double) * 6 * nbb);
+#undef ENS
+  double* bbox = c->misc.as<double>();           // 8 doubles
+  uint32_t* totals = (uint32_t*)(bbox + 8);      // scan totals
+
+  // S1: bounding box, validation, Morton keys
+  k_bbox_partial<<<nbb, BB_NT, 0, st>>>(pos, mass, h, n, c->bbox_part.as<double>(), c->d_status);
+  ++c->nlaunch;
+  k_bbox_final<<<1, 32, 0, st>>>(c->bbox_part.as<double>(), nbb, bbox);
+  ++c->nlaunch;
+  k_morton<<<nblk(n, 256), 256, 0, st>>>(pos, n, bbox, c->keys_a.as<uint64_t>(), c->idx_a.as<uint32_t>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
+
+  // S2: radix sort, 8 passes of 8 bits (the top pass holds 7 key bits)
+  const int ntiles = (n + RS_TILE - 1) / RS_TILE;
+  if ((rc = c->sort_counts.ensure(sizeof(uint32_t) * 256 * (size_t)ntiles)) != SFMM_OK) return rc;
+  uint64_t *ka = c->keys_a.as<uint64_t>(), *kb = c->keys_b.as<uint64_t>();
+  uint32_t *va = c->idx_a.as<uint32_t>(), *vb = c->idx_b.as<uint32_t>();
+  for (int shift = 0; shift < 64; shift += 8) {
+    k_rs_hist<<<ntiles, RS_NT, 0, st>>>(ka, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
+    if ((rc = exclusive_scan_u32(c, c->sort_counts.as<uint32_t>(), (int64_t)256 * ntiles, nullptr))) return rc;
+    k_rs_scatter<<<ntiles, RS_NT, 0, st>>>(ka, va, kb, vb, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  // after 8 passes the sorted data is back in keys_a / idx_a
+  k_gather<<<nblk(n, 256), 256, 0, st>>>(pos, mass, h, va, n, c->px.as<double>(), c->py.as<double>(),
+                                         c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(),
+                                         c->perm.as<int>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
+
+  // S3: radix tree, collapse, pre-order
+  int nnodes = 1;
+  if (n == 1) {
+    int one = 1, zero = 0, minus = -1;
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->nfirst.as<int>(), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->ncount.as<int>(), &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->nright.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->nparent.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->leaf_node.as<int>(), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    c->nnodes = 1;
+    c->nleaves = 1;
+  } else {
+    k_radix_tree<<<nblk(n - 1, 256), 256, 0, st>>>(ka, n, c->k_left.as<int>(), c->k_right.as<int>(),
+                                                     c->k_first.as<int>(), c->k_last.as<int>(),
+                                                     c->par_int.as<int>(), c->par_leaf.as<int>());
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaMemsetAsync(c->chain.p, 0, sizeof(uint32_t) * (n + 1), st));
+    k_mark<<<nblk(n, 256), 256, 0, st>>>(n, c->leaf_size, c->k_first.as<int>(), c->k_last.as<int>(),
+                                         c->par_int.as<int>(), c->par_leaf.as<int>(), c->chain.as<uint32_t>());
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
+    if ((rc = exclusive_scan_u32(c, c->chain.as<uint32_t>(), n, totals))) return rc;
+    k_preorder<<<nblk(n, 256), 256, 0, st>>>(n, c->leaf_size, c->k_first.as<int>(), c->k_last.as<int>(),
+                                             c->par_int.as<int>(), c->par_leaf.as<int>(),
+                                             c->chain.as<uint32_t>(), c->pre_int.as<int>(), c->pre_leaf.as<int>());
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
+    uint32_t h_tot = 0;
+    SFMM_CUDA_TRY(cudaMemcpyAsync(&h_tot, totals, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    SFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    nnodes = (int)h_tot;
+    c->nnodes = nnodes;
+    k_fill_nodes<<<nblk(n, 256), 256, 0, st>>>(n, c->leaf_size, c->k_left.as<int>(), c->k_right.as<int>(),
+                                               c->k_first.as<int>(), c->k_last.as<int>(), c->par_int.as<int>(),
+                                               c->par_leaf.as<int>(), c->pre_int.as<int>(), c->pre_leaf.as<int>(),
+                                               c->nfirst.as<int>(), c->ncount.as<int>(), c->nright.as<int>(),
+                                               c->nparent.as<int>(), c->isleaf.as<uint32_t>(), c->d_status);
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
+    if ((rc = exclusive_scan_u32(c, c->isleaf.as<uint32_t>(), nnodes, totals + 1))) return rc;
+    k_leaf_list<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->nright.as<int>(), c->isleaf.as<uint32_t>(),
+                                                   c->leaf_node.as<int>());
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
+    c->nleaves = (nnodes + 1) / 2;  // full binary tree
+  }
+  const int nl = c->nleaves;
+
+  // S4 geometry
+  k_leaf_geom<<<nblk((int64_t)nl * 32, 256), 256, 0, st>>>(
+      nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
+      c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
+      c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaMemsetAsync(c->flags.p, 0, sizeof(int) * nnodes, st));
+  k_upward<<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
+                                          c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
+                                          c->nmass.as<double>(), c->nhmax.as<double>(), c->flags.as<int>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaMemsetAsync(c->l2bits.p, 0, sizeof(unsigned long long) * nnodes, st));
+  k_size<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
+                                       c->pnode.as<int>(), c->nparent.as<int>(), c->ncx.as<double>(),
+                                       c->ncy.as<double>(), c->ncz.as<double>(),
+                                       c->l2bits.as<unsigned long long>());
+  ++c->nlaunch;
+  k_finalize_nodes<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->l2bits.as<unsigned long long>(), c->ncx.as<double>(),
+                                                      c->ncy.as<double>(), c->ncz.as<double>(), c->nhmax.as<double>(),
+                                                      c->nsize.as<double>(), c->geo_hi.as<float4>(),
+                                                      c->geo_lo.as<float4>());
+  ++c->nlaunch;
+  k_particles_f32<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
+                                                c->pm.as<double>(), c->ph.as<double>(), c->pnode.as<int>(),
+                                                c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
+                                                c->prel.as<float4>(), c->ph32.as<float>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
+  if (c->keys_a.p != (void*)ka) {
+    // keep the sorted keys in keys_a for export (even number of passes: no-op)
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->keys_a.p, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
+  }
+  return SFMM_OK;
+}
+
+}  // namespace sfmm

@@ -1,0 +1,30 @@
+"""Shared helpers of the GPU parity tests: tolerances and error metrics."""
+import numpy as np
+
+TOL_FP64 = 1e-10      # per particle, relative (acceleration and potential)
+TOL_FP32_RMS = 1e-5   # rms relative acceleration error of the FP32 form
+TOL_MOM_FP64 = 1e-14  # |sum m a| / sum |m a|
+TOL_MOM_FP32 = 1e-6
+
+
+def acc_rel(acc, ref):
+    """|da| / max(|a|, 1e-3 rms |a|) per particle (the floor keeps particles
+    with a ~ 0 near the centre of a symmetric system from dominating)."""
+    an = np.linalg.norm(ref, axis=1)
+    floor = 1e-3 * np.sqrt((an**2).mean())
+    return np.linalg.norm(acc - ref, axis=1) / np.maximum(an, floor)
+
+
+def pot_rel(pot, ref):
+    return np.abs(pot - ref) / np.abs(ref)
+
+
+def momentum_residual(m, acc):
+    ma = m[:, None] * acc
+    return np.linalg.norm(ma.sum(0)) / np.abs(ma).sum()
+
+
+def solver(prec, **opts):
+    from paper_2602_05804_gb300 import sfmm
+
+    return sfmm.Solver(0, prec, **opts)
