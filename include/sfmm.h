@@ -182,6 +182,38 @@ int sfmm_moments_export(sfmm_ctx* ctx, int order, double* Q, int32_t* mi);
 int sfmm_lists(sfmm_ctx* ctx, double theta, int64_t* m2l_off, int32_t* m2l_level, int32_t* m2l_src,
                int64_t cap_m2l, int64_t* p2p_off, int32_t* p2p_src, int64_t cap_p2p);
 
+/* Largest n accepted by sfmm_reduce_noalloc. */
+#define SFMM_NOALLOC_MAX_N 67108864
+
+/* Momentum and energy sums of a particle set WITHOUT ANY DEVICE ALLOCATION:
+ * out[0..2] = sum_i m_i a_i, out[3] = sum_i sum_d |m_i a_i,d|,
+ * out[4] = 1/2 sum_i m_i Phi_i (0 when pot is NULL) -- the same sums that
+ * sfmm_get_stats reports after sfmm_gravity, here over caller arrays.  The
+ * paper has no counterpart: this is a service for callers that cannot call
+ * cudaMalloc, such as code that must draw all device memory from its own
+ * pre-reserved pool or must not change the device's memory footprint once it
+ * is running.  No context is needed and nothing is allocated, freed or taken
+ * from a library allocator.
+ *   n     number of particles, 1 <= n <= SFMM_NOALLOC_MAX_N (larger n is
+ *         rejected with SFMM_EINVAL);
+ *   mass  device, n float64;  acc device, n x 3 float64;  pot device, n
+ *         float64 or NULL;  out device, 5 float64, written;
+ *   stream  cudaStream_t to run on (NULL: the default stream), on the
+ *         current device.
+ * Scratch: per-tile partial sums (one per 4096 particles) in a fixed 640 KB
+ * array of device memory inside this library, which every GPU that loads the
+ * library holds until the process exits.  Every call shares that array, which
+ * keeps the last call's contents; each call writes every partial it reads, so
+ * nothing needs clearing.  Each GPU has its own copy of the array; calls that
+ * overlap on the same GPU (for example on two streams) race on the partials,
+ * so serialise them.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Unlike the other entry points this call
+ * does not synchronise: out is ready when the stream reaches it.
+ * Errors: EINVAL (n out of range, NULL pointer), ECUDA. */
+int sfmm_reduce_noalloc(int64_t n, const double* mass, const double* acc, const double* pot, double* out,
+                        void* stream);
+
 /* Message describing an error code. */
 const char* sfmm_strerror(int code);
 

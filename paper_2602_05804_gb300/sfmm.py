@@ -22,7 +22,8 @@ SFMM_FP64, SFMM_FP32 = 0, 1
 # every symbol include/sfmm.h declares
 EXPORTS = ("sfmm_create", "sfmm_destroy", "sfmm_set_stream", "sfmm_set_option", "sfmm_build", "sfmm_gravity",
            "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
-           "sfmm_lists", "sfmm_strerror", "sfmm_last_error", "sfmm_version")
+           "sfmm_lists", "sfmm_strerror", "sfmm_last_error", "sfmm_version", "sfmm_reduce_noalloc")
+SFMM_NOALLOC_MAX_N = 67108864
 
 
 class sfmm_stats(ctypes.Structure):
@@ -76,6 +77,8 @@ def load(path: str = LIB_PATH):
     lib.sfmm_last_error.argtypes = [P]
     lib.sfmm_last_error.restype = ctypes.c_char_p
     lib.sfmm_version.restype = ctypes.c_char_p
+    lib.sfmm_reduce_noalloc.argtypes = [i64, P, P, P, P, P]
+    lib.sfmm_reduce_noalloc.restype = i32
     for name in ("sfmm_create", "sfmm_set_stream", "sfmm_set_option", "sfmm_build", "sfmm_gravity",
                  "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
                  "sfmm_lists"):
@@ -177,6 +180,13 @@ def sfmm_lists(ctx, theta):
     _check(load().sfmm_lists(ctx, float(theta), _ptr(mo), _ptr(lv), _ptr(src), int(mo[-1]), _ptr(po), _ptr(ps),
                              int(po[-1])), ctx)
     return mo, lv[:mo[-1]], src[:mo[-1]], po, ps[:po[-1]]
+
+
+def sfmm_reduce_noalloc(n, mass, acc, pot, out, stream=None):
+    """Momentum/energy sums over device arrays without any device allocation
+    (see include/sfmm.h); ``out`` is a device buffer of 5 float64."""
+    _check(load().sfmm_reduce_noalloc(int(n), _ptr(mass), _ptr(acc), _ptr(pot), _ptr(out),
+                                      ctypes.c_void_p(stream) if stream else None))
 
 
 def sfmm_strerror(code: int) -> str:
