@@ -245,8 +245,8 @@ def run_gpu(args):
     pot = torch.empty(w["n"], dtype=torch.float64, device=dev)
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    s32 = sfmm.Solver(local, "fp32", profile=1)
-    s64 = sfmm.Solver(local, "fp64", profile=1)
+    s32 = sfmm.Solver(local, "fp32", profile=1, walk=args.walk)
+    s64 = sfmm.Solver(local, "fp64", profile=1, walk=args.walk)
 
     def barrier():
         if dist is not None:
@@ -376,6 +376,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="particle count (default: the workload's 10^6)")
+    ap.add_argument("--walk", type=int, default=0, choices=[0, 1],
+                    help="headline walk: 0 per-leaf replay (Algorithm 1), 1 per-node shared pairs")
     ap.add_argument("--only", default="all", choices=["all", "fp32"],
                     help="fp32: time the headline FP32 step only (for profiler launch lists)")
     args = ap.parse_args()

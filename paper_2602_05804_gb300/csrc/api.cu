@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -160,11 +161,12 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->idx_a, &c->idx_b, &c->sort_counts, &c->scan_tmp, &c->bbox_part, &c->k_left,
                     &c->k_right, &c->k_first, &c->k_last, &c->par_int, &c->par_leaf, &c->chain,
                     &c->pre_int, &c->pre_leaf, &c->misc, &c->px, &c->py, &c->pz, &c->pm, &c->ph,
-                    &c->perm, &c->pnode, &c->prel, &c->ph32, &c->nfirst, &c->ncount, &c->nright,
+                    &c->perm, &c->pnode, &c->prel, &c->ph32, &c->phh, &c->nfirst, &c->ncount, &c->nright,
                     &c->nparent, &c->ndepth, &c->ncx, &c->ncy, &c->ncz, &c->nsize, &c->nhmax, &c->nmass,
                     &c->l2bits, &c->flags, &c->geo_hi, &c->geo_lo, &c->leaf_node, &c->isleaf, &c->Qd,
                     &c->Qf, &c->ring, &c->far, &c->arena, &c->p2p_off, &c->p2p_cnt, &c->counters,
-                    &c->red_part, &c->dump};
+                    &c->red_part, &c->dump, &c->nlu, &c->level_nodes, &c->level_off, &c->level_cur,
+                    &c->cf_arena, &c->cf_off, &c->cf_cnt, &c->Tnode};
   for (DevBuf* b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -207,6 +209,9 @@ int sfmm_set_option(sfmm_ctx* c, const char* key, double v) {
   } else if (!strcmp(key, "list_capacity")) {
     if (v < 0) return set_error(c, SFMM_EINVAL, "list_capacity must be >= 0");
     c->list_capacity = (int64_t)v;
+  } else if (!strcmp(key, "walk")) {
+    if (v != 0.0 && v != 1.0) return set_error(c, SFMM_EINVAL, "walk: 0 (per-leaf replay) or 1 (per-node shared pairs)");
+    c->walk_mode = (int)v;
   } else if (!strcmp(key, "profile")) {
     c->profile = (v != 0.0);
   } else {
@@ -228,12 +233,27 @@ int sfmm_build(sfmm_ctx* c, int64_t n, const double* pos, const double* mass, co
   if (c->profile) cudaEventRecord(c->ev[0], c->stream);
   int rc = build_tree(c, pos, mass, h);
   if (rc) return set_error(c, rc, "tree build failed");
+  if ((rc = build_levels(c))) return set_error(c, rc, "level lists failed");
+  // level offsets to the host (the tree is at most 96 levels deep: keys and
+  // sorted positions give 95 distinguishing bits)
+  const int ncopy = (int)std::min<int64_t>((int64_t)c->nnodes + 1, 130);
+  c->h_level_off.assign(ncopy, 0);
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_off.data(), c->level_off.p, sizeof(int) * ncopy, cudaMemcpyDeviceToHost,
+                                c->stream));
   if (c->profile) cudaEventRecord(c->ev[1], c->stream);
   int bits = 0;
   if ((rc = sync_status(c, &bits))) return rc;
   if (bits & (SFMM_ST_NONFINITE | SFMM_ST_NONPOSITIVE))
     return set_error(c, SFMM_ENONFINITE, "non-finite position/mass/h or non-positive mass/h");
   if (bits) return set_error(c, SFMM_ECUDA, "internal consistency check of the tree failed");
+  c->max_depth = -1;
+  for (int d = 0; d + 1 < (int)c->h_level_off.size(); ++d)
+    if (c->h_level_off[d + 1] >= c->nnodes) {
+      c->max_depth = d;
+      break;
+    }
+  if (c->max_depth < 0) return set_error(c, SFMM_ESTACK, "tree deeper than 128 levels");
+  c->h_level_off.resize(c->max_depth + 2);
   c->built = true;
   c->stats = sfmm_stats{};
   c->stats.n = n;
@@ -257,13 +277,13 @@ int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot)
     if ((rc = compute_moments(c, order))) return set_error(c, rc, "moment pass failed");
   }
   if (c->profile) cudaEventRecord(c->ev[3], st);
-  if ((rc = run_walk(c, theta, order, false, 0, 0))) return rc;
+  if ((rc = (c->walk_mode == 1) ? run_walk_shared(c, theta, order) : run_walk(c, theta, order, false, 0, 0))) return rc;
   if (c->profile) cudaEventRecord(c->ev[4], st);
   if ((rc = run_p2p(c, acc, pot))) return set_error(c, rc, "near-field pass failed");
   if (c->profile) cudaEventRecord(c->ev[5], st);
-  if ((rc = run_reduce(c, acc, pot))) return set_error(c, rc, "reduction failed");
+  double* red = nullptr;
+  if ((rc = run_reduce(c, &red))) return set_error(c, rc, "reduction failed");
   if (c->profile) cudaEventRecord(c->ev[6], st);
-  double* red = c->red_part.as<double>() + 5 * (size_t)c->nleaves;
   cudaError_t e = cudaMemcpyAsync(c->h_scalars + 16, red, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return set_error(c, SFMM_ECUDA, cudaGetErrorString(e));
   int bits = 0;

@@ -16,7 +16,7 @@ namespace sfmm {
 
 #define P2P_WARPS 8
 #define P2P_NT (P2P_WARPS * 32)
-#define P2P_SB 128
+#define P2P_SB 64
 
 struct P2PArgs {
   int nleaves;
@@ -38,6 +38,9 @@ struct P2PArgs {
   const int* perm;
   const float4* far32;
   const double* far64;
+  const double* ncx;
+  const double* ncy;
+  const double* ncz;
   double G;
   int self_pot;
   int* leaf_counter;
@@ -65,15 +68,62 @@ __device__ __forceinline__ void m4_kernel(R q, R hinv, R rinv, R& g, R& phi) {
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
+template <typename R> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4; };
+
+// Far pair (no softening): a -= m r^-3 d, phi -= m / r.
+template <typename R>
+__device__ __forceinline__ void pair_far(R xi, R yi, R zi, const typename Vec4<R>::T& s, R& ax, R& ay, R& az,
+                                         R& pt) {
+  const R dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
+  const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+  const R ri = rsq(r2);
+  const R mr = s.w * ri;
+  const R mr3 = mr * (ri * ri);
+  ax = fma(-mr3, dx, ax);
+  ay = fma(-mr3, dy, ay);
+  az = fma(-mr3, dz, az);
+  pt -= mr;
+}
+
+// Softened pair (both particles' kernels, mean): returns the factor g-bar
+// multiplying -m d and the potential factor phi-bar multiplying m.
+template <typename R>
+__device__ __forceinline__ void pair_soft(R r2, R hinvi, R hinvj, R& gbar, R& pbar) {
+  const R ri = (r2 > R(0)) ? rsq(r2) : R(0);
+  const R r = r2 * ri;
+  R gi, pi, gj, pj;
+  m4_kernel<R>(r * hinvi, hinvi, ri, gi, pi);
+  m4_kernel<R>(r * hinvj, hinvj, ri, gj, pj);
+  gbar = R(0.5) * (gi + gj);
+  pbar = R(0.5) * (pi + pj);
+}
+
+// Sources are staged per warp, split once per source into those that may lie
+// inside the kernel of some target of the leaf (|x_j - s_L| < l_L +
+// 2 max(h_max,L, h_j), with a small safety factor) and those that cannot; the
+// latter take the unsoftened branch-free loop.
+template <bool F32> __host__ __device__ constexpr int p2p_warps() { return F32 ? P2P_WARPS : P2P_WARPS / 2; }
+
 template <bool F32>
 __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
   using R = typename std::conditional<F32, float, double>::type;
-  __shared__ R s_x[P2P_WARPS][P2P_SB], s_y[P2P_WARPS][P2P_SB], s_z[P2P_WARPS][P2P_SB];
-  __shared__ R s_m[P2P_WARPS][P2P_SB], s_h2[P2P_WARPS][P2P_SB], s_hi[P2P_WARPS][P2P_SB];
-  __shared__ int s_idx[P2P_WARPS][P2P_SB];
-  __shared__ R s_red[P2P_WARPS][4][32];
+  using V = typename Vec4<R>::T;
+  constexpr int NW = p2p_warps<F32>();           // warps per block (48 KB static limit)
+  constexpr int SB = P2P_SB;                     // staged sources per warp (>= 64, a full leaf)
+  __shared__ V s_far[NW][SB];
+  __shared__ V s_near[NW][SB];
+  __shared__ R s_nhinv[NW][SB];
+  __shared__ R s_nh2[NW][SB];                   // (2h)^2 of the candidate
+  __shared__ int s_nidx[NW][SB];
+  __shared__ R s_red[NW][4][32];
+  __shared__ V s_tgt[NW][64];            // targets: x, y, z, 1/h
+  __shared__ R s_acc[NW][64][4];                // softened part per target
+  __shared__ int s_q[NW][64];            // queued pairs: target << 16 | candidate
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt();
   while (true) {
     int leaf = 0;
     if (lane == 0) leaf = atomicAdd(a.leaf_counter, 1);
@@ -82,51 +132,71 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
     const int L = a.leaf_node[leaf];
     const int fL = a.nfirst[L], nL = a.ncount[L];
     const float4 hiL = a.geo_hi[L], loL = a.geo_lo[L];
+    // target leaf radius and largest smoothing length, with a safety factor
+    // covering the float32 rounding of the relative coordinates
+    const R lL = (R)hiL.w * R(1.0001), hL = (R)loL.w * R(1.0001);
+    const double cLx = F32 ? 0.0 : a.ncx[L], cLy = F32 ? 0.0 : a.ncy[L], cLz = F32 ? 0.0 : a.ncz[L];
     // lane -> (target slot, phase)
     const int nph = (nL <= 16) ? (32 / nL) : 1;
     const int ntl = (nL <= 32) ? nL : 32;
     const int ph = lane / ntl;
     const bool lane_on = ph < nph;
     const int t0 = lane % ntl;
-    const int t1 = t0 + 32;  // second target slot (leaves of 33..64)
+    const int t1 = t0 + 32;
     const bool on0 = lane_on && t0 < nL;
     const bool on1 = lane_on && nL > 32 && t1 < nL;
-    R xi0 = R(0), yi0 = R(0), zi0 = R(0), h2i0 = R(0), hinvi0 = R(0);
-    R xi1 = R(0), yi1 = R(0), zi1 = R(0), h2i1 = R(0), hinvi1 = R(0);
-    auto load_t = [&](int t, R& x, R& y, R& z, R& h2, R& hinv) {
+    R xi0 = R(0), yi0 = R(0), zi0 = R(0), hinvi0 = R(0);
+    R xi1 = R(0), yi1 = R(0), zi1 = R(0), hinvi1 = R(0);
+    if (on0) {
+      const int i = fL + t0;
+      if constexpr (F32) {
+        const float4 p = a.prel[i];
+        xi0 = p.x; yi0 = p.y; zi0 = p.z;
+        hinvi0 = 1.0f / a.ph32[i];
+      } else {
+        xi0 = a.px[i]; yi0 = a.py[i]; zi0 = a.pz[i];
+        hinvi0 = 1.0 / a.ph[i];
+      }
+    }
+    if (on1) {
+      const int i = fL + t1;
+      if constexpr (F32) {
+        const float4 p = a.prel[i];
+        xi1 = p.x; yi1 = p.y; zi1 = p.z;
+        hinvi1 = 1.0f / a.ph32[i];
+      } else {
+        xi1 = a.px[i]; yi1 = a.py[i]; zi1 = a.pz[i];
+        hinvi1 = 1.0 / a.ph[i];
+      }
+    }
+    // target table for the queued softened pairs
+    for (int t = lane; t < nL; t += 32) {
       const int i = fL + t;
       if constexpr (F32) {
         const float4 p = a.prel[i];
-        x = p.x;
-        y = p.y;
-        z = p.z;
-        const float h = a.ph32[i];
-        h2 = 4.0f * h * h;
-        hinv = 1.0f / h;
+        s_tgt[warp][t] = make_float4(p.x, p.y, p.z, 1.0f / a.ph32[i]);
       } else {
-        x = a.px[i];
-        y = a.py[i];
-        z = a.pz[i];
-        const double h = a.ph[i];
-        h2 = 4.0 * h * h;
-        hinv = 1.0 / h;
+        s_tgt[warp][t] = make_double4(a.px[i], a.py[i], a.pz[i], 1.0 / a.ph[i]);
       }
-    };
-    if (on0) load_t(t0, xi0, yi0, zi0, h2i0, hinvi0);
-    if (on1) load_t(t1, xi1, yi1, zi1, h2i1, hinvi1);
+      s_acc[warp][t][0] = s_acc[warp][t][1] = s_acc[warp][t][2] = s_acc[warp][t][3] = R(0);
+    }
+    __syncwarp();
+    const R h2i0 = (hinvi0 > R(0)) ? R(4) / (hinvi0 * hinvi0) : R(0);
+    const R h2i1 = (hinvi1 > R(0)) ? R(4) / (hinvi1 * hinvi1) : R(0);
+    int nqp = 0;  // queued softened pairs
+    // unsoftened accumulators per slot
     R ax0 = R(0), ay0 = R(0), az0 = R(0), pt0 = R(0);
     R ax1 = R(0), ay1 = R(0), az1 = R(0), pt1 = R(0);
 
     const long long off = a.p2p_off[leaf];
     const int cnt = a.p2p_cnt[leaf];
-    int nb = 0;
-    int e = 0;
+    int nfar = 0, nnear = 0, e = 0;
     while (true) {
-      // stage whole source leaves while they fit
+      // stage whole source leaves while both buffers have room
       while (e < cnt) {
         const int S = a.arena[off + e];
         const int fS = a.nfirst[S], nS = a.ncount[S];
-        if (nb + nS > P2P_SB) break;
+        if (nfar + nS > SB || nnear + nS > SB) break;
         R ox = R(0), oy = R(0), oz = R(0);
         if constexpr (F32) {
           const float4 hS = a.geo_hi[S], lS = a.geo_lo[S];
@@ -134,99 +204,164 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
           oy = df_diff(hS.y, lS.y, hiL.y, loL.y);
           oz = df_diff(hS.z, lS.z, hiL.z, loL.z);
         }
-        for (int j = lane; j < nS; j += 32) {
-          const int i = fS + j;
-          R x, y, z, m, h;
-          if constexpr (F32) {
-            const float4 p = a.prel[i];
-            x = p.x + ox;
-            y = p.y + oy;
-            z = p.z + oz;
-            m = p.w;
-            h = a.ph32[i];
-          } else {
-            x = a.px[i];
-            y = a.py[i];
-            z = a.pz[i];
-            m = a.pm[i];
-            h = a.ph[i];
+        for (int j0 = 0; j0 < nS; j0 += 32) {
+          const int j = j0 + lane;
+          const bool valid = j < nS;
+          V v = {R(0), R(0), R(0), R(0)};
+          R h = R(1);
+          if (valid) {
+            const int i = fS + j;
+            if constexpr (F32) {
+              const float4 p = a.prel[i];
+              v = make_float4(p.x + ox, p.y + oy, p.z + oz, p.w);
+              h = a.ph32[i];
+            } else {
+              v = make_double4(a.px[i], a.py[i], a.pz[i], a.pm[i]);
+              h = a.ph[i];
+            }
           }
-          s_x[warp][nb + j] = x;
-          s_y[warp][nb + j] = y;
-          s_z[warp][nb + j] = z;
-          s_m[warp][nb + j] = m;
-          s_h2[warp][nb + j] = R(4) * h * h;
-          s_hi[warp][nb + j] = R(1) / h;
-          s_idx[warp][nb + j] = i;
+          // distance to the target leaf's centre
+          R rx = v.x, ry = v.y, rz = v.z;
+          if constexpr (!F32) {
+            rx -= cLx;
+            ry -= cLy;
+            rz -= cLz;
+          }
+          const R reach = lL + R(2) * fmax(hL, h * R(1.0001));
+          const bool near = valid && (fma(rx, rx, fma(ry, ry, rz * rz)) < reach * reach);
+          const unsigned bn = __ballot_sync(SFMM_FULL, near), bf = __ballot_sync(SFMM_FULL, valid && !near);
+          if (near) {
+            const int q = nnear + __popc(bn & lt);
+            s_near[warp][q] = v;
+            s_nhinv[warp][q] = R(1) / h;
+            s_nh2[warp][q] = R(4) * h * h;
+            s_nidx[warp][q] = fS + j;
+          } else if (valid) {
+            s_far[warp][nfar + __popc(bf & lt)] = v;
+          }
+          nnear += __popc(bn);
+          nfar += __popc(bf);
         }
-        nb += nS;
         ++e;
       }
-      if (nb == 0) break;
+      if (nfar == 0 && nnear == 0) break;
       __syncwarp();
-      const int iters = (nb + nph - 1) / nph;
-      for (int it = 0; it < iters; ++it) {
-        const int j = it * nph + ph;
-        const bool vj = lane_on && j < nb;
-        const int jj = vj ? j : 0;
-        const R xj = s_x[warp][jj], yj = s_y[warp][jj], zj = s_z[warp][jj];
-        const R mj = vj ? s_m[warp][jj] : R(0);
-        const R h2j = s_h2[warp][jj], hinvj = s_hi[warp][jj];
-        const int idxj = s_idx[warp][jj];
-        // target slot 0
-        {
-          const R dx = xi0 - xj, dy = yi0 - yj, dz = zi0 - zj;
-          const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-          const bool self = !on0 || !vj || (idxj == fL + t0);
-          const R rinv = (r2 > R(0)) ? rsq(r2) : R(0);
-          const bool near = !self && r2 < fmax(h2i0, h2j);
-          R g, phi;
-          if (__any_sync(SFMM_FULL, near)) {
-            const R r = r2 * rinv;
-            R gi, pi, gj, pj;
-            m4_kernel<R>(r * hinvi0, hinvi0, rinv, gi, pi);
-            m4_kernel<R>(r * hinvj, hinvj, rinv, gj, pj);
-            g = R(0.5) * (gi + gj);
-            phi = R(0.5) * (pi + pj);
-          } else {
-            g = rinv * rinv * rinv;
-            phi = -rinv;
+      // unsoftened sources
+      if (lane_on) {
+        int j = ph;
+        for (; j + nph < nfar; j += 2 * nph) {
+          const V s0 = s_far[warp][j], s1 = s_far[warp][j + nph];
+          pair_far<R>(xi0, yi0, zi0, s0, ax0, ay0, az0, pt0);
+          pair_far<R>(xi0, yi0, zi0, s1, ax0, ay0, az0, pt0);
+          if (nL > 32) {
+            pair_far<R>(xi1, yi1, zi1, s0, ax1, ay1, az1, pt1);
+            pair_far<R>(xi1, yi1, zi1, s1, ax1, ay1, az1, pt1);
           }
-          const R mg = self ? R(0) : mj * g;
-          ax0 = fma(-mg, dx, ax0);
-          ay0 = fma(-mg, dy, ay0);
-          az0 = fma(-mg, dz, az0);
-          pt0 = fma(self ? R(0) : mj, phi, pt0);
         }
-        if (nL > 32) {
-          const R dx = xi1 - xj, dy = yi1 - yj, dz = zi1 - zj;
-          const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-          const bool self = !on1 || !vj || (idxj == fL + t1);
-          const R rinv = (r2 > R(0)) ? rsq(r2) : R(0);
-          const bool near = !self && r2 < fmax(h2i1, h2j);
-          R g, phi;
-          if (__any_sync(SFMM_FULL, near)) {
-            const R r = r2 * rinv;
-            R gi, pi, gj, pj;
-            m4_kernel<R>(r * hinvi1, hinvi1, rinv, gi, pi);
-            m4_kernel<R>(r * hinvj, hinvj, rinv, gj, pj);
-            g = R(0.5) * (gi + gj);
-            phi = R(0.5) * (pi + pj);
-          } else {
-            g = rinv * rinv * rinv;
-            phi = -rinv;
+        if (j < nfar) {
+          const V s0 = s_far[warp][j];
+          pair_far<R>(xi0, yi0, zi0, s0, ax0, ay0, az0, pt0);
+          if (nL > 32) pair_far<R>(xi1, yi1, zi1, s0, ax1, ay1, az1, pt1);
+        }
+      }
+      // one full batch of queued softened pairs, one per lane (queue <= 63)
+      auto drain32 = [&]() {
+        __syncwarp();
+        // one full batch: each lane one queued softened pair
+        const int qv = s_q[warp][nqp - 32 + lane];
+        __syncwarp();
+        const int tq = qv >> 16, jq = qv & 0xffff;
+        const V T = s_tgt[warp][tq];
+        const V S = s_near[warp][jq];
+        const R ddx = T.x - S.x, ddy = T.y - S.y, ddz = T.z - S.z;
+        R gb, pb;
+        pair_soft<R>(fma(ddx, ddx, fma(ddy, ddy, ddz * ddz)), T.w, s_nhinv[warp][jq], gb, pb);
+        const R mg = S.w * gb;
+        atomicAdd(&s_acc[warp][tq][0], -mg * ddx);
+        atomicAdd(&s_acc[warp][tq][1], -mg * ddy);
+        atomicAdd(&s_acc[warp][tq][2], -mg * ddz);
+        atomicAdd(&s_acc[warp][tq][3], S.w * pb);
+        nqp -= 32;
+      };
+      // candidates: exact per-pair kernel test; pairs outside both kernels take
+      // the unsoftened formula, pairs inside one are queued (self pairs drop out)
+      {
+        const int iters = (nnear + nph - 1) / nph;
+        for (int it = 0; it < iters; ++it) {
+          const int jn = it * nph + ph;
+          const bool vj = lane_on && jn < nnear;
+          const int jj = vj ? jn : 0;
+          const V s0 = s_near[warp][jj];
+          const R h2j = s_nh2[warp][jj];
+          const int ij = s_nidx[warp][jj];
+          bool soft;
+          {
+            const R dx = xi0 - s0.x, dy = yi0 - s0.y, dz = zi0 - s0.z;
+            const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            const bool live = vj && on0 && (ij != fL + t0);
+            soft = live && r2 < fmax(h2i0, h2j);
+            if (live && !soft) {
+              const R ri = rsq(r2);
+              const R mr = s0.w * ri;
+              const R mr3 = mr * (ri * ri);
+              ax0 = fma(-mr3, dx, ax0);
+              ay0 = fma(-mr3, dy, ay0);
+              az0 = fma(-mr3, dz, az0);
+              pt0 -= mr;
+            }
           }
-          const R mg = self ? R(0) : mj * g;
-          ax1 = fma(-mg, dx, ax1);
-          ay1 = fma(-mg, dy, ay1);
-          az1 = fma(-mg, dz, az1);
-          pt1 = fma(self ? R(0) : mj, phi, pt1);
+          const unsigned bq = __ballot_sync(SFMM_FULL, soft);
+          if (soft) s_q[warp][nqp + __popc(bq & lt)] = (t0 << 16) | jj;
+          nqp += __popc(bq);
+          if (nqp >= 32) drain32();
+          if (nL > 32) {  // second target slot (leaves of 33..64 particles)
+            const R dx = xi1 - s0.x, dy = yi1 - s0.y, dz = zi1 - s0.z;
+            const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            const bool live = vj && on1 && (ij != fL + t1);
+            const bool soft1 = live && r2 < fmax(h2i1, h2j);
+            if (live && !soft1) {
+              const R ri = rsq(r2);
+              const R mr = s0.w * ri;
+              const R mr3 = mr * (ri * ri);
+              ax1 = fma(-mr3, dx, ax1);
+              ay1 = fma(-mr3, dy, ay1);
+              az1 = fma(-mr3, dz, az1);
+              pt1 -= mr;
+            }
+            const unsigned b1 = __ballot_sync(SFMM_FULL, soft1);
+            if (soft1) s_q[warp][nqp + __popc(b1 & lt)] = (t1 << 16) | jj;
+            nqp += __popc(b1);
+            if (nqp >= 32) drain32();
+          }
         }
       }
       __syncwarp();
-      nb = 0;
+      // drain the queue before the staged candidates are overwritten
+      if (nqp > 0) {
+        const int qv = (lane < nqp) ? s_q[warp][lane] : 0;
+        __syncwarp();
+        if (lane < nqp) {
+          const int tq = qv >> 16, jq = qv & 0xffff;
+          const V T = s_tgt[warp][tq];
+          const V S = s_near[warp][jq];
+          const R ddx = T.x - S.x, ddy = T.y - S.y, ddz = T.z - S.z;
+          R gb, pb;
+          pair_soft<R>(fma(ddx, ddx, fma(ddy, ddy, ddz * ddz)), T.w, s_nhinv[warp][jq], gb, pb);
+          const R mg = S.w * gb;
+          atomicAdd(&s_acc[warp][tq][0], -mg * ddx);
+          atomicAdd(&s_acc[warp][tq][1], -mg * ddy);
+          atomicAdd(&s_acc[warp][tq][2], -mg * ddz);
+          atomicAdd(&s_acc[warp][tq][3], S.w * pb);
+        }
+        nqp = 0;
+      }
+      __syncwarp();
+      nfar = 0;
+      nnear = 0;
       if (e >= cnt) break;
     }
+    if (!on0) { ax0 = ay0 = az0 = pt0 = R(0); }
+    if (!on1) { ax1 = ay1 = az1 = pt1 = R(0); }
 
     // combine the phases of each target, add the far field, write out
     double sm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -242,9 +377,9 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
         R v[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          R s = R(0);
-          for (int q = 0; q < nph; ++q) s += s_red[warp][c][q * ntl + lane];
-          v[c] = s;
+          R sacc = s_acc[warp][t][c];
+          for (int q = 0; q < nph; ++q) sacc += s_red[warp][c][q * ntl + lane];
+          v[c] = sacc;
         }
         const int i = fL + t;
         double f[4];
@@ -280,10 +415,10 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      double s = sm[c];
+      double sv = sm[c];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(SFMM_FULL, s, o);
-      sm[c] = s;
+      for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(SFMM_FULL, sv, o);
+      sm[c] = sv;
     }
     if (lane == 0) {
 #pragma unroll
@@ -292,24 +427,41 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
   }
 }
 
-// Fixed-order reduction of the per-leaf sums: one block, Neumaier
-// compensated partial sums per thread, then a tree over threads.
-__global__ void k_reduce_leafsum(int nleaves, const double* __restrict__ leafsum, double* __restrict__ out) {
-  __shared__ double sh[5][256];
-  double s[5] = {0, 0, 0, 0, 0}, cmp[5] = {0, 0, 0, 0, 0};
-  for (int q = threadIdx.x; q < nleaves; q += blockDim.x) {
+// Fixed-order reduction of the per-leaf sums: every block sums a contiguous
+// range of leaves (tree over threads), then one block sums the block
+// partials; the order never changes, so reruns are bitwise identical.
+#define RED_NT 256
+#define RED_BLOCKS 152
+
+__global__ void k_reduce_leafsum(int nleaves, const double* __restrict__ leafsum, double* __restrict__ part) {
+  __shared__ double sh[5][RED_NT];
+  const int per = (nleaves + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * per, hi = min(nleaves, lo + per);
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int q = lo + threadIdx.x; q < hi; q += RED_NT)
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const double v = leafsum[5 * (size_t)q + c];
-      const double t = s[c] + v;
-      cmp[c] += (fabs(s[c]) >= fabs(v)) ? (s[c] - t) + v : (v - t) + s[c];
-      s[c] = t;
-    }
-  }
+    for (int c = 0; c < 5; ++c) s[c] += leafsum[5 * (size_t)q + c];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = s[c] + cmp[c];
+  for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = s[c];
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+  for (int w = RED_NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) part[5 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_reduce_final(int nparts, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double sh[5][RED_NT];
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int q = threadIdx.x; q < nparts; q += RED_NT)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) s[c] += part[5 * q + c];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = s[c];
+  __syncthreads();
+  for (int w = RED_NT / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
       for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
     __syncthreads();
@@ -320,7 +472,7 @@ __global__ void k_reduce_leafsum(int nleaves, const double* __restrict__ leafsum
 int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   const int nl = c->nleaves;
   int rc;
-  if ((rc = c->red_part.ensure(sizeof(double) * 5 * (size_t)nl + 64))) return rc;
+  if ((rc = c->red_part.ensure(sizeof(double) * 5 * ((size_t)nl + RED_BLOCKS + 1)))) return rc;
   unsigned long long* ctr = c->counters.as<unsigned long long>();
   SFMM_CUDA_TRY(cudaMemsetAsync(ctr + 10, 0, sizeof(unsigned long long), c->stream));
   P2PArgs a{};
@@ -343,6 +495,9 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   a.perm = c->perm.as<int>();
   a.far32 = c->far.as<float4>();
   a.far64 = c->far.as<double>();
+  a.ncx = c->ncx.as<double>();
+  a.ncy = c->ncy.as<double>();
+  a.ncz = c->ncz.as<double>();
   a.G = c->G;
   a.self_pot = c->self_potential;
   a.leaf_counter = reinterpret_cast<int*>(ctr + 10);
@@ -350,22 +505,27 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   a.pot = pot;
   a.leafsum = c->red_part.as<double>();
   const bool f32 = (c->precision == SFMM_FP32);
+  const int nt = 32 * (f32 ? p2p_warps<true>() : p2p_warps<false>());
   int per_sm = 0;
-  if (f32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<true>, P2P_NT, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<false>, P2P_NT, 0);
+  if (f32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<true>, nt, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<false>, nt, 0);
   if (per_sm < 1) per_sm = 1;
   const int nblocks = per_sm * num_sms(c->device);
-  if (f32) k_p2p<true><<<nblocks, P2P_NT, 0, c->stream>>>(a);
-  else k_p2p<false><<<nblocks, P2P_NT, 0, c->stream>>>(a);
+  if (f32) k_p2p<true><<<nblocks, nt, 0, c->stream>>>(a);
+  else k_p2p<false><<<nblocks, nt, 0, c->stream>>>(a);
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   return SFMM_OK;
 }
 
-int run_reduce(sfmm_ctx* c, const double*, const double*) {
-  double* out = c->red_part.as<double>() + 5 * (size_t)c->nleaves;
-  k_reduce_leafsum<<<1, 256, 0, c->stream>>>(c->nleaves, c->red_part.as<double>(), out);
+int run_reduce(sfmm_ctx* c, double** out_dev) {
+  double* part = c->red_part.as<double>() + 5 * (size_t)c->nleaves;
+  double* out = part + 5 * RED_BLOCKS;
+  k_reduce_leafsum<<<RED_BLOCKS, RED_NT, 0, c->stream>>>(c->nleaves, c->red_part.as<double>(), part);
   ++c->nlaunch;
+  k_reduce_final<<<1, RED_NT, 0, c->stream>>>(RED_BLOCKS, part, out);
+  ++c->nlaunch;
+  *out_dev = out;
   SFMM_CUDA_TRY(cudaGetLastError());
   return SFMM_OK;
 }

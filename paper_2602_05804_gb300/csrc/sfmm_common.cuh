@@ -16,6 +16,7 @@
 #define SFMM_ST_ARENA       0x08  // P2P list arena overflow (capacity)
 #define SFMM_ST_DEPTH       0x10  // branch deeper than SFMM_MAXDEPTH
 #define SFMM_ST_INTERNAL    0x20  // internal consistency check failed
+#define SFMM_ST_CHILDLIST   0x40  // child-frontier arena overflow (capacity)
 
 #define SFMM_MAXDEPTH 128
 

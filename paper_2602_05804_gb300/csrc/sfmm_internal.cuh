@@ -2,6 +2,7 @@
 // stage launchers implemented in tree.cu, moments.cu, walk.cu, p2p.cu.
 #pragma once
 #include <string>
+#include <vector>
 
 #include "sfmm_common.cuh"
 
@@ -26,6 +27,7 @@ struct sfmm_ctx {
   int self_potential = 0;
   int ring_capacity = 8192;
   int64_t list_capacity = 0;
+  int64_t cf_capacity = 0;  // child-frontier arena entries per level parity (0 = automatic)
   int profile = 0;
 
   // built state
@@ -34,6 +36,9 @@ struct sfmm_ctx {
   int leaf_size = 0;
   int32_t nnodes = 0, nleaves = 0;
   int moments_order = -1;  // order of the cached moments (-1: none)
+  int walk_mode = 0;        // 0: per-leaf replay (Algorithm 1), 1: per-node shared pairs
+  int max_depth = 0;
+  std::vector<int> h_level_off;  // host copy, max_depth + 2 entries
 
   // inputs staged from host (sfmm_solve_host)
   DevBuf in_pos, in_mass, in_h;
@@ -50,6 +55,7 @@ struct sfmm_ctx {
   DevBuf pnode;                 // int32 sorted position -> leaf node
   DevBuf prel;                  // float4 {x - s_leaf, y - s_leaf, z - s_leaf, m}
   DevBuf ph32;                  // float h
+  DevBuf phh;                   // float2 {1/h, (2h)^2}
 
   // nodes (pre-order)
   DevBuf nfirst, ncount, nright, nparent, ndepth;
@@ -57,10 +63,13 @@ struct sfmm_ctx {
   DevBuf l2bits, flags;
   DevBuf geo_hi, geo_lo;        // float4 walk records
   DevBuf leaf_node, isleaf;
+  DevBuf nlu;                   // leaves under each node
+  DevBuf level_nodes, level_off, level_cur;  // nodes grouped by depth
   DevBuf Qd, Qf;                // scaled moments float64 [nn x NQ], float32 [nn x NQS]
 
   // gravity
   DevBuf ring, far, arena, p2p_off, p2p_cnt, counters, red_part, dump;
+  DevBuf cf_arena, cf_off, cf_cnt, Tnode;  // shared walk: child frontiers, node coefficients
 
   // status word (device) + pinned host mirror
   int* d_status = nullptr;
@@ -79,6 +88,7 @@ int set_error(sfmm_ctx* c, int code, const char* msg);
 // tree.cu
 int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double* h);
 int compute_depth(sfmm_ctx* c);
+int build_levels(sfmm_ctx* c);  // depth, level lists, leaves under each node
 
 // scan (tree.cu): exclusive scan of n uint32 values in place, returns total
 // through `total_dev` (device uint32, may be null)
@@ -87,12 +97,15 @@ int exclusive_scan_u32(sfmm_ctx* c, uint32_t* data, int64_t n, uint32_t* total_d
 // moments.cu
 int compute_moments(sfmm_ctx* c, int order);
 
+// walk_shared.cu
+int run_walk_shared(sfmm_ctx* c, double theta, int order);
+
 // walk.cu
 int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, int64_t cap_p2p);
 
 // p2p.cu
 int run_p2p(sfmm_ctx* c, double* acc, double* pot);
-int run_reduce(sfmm_ctx* c, const double* acc, const double* pot);
+int run_reduce(sfmm_ctx* c, double** out_dev);  // device pointer of the 5 sums
 
 int check_status(sfmm_ctx* c);
 int sync_status(sfmm_ctx* c, int* bits);

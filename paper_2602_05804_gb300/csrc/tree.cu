@@ -147,13 +147,19 @@ __global__ void k_bbox_partial(const double* __restrict__ pos, const double* __r
 
 // bbox[0..2] min, [3..5] max, [6] cube extent E, [7] key scale 2^21 / E (0 if E == 0)
 __global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ bbox) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x;  // one warp
   double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-  for (int b = 0; b < nb; ++b)
+  for (int b = lane; b < nb; b += 32)
     for (int c = 0; c < 3; ++c) {
       mn[c] = fmin(mn[c], part[6 * b + c]);
       mx[c] = fmax(mx[c], part[6 * b + 3 + c]);
     }
+  for (int c = 0; c < 3; ++c)
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[c] = fmin(mn[c], __shfl_xor_sync(SFMM_FULL, mn[c], o));
+      mx[c] = fmax(mx[c], __shfl_xor_sync(SFMM_FULL, mx[c], o));
+    }
+  if (lane != 0) return;
   double E = 0.0;
   for (int c = 0; c < 3; ++c) {
     bbox[c] = mn[c];
@@ -446,7 +452,8 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
                             const double* __restrict__ py, const double* __restrict__ pz,
                             const double* __restrict__ pm, const double* __restrict__ ph,
                             double* __restrict__ ncx, double* __restrict__ ncy, double* __restrict__ ncz,
-                            double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ pnode) {
+                            double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ pnode,
+                            int* __restrict__ nlu) {
   int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (w >= nleaves) return;
@@ -475,13 +482,14 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
     ncy[v] = __ddiv_rn(sy, M);
     ncz[v] = __ddiv_rn(sz, M);
     nhmax[v] = hm;
+    nlu[v] = 1;
   }
 }
 
 // Bottom-up: the second child to finish computes its parent.
 __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nparent,
                          const int* __restrict__ nright, double* ncx, double* ncy, double* ncz, double* nmass,
-                         double* nhmax, int* flags) {
+                         double* nhmax, int* nlu, int* flags) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nleaves) return;
   int v = nparent[leaf_node[q]];
@@ -497,6 +505,7 @@ __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const i
     ncz[v] = __ddiv_rn(dadd(dmul(mL, __ldcg(&ncz[L])), dmul(mR, __ldcg(&ncz[R]))), M);
     nmass[v] = M;
     nhmax[v] = fmax(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
+    nlu[v] = __ldcg(&nlu[L]) + __ldcg(&nlu[R]);
     v = nparent[v];
   }
 }
@@ -557,13 +566,15 @@ __global__ void k_particles_f32(int n, const double* __restrict__ px, const doub
                                 const double* __restrict__ ph, const int* __restrict__ pnode,
                                 const double* __restrict__ ncx, const double* __restrict__ ncy,
                                 const double* __restrict__ ncz, float4* __restrict__ prel,
-                                float* __restrict__ ph32) {
+                                float* __restrict__ ph32, float2* __restrict__ phh) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int v = pnode[i];
   prel[i] = make_float4(__double2float_rn(dsub(px[i], ncx[v])), __double2float_rn(dsub(py[i], ncy[v])),
                         __double2float_rn(dsub(pz[i], ncz[v])), __double2float_rn(pm[i]));
-  ph32[i] = __double2float_rn(ph[i]);
+  const double h = ph[i];
+  ph32[i] = __double2float_rn(h);
+  phh[i] = make_float2(__double2float_rn(1.0 / h), __double2float_rn(4.0 * h * h));
 }
 
 __global__ void k_depth(int nn, const int* __restrict__ nparent, int* __restrict__ depth) {
@@ -577,7 +588,43 @@ __global__ void k_depth(int nn, const int* __restrict__ nparent, int* __restrict
   depth[v] = d;
 }
 
+// Nodes grouped by depth (level lists for the per-node walk).
+__global__ void k_level_count(int nn, const int* __restrict__ depth, uint32_t* __restrict__ cnt) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nn) atomicAdd(&cnt[depth[v]], 1u);
+}
+
+__global__ void k_level_scatter(int nn, const int* __restrict__ depth, const uint32_t* __restrict__ off,
+                                uint32_t* __restrict__ cur, int* __restrict__ level_nodes) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nn) return;
+  int d = depth[v];
+  level_nodes[off[d] + atomicAdd(&cur[d], 1u)] = v;
+}
+
 static inline unsigned nblk(int64_t n, int nt) { return (unsigned)((n + nt - 1) / nt); }
+
+int build_levels(sfmm_ctx* c) {
+  const int nn = c->nnodes;
+  int rc;
+  if ((rc = compute_depth(c))) return rc;
+  // depth < nn always; counts sized for the worst case
+  if ((rc = c->level_off.ensure(sizeof(uint32_t) * ((size_t)nn + 2)))) return rc;
+  if ((rc = c->level_cur.ensure(sizeof(uint32_t) * ((size_t)nn + 2)))) return rc;
+  if ((rc = c->level_nodes.ensure(sizeof(int) * (size_t)nn))) return rc;
+  cudaStream_t st = c->stream;
+  SFMM_CUDA_TRY(cudaMemsetAsync(c->level_off.p, 0, sizeof(uint32_t) * ((size_t)nn + 2), st));
+  SFMM_CUDA_TRY(cudaMemsetAsync(c->level_cur.p, 0, sizeof(uint32_t) * ((size_t)nn + 2), st));
+  k_level_count<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->level_off.as<uint32_t>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
+  if ((rc = exclusive_scan_u32(c, c->level_off.as<uint32_t>(), (int64_t)nn + 1, nullptr))) return rc;
+  k_level_scatter<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->level_off.as<uint32_t>(),
+                                                 c->level_cur.as<uint32_t>(), c->level_nodes.as<int>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
+  return SFMM_OK;
+}
 
 int compute_depth(sfmm_ctx* c) {
   int rc = c->ndepth.ensure(sizeof(int) * (size_t)c->nnodes);
@@ -612,6 +659,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ENS(pnode, sizeof(int) * n);
   ENS(prel, sizeof(float4) * n);
   ENS(ph32, sizeof(float) * n);
+  ENS(phh, sizeof(float2) * n);
   ENS(k_left, sizeof(int) * n);
   ENS(k_right, sizeof(int) * n);
   ENS(k_first, sizeof(int) * n);
@@ -637,6 +685,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ENS(geo_hi, sizeof(float4) * nn_max);
   ENS(geo_lo, sizeof(float4) * nn_max);
   ENS(leaf_node, sizeof(int) * nn_max);
+  ENS(nlu, sizeof(int) * nn_max);
   const int nbb = 2 * num_sms(c->device);
   ENS(bbox_part, sizeof(double) * 6 * nbb);
 #undef ENS
@@ -727,12 +776,14 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   k_leaf_geom<<<nblk((int64_t)nl * 32, 256), 256, 0, st>>>(
       nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
       c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
-      c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>());
+      c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),
+      c->nlu.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaMemsetAsync(c->flags.p, 0, sizeof(int) * nnodes, st));
   k_upward<<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
                                           c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                          c->nmass.as<double>(), c->nhmax.as<double>(), c->flags.as<int>());
+                                          c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
+                                          c->flags.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaMemsetAsync(c->l2bits.p, 0, sizeof(unsigned long long) * nnodes, st));
   k_size<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
@@ -748,7 +799,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   k_particles_f32<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
                                                 c->pm.as<double>(), c->ph.as<double>(), c->pnode.as<int>(),
                                                 c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                                c->prel.as<float4>(), c->ph32.as<float>());
+                                                c->prel.as<float4>(), c->ph32.as<float>(), c->phh.as<float2>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   if (c->keys_a.p != (void*)ka) {

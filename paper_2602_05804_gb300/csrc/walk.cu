@@ -19,170 +19,9 @@
 // a certified error bound; within 1e-5 relative of a tie the decision is
 // taken again in float64 with the exact expression of the acceptance test,
 // so the interaction lists equal those of a plain float64 evaluation.
-#include <type_traits>
-
-#include "expansion_gen.cuh"
-#include "sfmm_internal.cuh"
+#include "walk_common.cuh"
 
 namespace sfmm {
-
-#define WALK_WARPS 4
-#define WALK_NT (WALK_WARPS * 32)
-#define WALK_MQ 64
-
-enum { MODE_COMPUTE = 0, MODE_COUNT = 1, MODE_WRITE = 2 };
-
-struct WalkArgs {
-  int nleaves;
-  const int* leaf_node;
-  const int* nfirst;
-  const int* ncount;
-  const int* nright;
-  const float4* geo_hi;
-  const float4* geo_lo;
-  const double* ncx;
-  const double* ncy;
-  const double* ncz;
-  const double* nsize;
-  const double* nhmax;
-  const float* Qf;
-  const double* Qd;
-  int nqs;  // row stride of Qf
-  const float4* prel;
-  const double* px;
-  const double* py;
-  const double* pz;
-  int* ring;
-  int ring_cap;  // power of two
-  int* leaf_counter;
-  int* arena;
-  unsigned long long* arena_counter;
-  long long arena_cap;
-  long long* p2p_off;
-  int* p2p_cnt;
-  float4* far32;
-  double* far64;
-  int* status;
-  unsigned long long* stat;  // m2l, m2l_unique, p2p_leaves, p2p_pairs, fallbacks
-  double theta;
-  float theta_f;
-  int* m2l_cnt;               // MODE_COUNT
-  const long long* m2l_off;   // MODE_WRITE
-  int* dump_level;
-  int* dump_src;
-};
-
-template <int P> struct Exp;
-#define SFMM_EXP(PP, PP1)                                                                                      \
-  template <> struct Exp<PP> {                                                                                 \
-    static constexpr int NM = SFMM_NM_##PP, NF = SFMM_NF_##PP, NC = NM + NF;                                   \
-    static constexpr int NQ = ncoef(PP), NMONO1 = ncoef(PP + 1);                                               \
-    template <typename T> __device__ static void derivs(T x, T y, T z, T ri, T* D) { sfmm_derivs_##PP1(x, y, z, ri, D); } \
-    template <typename T> __device__ static void m2l(const T* D, const T* Q, T* C) { sfmm_m2l_##PP(D, Q, C); }  \
-    template <typename T> __device__ static void m2l_nodip(const T* D, const T* Q, T* C) { sfmm_m2l_##PP##_nodip(D, Q, C); } \
-    template <typename T, typename U> __device__ static void l2p(const T* am, const U* C, T* o) { sfmm_l2p_##PP(am, C, o); } \
-    template <typename T> __device__ static void mono(T x, T y, T z, T* o) { sfmm_mono_##PP(x, y, z, o); }     \
-    template <typename T> __device__ static void mono1(T x, T y, T z, T* o) { sfmm_mono_##PP1(x, y, z, o); }   \
-    __device__ static const signed char* table() { return &sfmm_l2l_table_##PP[0][0]; }                       \
-  };
-SFMM_EXP(0, 1)
-SFMM_EXP(1, 2)
-SFMM_EXP(2, 3)
-SFMM_EXP(3, 4)
-SFMM_EXP(4, 5)
-#undef SFMM_EXP
-
-// Reduce-scatter over the warp: on entry every lane holds v[0..32); on exit
-// v[0] on lane l is the warp sum of entry l.
-template <typename T>
-__device__ __forceinline__ T reduce_scatter32(T (&v)[32], int lane) {
-#pragma unroll
-  for (int step = 0; step < 5; ++step) {
-    const int o = 16 >> step;
-    const bool upper = (lane & o) != 0;
-#pragma unroll
-    for (int c = 0; c < o; ++c) {
-      T send = upper ? v[c] : v[c + o];
-      T keep = upper ? v[c + o] : v[c];
-      v[c] = keep + __shfl_xor_sync(SFMM_FULL, send, o);
-    }
-  }
-  return v[0];
-}
-
-// Acceptance test of Sect. 3: accept iff (l_t + l_s) < theta d and not
-// d < l_t + l_s + R_kern max(h_t, h_s).
-__device__ __forceinline__ bool decide(const float4& hiA, const float4& loA, const float4& hiB, const float4& loB,
-                                       int A, int B, const WalkArgs& a, int& nfb) {
-  const float dx = df_diff(hiB.x, loB.x, hiA.x, loA.x);
-  const float dy = df_diff(hiB.y, loB.y, hiA.y, loA.y);
-  const float dz = df_diff(hiB.z, loB.z, hiA.z, loA.z);
-  const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  const float d = __fsqrt_rn(d2);
-  const float ls = hiA.w + hiB.w;
-  const float hm = fmaxf(loA.w, loB.w);
-  const float td = a.theta_f * d;
-  const float m1 = td - ls, t1 = 1e-5f * (td + ls);
-  const float rhs = fmaf(2.0f, hm, ls);
-  const float m2 = d - rhs, t2 = 1e-5f * (d + rhs);
-  if (d2 >= 1e-30f && d2 <= 1e30f) {
-    if (m1 < -t1 || m2 < -t2) return false;
-    if (m1 > t1 && m2 > t2) return true;
-  }
-  ++nfb;
-  const double ddx = dsub(a.ncx[B], a.ncx[A]);
-  const double ddy = dsub(a.ncy[B], a.ncy[A]);
-  const double ddz = dsub(a.ncz[B], a.ncz[A]);
-  const double dd = __dsqrt_rn(dadd(dadd(dmul(ddx, ddx), dmul(ddy, ddy)), dmul(ddz, ddz)));
-  const double lsd = dadd(a.nsize[A], a.nsize[B]);
-  const double hmd = fmax(a.nhmax[A], a.nhmax[B]);
-  const bool mac = lsd < dmul(a.theta, dd);
-  const bool soft = dd < dadd(lsd, dmul(SFMM_RKERN, hmd));
-  return mac && !soft;
-}
-
-// One node-node interaction (target centre A, source node s) accumulated
-// into the lane's coefficients.
-template <int P, bool F32>
-__device__ __forceinline__ void m2l_eval(int s, const float4& hiA, const float4& loA, double cAx, double cAy,
-                                         double cAz, const WalkArgs& a,
-                                         typename std::conditional<F32, float, double>::type* C) {
-  using E = Exp<P>;
-  if (s < 0) return;
-  if constexpr (F32) {
-    const float4 hB = a.geo_hi[s], lB = a.geo_lo[s];
-    const float rx = df_diff(hB.x, lB.x, hiA.x, loA.x);
-    const float ry = df_diff(hB.y, lB.y, hiA.y, loA.y);
-    const float rz = df_diff(hB.z, lB.z, hiA.z, loA.z);
-    const float ri = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
-    float D[E::NMONO1];
-    E::derivs(rx * ri, ry * ri, rz * ri, ri, D);
-    constexpr int NQ4 = (E::NQ + 3) / 4;
-    float Q[NQ4 * 4];
-    const float4* q4 = reinterpret_cast<const float4*>(a.Qf + (size_t)s * a.nqs);
-#pragma unroll
-    for (int t = 0; t < NQ4; ++t) {
-      float4 v = __ldg(q4 + t);
-      Q[4 * t] = v.x;
-      Q[4 * t + 1] = v.y;
-      Q[4 * t + 2] = v.z;
-      Q[4 * t + 3] = v.w;
-    }
-    // moments are about the centre of mass: the dipole vanishes to rounding
-    E::m2l_nodip(D, Q, C);
-  } else {
-    const double rx = a.ncx[s] - cAx, ry = a.ncy[s] - cAy, rz = a.ncz[s] - cAz;
-    const double ri = rsqrt(fma(rx, rx, fma(ry, ry, rz * rz)));
-    double D[E::NMONO1];
-    E::derivs(rx * ri, ry * ri, rz * ri, ri, D);
-    double Q[E::NQ];
-    const double* q = a.Qd + (size_t)s * E::NQ;
-#pragma unroll
-    for (int t = 0; t < E::NQ; ++t) Q[t] = __ldg(q + t);
-    E::m2l(D, Q, C);
-  }
-}
-
 template <int P, bool F32, int MODE>
 __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
   using E = Exp<P>;
@@ -205,7 +44,7 @@ __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
   const int gw = blockIdx.x * WALK_WARPS + warp;
-  const int cap = a.ring_cap, mask = cap - 1;
+  const int cap = a.ring_cap;
   int* const bufA = a.ring + (size_t)gw * 2 * cap;
   int* const bufB = bufA + cap;
 
@@ -259,9 +98,17 @@ __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
       while (true) {
         const bool more = head < tail;
         if (more) {
+          // FIFO over the fixed frontier of an internal branch node; LIFO at the
+          // leaf, where lowering pushes children (keeps the live list short)
           const int cnt = min(32, tail - head);
-          const int s = (lane < cnt) ? cur[(head + lane) & mask] : -1;
-          head += cnt;
+          int s;
+          if (!leafA) {
+            s = (lane < cnt) ? cur[head + lane] : -1;
+            head += cnt;
+          } else {
+            s = (lane < cnt) ? cur[tail - cnt + lane] : -1;
+            tail -= cnt;
+          }
           bool acc = false, open = false;
           int rB = -1;
           if (s >= 0) {
@@ -310,14 +157,14 @@ __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
           } else {
             const unsigned bl = __ballot_sync(SFMM_FULL, sleaf), bi = __ballot_sync(SFMM_FULL, sint);
             const int addl = __popc(bl), addi = 2 * __popc(bi);
-            if (nn + addl > cap || tail + addi - head > cap) {
+            if (nn + addl > cap || tail + addi > cap) {
               bad = true;
             } else {
               if (sleaf) nxt[nn + __popc(bl & lt)] = s;
               if (sint) {
                 const int cp = tail + 2 * __popc(bi & lt);
-                cur[cp & mask] = s + 1;
-                cur[(cp + 1) & mask] = rB;
+                cur[cp] = s + 1;
+                cur[cp + 1] = rB;
               }
             }
             nn += addl;
@@ -596,6 +443,7 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
     a.stat = ctr;
     a.theta = theta;
     a.theta_f = (float)theta;
+    a.theta2_f = (float)(theta * theta);
     if (dump) {
       // counting pass, then the writing pass at the scanned offsets
       if ((rc = c->dump.ensure(sizeof(int) * (size_t)(nl + 1) + sizeof(long long) * (size_t)(nl + 1)))) return rc;
@@ -667,6 +515,7 @@ int run_walk_dump_write(sfmm_ctx* c, double theta, const long long* d_off, int* 
   a.stat = ctr;
   a.theta = theta;
   a.theta_f = (float)theta;
+  a.theta2_f = (float)(theta * theta);
   a.m2l_off = d_off;
   a.dump_level = d_level;
   a.dump_src = d_src;

@@ -1,0 +1,502 @@
+// Shared-interaction walk: the pairs of Algorithm 2 evaluated once per node
+// instead of once per leaf below it.
+//
+// In the per-leaf replay (Algorithm 1) the pairs whose target is a branch
+// node c_k depend only on c_k, not on the leaf: a pair (c_k, s) opened at an
+// internal c_k is pushed as (c_{k+1}, .) whichever child c_{k+1} is, so both
+// children of a node receive the same opened list.  Processing the tree
+// level by level, one warp per node, therefore visits every pair exactly once
+// -- the caching of shared long-range interactions suggested in Sect. 5 --
+// and yields the same interactions, hence the same result up to the order of
+// summation.  The inherited coefficients are translated once per node
+// (T(A) = shift(T(parent)) + C(A), Eq. gravmtranslat) and evaluated at the
+// leaves (L2P).  Leaves run the lowering of Algorithm 2 and emit their
+// neighbour lists exactly as in the per-leaf replay.
+#include "walk_common.cuh"
+
+namespace sfmm {
+
+struct LevelArgs {
+  WalkArgs w;
+  int level;
+  const int* level_nodes;
+  int level_begin, level_count;
+  const int* nparent;
+  const int* nlu;
+  const uint32_t* leaf_index;  // exclusive scan of leaf flags: leaf number of a leaf node
+  const int* cf_in;            // child frontiers written by the previous level
+  const long long* cf_off;
+  const int* cf_cnt;
+  int* cf_out;
+  long long* cf_off_out;
+  int* cf_cnt_out;
+  unsigned long long* cf_counter;
+  long long cf_cap;
+  float* T32;                  // node coefficients: hi/lo pairs (FP32 form)
+  double* T64;                 // node coefficients (FP64 form)
+  int tstride;                 // coefficients per node (padded)
+};
+
+template <int P, bool F32>
+__global__ void __launch_bounds__(WALK_NT) k_walk_level(const LevelArgs la) {
+  using E = Exp<P>;
+  using R = typename std::conditional<F32, float, double>::type;
+  constexpr int NC = E::NC;
+  constexpr int NCS = (NC + 31) / 32;
+  const WalkArgs& a = la.w;
+
+  __shared__ int s_queue[WALK_WARPS][WALK_MQ];
+  __shared__ R s_T[WALK_WARPS][NCS * 32];
+  __shared__ R s_h[WALK_WARPS][E::NMONO1];
+  __shared__ signed char s_tab[NC * NC];
+  {
+    const signed char* tab = E::table();
+    for (int t = threadIdx.x; t < NC * NC; t += WALK_NT) s_tab[t] = tab[t];
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt();
+  const int gw = blockIdx.x * WALK_WARPS + warp;
+  const int cap = a.ring_cap;
+  int* const stk = a.ring + (size_t)gw * 2 * cap;  // lowering stack (leaves)
+  int* const out = stk + cap;                      // child frontier / neighbour list
+
+  unsigned long long st_m2l = 0, st_uniq = 0, st_pl = 0, st_pp = 0;
+  int st_fb = 0;
+
+  while (true) {
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(a.leaf_counter, 1);
+    idx = __shfl_sync(SFMM_FULL, idx, 0);
+    if (idx >= la.level_count) break;
+    const int A = la.level_nodes[la.level_begin + idx];
+    const int rA = a.nright[A];
+    const bool leafA = rA < 0;
+    const int par = la.nparent[A];
+    const float4 hiA = a.geo_hi[A], loA = a.geo_lo[A];
+    double cAx = 0.0, cAy = 0.0, cAz = 0.0;
+    if (!F32) {
+      cAx = a.ncx[A];
+      cAy = a.ncy[A];
+      cAz = a.ncz[A];
+    }
+    // the opened list inherited from the parent (the root starts from itself)
+    const int* fin = nullptr;
+    int nF = 1;
+    if (par >= 0) {
+      fin = la.cf_in + la.cf_off[par];
+      nF = la.cf_cnt[par];
+    }
+    int head = 0, tail = nF, nn = 0;
+    bool bad = false;
+    if (leafA) {
+      // lowering mutates the list: copy it to the warp's stack
+      if (nF > cap) bad = true;
+      else {
+        for (int t = lane; t < nF; t += 32) stk[t] = fin ? fin[t] : 0;
+      }
+      __syncwarp();
+    }
+    R C[NCS * 32];
+#pragma unroll
+    for (int t = 0; t < NCS * 32; ++t) C[t] = R(0);
+    int nq = 0, nacc_tot = 0;
+    while (!bad) {
+      const bool more = head < tail;
+      if (more) {
+        const int cnt = min(32, tail - head);
+        int s;
+        if (!leafA) {
+          s = (lane < cnt) ? (fin ? fin[head + lane] : 0) : -1;
+          head += cnt;
+        } else {
+          s = (lane < cnt) ? stk[tail - cnt + lane] : -1;
+          tail -= cnt;
+        }
+        bool acc = false, open = false;
+        int rB = -1;
+        if (s >= 0) {
+          const float4 hiB = a.geo_hi[s], loB = a.geo_lo[s];
+          rB = a.nright[s];
+          if (s == A) open = true;
+          else {
+            acc = decide(hiA, loA, hiB, loB, A, s, a, st_fb);
+            open = !acc;
+          }
+        }
+        const unsigned bacc = __ballot_sync(SFMM_FULL, acc);
+        const int nacc = __popc(bacc);
+        nacc_tot += nacc;
+        if (acc) s_queue[warp][nq + __popc(bacc & lt)] = s;
+        nq += nacc;
+        const bool sleaf = open && rB < 0;
+        const bool sint = open && rB >= 0;
+        if (!leafA) {
+          const unsigned b1 = __ballot_sync(SFMM_FULL, open), b2 = __ballot_sync(SFMM_FULL, sint);
+          const int add = __popc(b1) + __popc(b2);
+          if (nn + add > cap) {
+            bad = true;
+          } else if (open) {
+            const int pos = nn + __popc(b1 & lt) + __popc(b2 & lt);
+            if (sleaf) out[pos] = s;
+            else {
+              out[pos] = s + 1;
+              out[pos + 1] = rB;
+            }
+          }
+          nn += add;
+        } else {
+          const unsigned bl = __ballot_sync(SFMM_FULL, sleaf), bi = __ballot_sync(SFMM_FULL, sint);
+          const int addl = __popc(bl), addi = 2 * __popc(bi);
+          if (nn + addl > cap || tail + addi > cap) {
+            bad = true;
+          } else {
+            if (sleaf) out[nn + __popc(bl & lt)] = s;
+            if (sint) {
+              const int cp = tail + 2 * __popc(bi & lt);
+              stk[cp] = s + 1;
+              stk[cp + 1] = rB;
+            }
+          }
+          nn += addl;
+          tail += addi;
+        }
+        __syncwarp();
+        if (bad) break;
+      }
+      while (nq >= 32 || (!more && nq > 0)) {
+        const int take = min(nq, 32);
+        const int src = (lane < take) ? s_queue[warp][nq - take + lane] : -1;
+        __syncwarp();
+        m2l_eval<P, F32>(src, hiA, loA, cAx, cAy, cAz, a, C);
+        nq -= take;
+      }
+      if (!more) break;
+    }
+    if (bad) {
+      // leave empty lists behind so that nothing downstream reads stale offsets
+      if (lane == 0) {
+        set_status(a.status, SFMM_ST_RING);
+        if (leafA) a.p2p_cnt[la.leaf_index[A]] = 0;
+        else la.cf_cnt_out[A] = 0;
+      }
+      continue;
+    }
+    if (lane == 0) {
+      st_uniq += nacc_tot;
+      st_m2l += (unsigned long long)nacc_tot * la.nlu[A];
+    }
+
+    // coefficients of A: own level sum plus the parent's, translated
+    R lev[NCS];
+#pragma unroll
+    for (int b = 0; b < NCS; ++b) {
+      R v[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) v[t] = C[32 * b + t];
+      lev[b] = reduce_scatter32(v, lane);
+    }
+    R Tn[NCS];
+    float Tl[NCS];
+#pragma unroll
+    for (int b = 0; b < NCS; ++b) {
+      Tn[b] = R(0);
+      Tl[b] = 0.0f;
+    }
+    if (par >= 0) {
+      const float4 hiP = a.geo_hi[par], loP = a.geo_lo[par];
+#pragma unroll
+      for (int b = 0; b < NCS; ++b) {
+        const int j = lane + 32 * b;
+        if constexpr (F32) {
+          Tn[b] = la.T32[2 * ((size_t)par * la.tstride + j)];
+          Tl[b] = la.T32[2 * ((size_t)par * la.tstride + j) + 1];
+        } else {
+          Tn[b] = la.T64[(size_t)par * la.tstride + j];
+        }
+        s_T[warp][j] = Tn[b];
+      }
+      if (lane == 0) {
+        R hx, hy, hz;
+        if constexpr (F32) {
+          hx = df_diff(hiA.x, loA.x, hiP.x, loP.x);
+          hy = df_diff(hiA.y, loA.y, hiP.y, loP.y);
+          hz = df_diff(hiA.z, loA.z, hiP.z, loP.z);
+        } else {
+          hx = cAx - a.ncx[par];
+          hy = cAy - a.ncy[par];
+          hz = cAz - a.ncz[par];
+        }
+        R hm[E::NMONO1];
+        E::mono1(hx, hy, hz, hm);
+#pragma unroll
+        for (int t = 0; t < E::NMONO1; ++t) s_h[warp][t] = hm[t];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int b = 0; b < NCS; ++b) {
+        const int j = lane + 32 * b;
+        if (j < NC) {
+          R corr = R(0);
+          const signed char* row = s_tab + j * NC;
+          for (int i = 0; i < NC; ++i) {
+            const int t = row[i];
+            if (t > 0) corr = fma(s_h[warp][t], s_T[warp][i], corr);
+          }
+          if constexpr (F32) {
+            dfloat r = df_add_f(dfloat{Tn[b], Tl[b]}, corr);
+            Tn[b] = r.hi;
+            Tl[b] = r.lo;
+          } else {
+            Tn[b] += corr;
+          }
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int b = 0; b < NCS; ++b) {
+      const int j = lane + 32 * b;
+      if constexpr (F32) {
+        dfloat r = df_add_f(dfloat{Tn[b], Tl[b]}, lev[b]);
+        Tn[b] = r.hi;
+        Tl[b] = r.lo;
+        if (!leafA) {
+          la.T32[2 * ((size_t)A * la.tstride + j)] = Tn[b];
+          la.T32[2 * ((size_t)A * la.tstride + j) + 1] = Tl[b];
+        }
+      } else {
+        Tn[b] += lev[b];
+        if (!leafA) la.T64[(size_t)A * la.tstride + j] = Tn[b];
+      }
+    }
+
+    if (!leafA) {
+      // the opened list both children inherit
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(la.cf_counter, (unsigned long long)nn);
+      base = __shfl_sync(SFMM_FULL, base, 0);
+      if ((long long)(base + nn) > la.cf_cap) {
+        if (lane == 0) {
+          set_status(a.status, SFMM_ST_CHILDLIST);
+          la.cf_cnt_out[A] = 0;
+        }
+      } else {
+        for (int t = lane; t < nn; t += 32) la.cf_out[base + t] = out[t];
+        if (lane == 0) {
+          la.cf_off_out[A] = (long long)base;
+          la.cf_cnt_out[A] = nn;
+        }
+      }
+      __syncwarp();
+      continue;
+    }
+
+    // leaf: L2P, then its neighbour list
+    const int fL = a.nfirst[A], nL = a.ncount[A];
+    const int leaf = (int)la.leaf_index[A];
+#pragma unroll
+    for (int b = 0; b < NCS; ++b) {
+      if constexpr (F32) s_T[warp][lane + 32 * b] = Tn[b] + Tl[b];
+      else s_T[warp][lane + 32 * b] = Tn[b];
+    }
+    __syncwarp();
+    for (int t = lane; t < nL; t += 32) {
+      const int i = fL + t;
+      R ax, ay, az;
+      if constexpr (F32) {
+        const float4 p = a.prel[i];
+        ax = p.x;
+        ay = p.y;
+        az = p.z;
+      } else {
+        ax = a.px[i] - cAx;
+        ay = a.py[i] - cAy;
+        az = a.pz[i] - cAz;
+      }
+      R am[E::NQ], o4[4];
+      E::mono(ax, ay, az, am);
+      E::l2p(am, &s_T[warp][0], o4);
+      if constexpr (F32) a.far32[i] = make_float4(o4[1], o4[2], o4[3], -o4[0]);
+      else {
+        a.far64[4 * (size_t)i] = o4[1];
+        a.far64[4 * (size_t)i + 1] = o4[2];
+        a.far64[4 * (size_t)i + 2] = o4[3];
+        a.far64[4 * (size_t)i + 3] = -o4[0];
+      }
+    }
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.arena_counter, (unsigned long long)nn);
+    base = __shfl_sync(SFMM_FULL, base, 0);
+    if ((long long)(base + nn) > a.arena_cap) {
+      if (lane == 0) {
+        set_status(a.status, SFMM_ST_ARENA);
+        a.p2p_cnt[leaf] = 0;
+      }
+    } else {
+      unsigned long long pairs = 0;
+      for (int t = lane; t < nn; t += 32) {
+        const int sN = out[t];
+        a.arena[base + t] = sN;
+        pairs += (unsigned long long)nL * a.ncount[sN] - (sN == A ? nL : 0);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(SFMM_FULL, pairs, o);
+      if (lane == 0) {
+        a.p2p_off[leaf] = (long long)base;
+        a.p2p_cnt[leaf] = nn;
+        st_pl += nn;
+        st_pp += pairs;
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) st_fb += __shfl_xor_sync(SFMM_FULL, st_fb, o);
+  if (lane == 0) {
+    atomicAdd(&a.stat[0], st_m2l);
+    atomicAdd(&a.stat[1], st_uniq);
+    atomicAdd(&a.stat[2], st_pl);
+    atomicAdd(&a.stat[3], st_pp);
+    atomicAdd(&a.stat[4], (unsigned long long)st_fb);
+  }
+}
+
+template <int P, bool F32>
+static int run_levels(sfmm_ctx* c, double theta, int order) {
+  using E = Exp<P>;
+  constexpr int NCS = (E::NC + 31) / 32;
+  const int nn = c->nnodes, nl = c->nleaves;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_level<P, F32>, WALK_NT, 0);
+  if (per_sm < 1) per_sm = 1;
+  const int max_blocks = per_sm * num_sms(c->device);
+  const int tstride = NCS * 32;
+  int rc;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    const int nwarps = max_blocks * WALK_WARPS;
+    if ((rc = c->ring.ensure(sizeof(int) * (size_t)nwarps * 2 * c->ring_capacity))) return rc;
+    long long arena_cap = c->list_capacity > 0 ? c->list_capacity : (long long)nl * 96 + 1024;
+    if ((rc = c->arena.ensure(sizeof(int) * (size_t)arena_cap))) return rc;
+    arena_cap = (long long)(c->arena.bytes / sizeof(int));
+    long long cf_cap = c->cf_capacity > 0 ? c->cf_capacity : (long long)nn * 64 + 4096;
+    if ((rc = c->cf_arena.ensure(sizeof(int) * 2 * (size_t)cf_cap))) return rc;
+    cf_cap = (long long)(c->cf_arena.bytes / sizeof(int) / 2);
+    if ((rc = c->cf_off.ensure(sizeof(long long) * 2 * (size_t)nn))) return rc;
+    if ((rc = c->cf_cnt.ensure(sizeof(int) * 2 * (size_t)nn))) return rc;
+    if ((rc = c->Tnode.ensure((F32 ? 2 * sizeof(float) : sizeof(double)) * (size_t)nn * tstride))) return rc;
+    if ((rc = c->p2p_off.ensure(sizeof(long long) * (size_t)nl))) return rc;
+    if ((rc = c->p2p_cnt.ensure(sizeof(int) * (size_t)nl))) return rc;
+    const int nlev = c->max_depth + 1;
+    if ((rc = c->counters.ensure(sizeof(unsigned long long) * (16 + 2 * (size_t)nlev)))) return rc;
+    if ((rc = c->far.ensure((F32 ? sizeof(float4) : 4 * sizeof(double)) * (size_t)c->n))) return rc;
+    unsigned long long* ctr = c->counters.as<unsigned long long>();
+    SFMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * (16 + 2 * (size_t)nlev), c->stream));
+
+    LevelArgs la{};
+    WalkArgs& a = la.w;
+    a.nleaves = nl;
+    a.leaf_node = c->leaf_node.as<int>();
+    a.nfirst = c->nfirst.as<int>();
+    a.ncount = c->ncount.as<int>();
+    a.nright = c->nright.as<int>();
+    a.geo_hi = c->geo_hi.as<float4>();
+    a.geo_lo = c->geo_lo.as<float4>();
+    a.ncx = c->ncx.as<double>();
+    a.ncy = c->ncy.as<double>();
+    a.ncz = c->ncz.as<double>();
+    a.nsize = c->nsize.as<double>();
+    a.nhmax = c->nhmax.as<double>();
+    a.Qf = c->Qf.as<float>();
+    a.Qd = c->Qd.as<double>();
+    a.nqs = (ncoef(order) + 3) & ~3;
+    a.prel = c->prel.as<float4>();
+    a.px = c->px.as<double>();
+    a.py = c->py.as<double>();
+    a.pz = c->pz.as<double>();
+    a.ring = c->ring.as<int>();
+    a.ring_cap = c->ring_capacity;
+    a.arena = c->arena.as<int>();
+    a.arena_counter = ctr + 9;
+    a.arena_cap = arena_cap;
+    a.p2p_off = c->p2p_off.as<long long>();
+    a.p2p_cnt = c->p2p_cnt.as<int>();
+    a.far32 = c->far.as<float4>();
+    a.far64 = c->far.as<double>();
+    a.status = c->d_status;
+    a.stat = ctr;
+    a.theta = theta;
+    a.theta_f = (float)theta;
+    a.theta2_f = (float)(theta * theta);
+    la.level_nodes = c->level_nodes.as<int>();
+    la.nparent = c->nparent.as<int>();
+    la.nlu = c->nlu.as<int>();
+    la.leaf_index = c->isleaf.as<uint32_t>();
+    la.cf_cap = cf_cap;
+    la.T32 = c->Tnode.as<float>();
+    la.T64 = c->Tnode.as<double>();
+    la.tstride = tstride;
+    int* cfa = c->cf_arena.as<int>();
+    long long* cfo = c->cf_off.as<long long>();
+    int* cfc = c->cf_cnt.as<int>();
+    for (int k = 0; k < nlev; ++k) {
+      const int pin = (k + 1) & 1, pout = k & 1;
+      la.level = k;
+      la.level_begin = c->h_level_off[k];
+      la.level_count = c->h_level_off[k + 1] - c->h_level_off[k];
+      if (la.level_count <= 0) continue;
+      la.cf_in = cfa + (size_t)pin * cf_cap;
+      la.cf_off = cfo + (size_t)pin * nn;
+      la.cf_cnt = cfc + (size_t)pin * nn;
+      la.cf_out = cfa + (size_t)pout * cf_cap;
+      la.cf_off_out = cfo + (size_t)pout * nn;
+      la.cf_cnt_out = cfc + (size_t)pout * nn;
+      la.cf_counter = ctr + 16 + 2 * k;
+      a.leaf_counter = reinterpret_cast<int*>(ctr + 16 + 2 * k + 1);
+      const int blocks = min(max_blocks, (la.level_count + WALK_WARPS - 1) / WALK_WARPS);
+      k_walk_level<P, F32><<<blocks, WALK_NT, 0, c->stream>>>(la);
+      ++c->nlaunch;
+      SFMM_CUDA_TRY(cudaGetLastError());
+    }
+    int bits = 0;
+    if ((rc = sync_status(c, &bits))) return rc;
+    if (bits & SFMM_ST_DEPTH) return set_error(c, SFMM_ESTACK, "tree deeper than supported");
+    if (bits & (SFMM_ST_RING | SFMM_ST_ARENA | SFMM_ST_CHILDLIST)) {
+      if (attempt == 3) return set_error(c, SFMM_ECAPACITY, "walk buffers too small after three regrows");
+      if (bits & SFMM_ST_RING) c->ring_capacity = c->ring_capacity < (1 << 20) ? c->ring_capacity * 16 : (1 << 24);
+      if (bits & SFMM_ST_ARENA) {
+        unsigned long long need = 0;
+        SFMM_CUDA_TRY(cudaMemcpy(&need, ctr + 9, sizeof(need), cudaMemcpyDeviceToHost));
+        int64_t grown = 2 * (int64_t)arena_cap, want = (int64_t)(need + need / 4 + 1024);
+        c->list_capacity = want > grown ? want : grown;
+      }
+      if (bits & SFMM_ST_CHILDLIST) c->cf_capacity = 4 * cf_cap;
+      continue;
+    }
+    SFMM_CUDA_TRY(cudaMemcpy(c->h_scalars, ctr, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost));
+    const unsigned long long* hs = reinterpret_cast<const unsigned long long*>(c->h_scalars);
+    c->stats.m2l = (int64_t)hs[0];
+    c->stats.m2l_unique = (int64_t)hs[1];
+    c->stats.p2p_leaves = (int64_t)hs[2];
+    c->stats.p2p_pairs = (int64_t)hs[3];
+    c->stats.mac_fallbacks = (int64_t)hs[4];
+    return SFMM_OK;
+  }
+  return SFMM_ECAPACITY;
+}
+
+int run_walk_shared(sfmm_ctx* c, double theta, int order) {
+  const bool f32 = c->precision == SFMM_FP32;
+  switch (order) {
+    case 0: return f32 ? run_levels<0, true>(c, theta, order) : run_levels<0, false>(c, theta, order);
+    case 1: return f32 ? run_levels<1, true>(c, theta, order) : run_levels<1, false>(c, theta, order);
+    case 2: return f32 ? run_levels<2, true>(c, theta, order) : run_levels<2, false>(c, theta, order);
+    case 3: return f32 ? run_levels<3, true>(c, theta, order) : run_levels<3, false>(c, theta, order);
+    case 4: return f32 ? run_levels<4, true>(c, theta, order) : run_levels<4, false>(c, theta, order);
+    default: return SFMM_EINVAL;
+  }
+}
+
+}  // namespace sfmm

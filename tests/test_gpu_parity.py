@@ -121,11 +121,12 @@ PARITY = [("uniform", 6000, 10, 0.5, 2), ("plummer", 8001, 16, 0.5, 2), ("plumme
           ("plummer", 2500, 1, 0.5, 2), ("uniform", 1000, 64, 0.9, 2)]
 
 
+@pytest.mark.parametrize("walk", [0, 1])
 @pytest.mark.parametrize("kind,n,ls,theta,p", PARITY)
-def test_fp64_form_matches_oracle(kind, n, ls, theta, p):
+def test_fp64_form_matches_oracle(kind, n, ls, theta, p, walk):
     pos, m, h = _set(kind, n, 17)
     acc_o, pot_o, st_o = oracle.sfmm(pos, m, h, theta=theta, p=p, leaf_size=ls)
-    s = solver("fp64")
+    s = solver("fp64", walk=walk)
     s.build(pos, m, h, ls)
     acc, pot = s.gravity(theta, p)
     acc, pot = acc.cpu().numpy(), pot.cpu().numpy()
@@ -140,11 +141,12 @@ def test_fp64_form_matches_oracle(kind, n, ls, theta, p):
     assert abs(st["W"] - 0.5 * (m * pot_o).sum()) <= 1e-10 * abs(st["W"])
 
 
+@pytest.mark.parametrize("walk", [0, 1])
 @pytest.mark.parametrize("kind,n,ls,theta,p", PARITY)
-def test_fp32_form_matches_oracle(kind, n, ls, theta, p):
+def test_fp32_form_matches_oracle(kind, n, ls, theta, p, walk):
     pos, m, h = _set(kind, n, 17)
     acc_o, pot_o, st_o = oracle.sfmm(pos, m, h, theta=theta, p=p, leaf_size=ls)
-    s = solver("fp32")
+    s = solver("fp32", walk=walk)
     s.build(pos, m, h, ls)
     acc, pot = s.gravity(theta, p)
     acc, pot = acc.cpu().numpy(), pot.cpu().numpy()
@@ -265,3 +267,30 @@ def test_errors_are_reported():
         s.set_option("nonsense", 1.0)
     with pytest.raises(sfmm.SFMMError):
         s.set_option("ring_capacity", 1000)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_shared_walk_equals_replay(prec, tol):
+    """Per-node shared pairs and the per-leaf replay evaluate the same
+    interactions: equal counts, results equal up to summation order."""
+    pos, m, h = workloads.plummer(20000, 44)
+    out = []
+    for walk in (0, 1):
+        s = solver(prec, walk=walk)
+        s.build(pos, m, h, 16)
+        acc, pot = s.gravity(0.5, 2)
+        out.append((acc.cpu().numpy(), pot.cpu().numpy(), s.stats()))
+    (a0, p0, s0), (a1, p1, s1) = out
+    for k in ("m2l", "m2l_unique", "p2p_pairs", "p2p_leaves"):
+        assert s0[k] == s1[k], k
+    assert acc_rel(a1, a0).max() <= tol
+    assert pot_rel(p1, p0).max() <= tol
+
+
+def test_shared_walk_capacity_regrow():
+    pos, m, h = workloads.plummer(6000, 12)
+    acc_o, pot_o, _ = oracle.sfmm(pos, m, h, theta=0.3, p=2, leaf_size=16)
+    s = solver("fp64", walk=1, ring_capacity=256, list_capacity=64)
+    s.build(pos, m, h, 16)
+    acc, pot = s.gravity(0.3, 2)
+    assert acc_rel(acc.cpu().numpy(), acc_o).max() <= TOL_FP64
