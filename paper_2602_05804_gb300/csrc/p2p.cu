@@ -16,7 +16,7 @@ namespace sfmm {
 
 #define P2P_WARPS 8
 #define P2P_NT (P2P_WARPS * 32)
-#define P2P_SB 64
+#define P2P_SB 128
 
 struct P2PArgs {
   int nleaves;
@@ -30,6 +30,7 @@ struct P2PArgs {
   const int* p2p_cnt;
   const float4* prel;
   const float* ph32;
+  const float2* phh;
   const double* px;
   const double* py;
   const double* pz;
@@ -49,30 +50,42 @@ struct P2PArgs {
   double* leafsum;  // nleaves x 5: sum m a (3), sum |m a|, sum m Phi
 };
 
-// M4 softening kernel of one particle (compact support 2h): g = phi'(r)/r
-// and phi, -> 1/r^3 and -1/r outside 2h.  rinv = 1/r (0 when r = 0).
+// M4 softening kernel of one particle (compact support 2h), evaluated with
+// coefficients selected per piece: g = phi'(r)/r and phi, -> 1/r^3 and
+// -1/r outside 2h.  q = r/h, hinv = 1/h, ri = 1/r.
 template <typename R>
-__device__ __forceinline__ void m4_kernel(R q, R hinv, R rinv, R& g, R& phi) {
+__device__ __forceinline__ void m4_kernel(R q, R hinv, R ri, R& g, R& phi) {
+  const bool in1 = q < R(1);
+  const bool out2 = q >= R(2);
+  // g h^3 = c0 + c1 q + c2 q^2 + c3 q^3 (- 1/(15 q^3) for 1 <= q < 2)
+  const R c0 = in1 ? R(4.0 / 3.0) : R(8.0 / 3.0);
+  const R c1 = in1 ? R(0) : R(-3);
+  const R c2 = in1 ? R(-1.2) : R(1.2);
+  const R c3 = in1 ? R(0.5) : R(-1.0 / 6.0);
+  // phi h = d0 + d2 q^2 + d3 q^3 + d4 q^4 + d5 q^5 (+ 1/(15 q) for 1 <= q < 2)
+  const R d0 = in1 ? R(-1.4) : R(-1.6);
+  const R d2 = in1 ? R(2.0 / 3.0) : R(4.0 / 3.0);
+  const R d3 = in1 ? R(0) : R(-1);
+  const R d4 = in1 ? R(-0.3) : R(0.3);
+  const R d5 = in1 ? R(0.1) : R(-1.0 / 30.0);
   const R hinv3 = hinv * hinv * hinv;
-  const R q2 = q * q;
-  const R rinv3 = rinv * rinv * rinv;
-  const R g_in = hinv3 * fma(q2, fma(R(0.5), q, R(-1.2)), R(4.0 / 3.0));
-  const R p_in = hinv * fma(q2, fma(q2, fma(R(0.1), q, R(-0.3)), R(2.0 / 3.0)), R(-1.4));
-  const R g_mid = fma(hinv3, fma(q, fma(q, fma(R(-1.0 / 6.0), q, R(1.2)), R(-3.0)), R(8.0 / 3.0)), R(-1.0 / 15.0) * rinv3);
-  const R p_mid = fma(hinv, fma(q2, fma(q, fma(q, fma(R(-1.0 / 30.0), q, R(0.3)), R(-1.0)), R(4.0 / 3.0)), R(-1.6)),
-                      R(1.0 / 15.0) * rinv);
-  g = (q < R(1)) ? g_in : ((q < R(2)) ? g_mid : rinv3);
-  phi = (q < R(1)) ? p_in : ((q < R(2)) ? p_mid : -rinv);
+  const R ri3 = ri * ri * ri;
+  const R gp = hinv3 * fma(q, fma(q, fma(q, c3, c2), c1), c0);
+  const R pp = hinv * fma(q * q, fma(q, fma(q, fma(q, d5, d4), d3), d2), d0);
+  const R gm = in1 ? gp : fma(R(-1.0 / 15.0), ri3, gp);
+  const R pm = in1 ? pp : fma(R(1.0 / 15.0), ri, pp);
+  g = out2 ? ri3 : gm;
+  phi = out2 ? -ri : pm;
 }
 
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
 template <typename R> struct Vec4;
-template <> struct Vec4<float> { using T = float4; };
-template <> struct Vec4<double> { using T = double4; };
+template <> struct Vec4<float> { using T = float4; using T2 = float2; };
+template <> struct Vec4<double> { using T = double4; using T2 = double2; };
 
-// Far pair (no softening): a -= m r^-3 d, phi -= m / r.
+// Unsoftened pair: a -= m r^-3 d, phi -= m / r.
 template <typename R>
 __device__ __forceinline__ void pair_far(R xi, R yi, R zi, const typename Vec4<R>::T& s, R& ax, R& ay, R& az,
                                          R& pt) {
@@ -87,40 +100,55 @@ __device__ __forceinline__ void pair_far(R xi, R yi, R zi, const typename Vec4<R
   pt -= mr;
 }
 
-// Softened pair (both particles' kernels, mean): returns the factor g-bar
-// multiplying -m d and the potential factor phi-bar multiplying m.
+// Candidate pair: softened when r < 2 max(h_i, h_j) (mean of both kernels),
+// unsoftened otherwise; the self pair contributes nothing.
 template <typename R>
-__device__ __forceinline__ void pair_soft(R r2, R hinvi, R hinvj, R& gbar, R& pbar) {
+__device__ __forceinline__ void pair_cand(R xi, R yi, R zi, R hinvi, R h2i, bool self,
+                                          const typename Vec4<R>::T& s, const typename Vec4<R>::T2& hh, R& ax,
+                                          R& ay, R& az, R& pt) {
+  const R dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
+  const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
   const R ri = (r2 > R(0)) ? rsq(r2) : R(0);
-  const R r = r2 * ri;
-  R gi, pi, gj, pj;
-  m4_kernel<R>(r * hinvi, hinvi, ri, gi, pi);
-  m4_kernel<R>(r * hinvj, hinvj, ri, gj, pj);
-  gbar = R(0.5) * (gi + gj);
-  pbar = R(0.5) * (pi + pj);
+  R g, phi;
+  if (r2 < fmax(h2i, hh.y)) {
+    const R r = r2 * ri;
+    R gi, pi, gj, pj;
+    m4_kernel<R>(r * hinvi, hinvi, ri, gi, pi);
+    m4_kernel<R>(r * hh.x, hh.x, ri, gj, pj);
+    g = R(0.5) * (gi + gj);
+    phi = R(0.5) * (pi + pj);
+  } else {
+    g = ri * ri * ri;
+    phi = -ri;
+  }
+  const R m = self ? R(0) : s.w;
+  const R mg = m * g;
+  ax = fma(-mg, dx, ax);
+  ay = fma(-mg, dy, ay);
+  az = fma(-mg, dz, az);
+  pt = fma(m, phi, pt);
 }
 
-// Sources are staged per warp, split once per source into those that may lie
-// inside the kernel of some target of the leaf (|x_j - s_L| < l_L +
-// 2 max(h_max,L, h_j), with a small safety factor) and those that cannot; the
-// latter take the unsoftened branch-free loop.
 template <bool F32> __host__ __device__ constexpr int p2p_warps() { return F32 ? P2P_WARPS : P2P_WARPS / 2; }
 
+// One warp per target leaf.  Sources: the particles of the leaf's neighbour
+// list, streamed 32 at a time over consecutive list entries (every lane
+// busy), moved to the target leaf's frame (FP32 form) and split once per
+// source into those that may lie inside the kernel of some target
+// (|x_j - s_L| < l_L + 2 max(h_max,L, h_j), with a small safety factor) and
+// those that cannot; the latter take the unsoftened branch-free loop.
 template <bool F32>
 __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
   using R = typename std::conditional<F32, float, double>::type;
   using V = typename Vec4<R>::T;
-  constexpr int NW = p2p_warps<F32>();           // warps per block (48 KB static limit)
-  constexpr int SB = P2P_SB;                     // staged sources per warp (>= 64, a full leaf)
+  using V2 = typename Vec4<R>::T2;
+  constexpr int NW = p2p_warps<F32>();
+  constexpr int SB = P2P_SB;
   __shared__ V s_far[NW][SB];
   __shared__ V s_near[NW][SB];
-  __shared__ R s_nhinv[NW][SB];
-  __shared__ R s_nh2[NW][SB];                   // (2h)^2 of the candidate
+  __shared__ V2 s_nhh[NW][SB];
   __shared__ int s_nidx[NW][SB];
   __shared__ R s_red[NW][4][32];
-  __shared__ V s_tgt[NW][64];            // targets: x, y, z, 1/h
-  __shared__ R s_acc[NW][64][4];                // softened part per target
-  __shared__ int s_q[NW][64];            // queued pairs: target << 16 | candidate
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
@@ -132,8 +160,6 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
     const int L = a.leaf_node[leaf];
     const int fL = a.nfirst[L], nL = a.ncount[L];
     const float4 hiL = a.geo_hi[L], loL = a.geo_lo[L];
-    // target leaf radius and largest smoothing length, with a safety factor
-    // covering the float32 rounding of the relative coordinates
     const R lL = (R)hiL.w * R(1.0001), hL = (R)loL.w * R(1.0001);
     const double cLx = F32 ? 0.0 : a.ncx[L], cLy = F32 ? 0.0 : a.ncy[L], cLz = F32 ? 0.0 : a.ncz[L];
     // lane -> (target slot, phase)
@@ -145,109 +171,118 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
     const int t1 = t0 + 32;
     const bool on0 = lane_on && t0 < nL;
     const bool on1 = lane_on && nL > 32 && t1 < nL;
-    R xi0 = R(0), yi0 = R(0), zi0 = R(0), hinvi0 = R(0);
-    R xi1 = R(0), yi1 = R(0), zi1 = R(0), hinvi1 = R(0);
-    if (on0) {
-      const int i = fL + t0;
+    R xi0 = R(0), yi0 = R(0), zi0 = R(0), hinvi0 = R(0), h2i0 = R(0);
+    R xi1 = R(0), yi1 = R(0), zi1 = R(0), hinvi1 = R(0), h2i1 = R(0);
+    auto load_target = [&](int i, R& x, R& y, R& z, R& hinv, R& h2) {
       if constexpr (F32) {
         const float4 p = a.prel[i];
-        xi0 = p.x; yi0 = p.y; zi0 = p.z;
-        hinvi0 = 1.0f / a.ph32[i];
+        const float2 hh = a.phh[i];
+        x = p.x; y = p.y; z = p.z; hinv = hh.x; h2 = hh.y;
       } else {
-        xi0 = a.px[i]; yi0 = a.py[i]; zi0 = a.pz[i];
-        hinvi0 = 1.0 / a.ph[i];
+        const double h = a.ph[i];
+        x = a.px[i]; y = a.py[i]; z = a.pz[i]; hinv = 1.0 / h; h2 = 4.0 * h * h;
       }
-    }
-    if (on1) {
-      const int i = fL + t1;
-      if constexpr (F32) {
-        const float4 p = a.prel[i];
-        xi1 = p.x; yi1 = p.y; zi1 = p.z;
-        hinvi1 = 1.0f / a.ph32[i];
-      } else {
-        xi1 = a.px[i]; yi1 = a.py[i]; zi1 = a.pz[i];
-        hinvi1 = 1.0 / a.ph[i];
-      }
-    }
-    // target table for the queued softened pairs
-    for (int t = lane; t < nL; t += 32) {
-      const int i = fL + t;
-      if constexpr (F32) {
-        const float4 p = a.prel[i];
-        s_tgt[warp][t] = make_float4(p.x, p.y, p.z, 1.0f / a.ph32[i]);
-      } else {
-        s_tgt[warp][t] = make_double4(a.px[i], a.py[i], a.pz[i], 1.0 / a.ph[i]);
-      }
-      s_acc[warp][t][0] = s_acc[warp][t][1] = s_acc[warp][t][2] = s_acc[warp][t][3] = R(0);
-    }
-    __syncwarp();
-    const R h2i0 = (hinvi0 > R(0)) ? R(4) / (hinvi0 * hinvi0) : R(0);
-    const R h2i1 = (hinvi1 > R(0)) ? R(4) / (hinvi1 * hinvi1) : R(0);
-    int nqp = 0;  // queued softened pairs
-    // unsoftened accumulators per slot
+    };
+    if (on0) load_target(fL + t0, xi0, yi0, zi0, hinvi0, h2i0);
+    if (on1) load_target(fL + t1, xi1, yi1, zi1, hinvi1, h2i1);
     R ax0 = R(0), ay0 = R(0), az0 = R(0), pt0 = R(0);
     R ax1 = R(0), ay1 = R(0), az1 = R(0), pt1 = R(0);
 
     const long long off = a.p2p_off[leaf];
     const int cnt = a.p2p_cnt[leaf];
-    int nfar = 0, nnear = 0, e = 0;
+    int nfar = 0, nnear = 0;
+    int e = 0;                 // next list entry to load
+    int tot = 0, pdone = 0;    // particles of the loaded entries / staged so far
+    int cum = 0, fS = 0;       // this lane's entry: first particle in the stream, first particle index
+    R ox = R(0), oy = R(0), oz = R(0);
     while (true) {
-      // stage whole source leaves while both buffers have room
-      while (e < cnt) {
-        const int S = a.arena[off + e];
-        const int fS = a.nfirst[S], nS = a.ncount[S];
-        if (nfar + nS > SB || nnear + nS > SB) break;
-        R ox = R(0), oy = R(0), oz = R(0);
-        if constexpr (F32) {
-          const float4 hS = a.geo_hi[S], lS = a.geo_lo[S];
-          ox = df_diff(hS.x, lS.x, hiL.x, loL.x);
-          oy = df_diff(hS.y, lS.y, hiL.y, loL.y);
-          oz = df_diff(hS.z, lS.z, hiL.z, loL.z);
+      const bool stream_left = (pdone < tot) || (e < cnt);
+      if (stream_left && pdone == tot) {
+        // next 32 list entries, one per lane: prefix sum of their particle counts
+        const int k = e + lane;
+        int nS = 0;
+        if (k < cnt) {
+          const int S = a.arena[off + k];
+          fS = a.nfirst[S];
+          nS = a.ncount[S];
+          if constexpr (F32) {
+            const float4 hS = a.geo_hi[S], lS = a.geo_lo[S];
+            ox = df_diff(hS.x, lS.x, hiL.x, loL.x);
+            oy = df_diff(hS.y, lS.y, hiL.y, loL.y);
+            oz = df_diff(hS.z, lS.z, hiL.z, loL.z);
+          }
         }
-        for (int j0 = 0; j0 < nS; j0 += 32) {
-          const int j = j0 + lane;
-          const bool valid = j < nS;
-          V v = {R(0), R(0), R(0), R(0)};
-          R h = R(1);
-          if (valid) {
-            const int i = fS + j;
-            if constexpr (F32) {
-              const float4 p = a.prel[i];
-              v = make_float4(p.x + ox, p.y + oy, p.z + oz, p.w);
-              h = a.ph32[i];
-            } else {
-              v = make_double4(a.px[i], a.py[i], a.pz[i], a.pm[i]);
-              h = a.ph[i];
-            }
-          }
-          // distance to the target leaf's centre
-          R rx = v.x, ry = v.y, rz = v.z;
-          if constexpr (!F32) {
-            rx -= cLx;
-            ry -= cLy;
-            rz -= cLz;
-          }
-          const R reach = lL + R(2) * fmax(hL, h * R(1.0001));
-          const bool near = valid && (fma(rx, rx, fma(ry, ry, rz * rz)) < reach * reach);
-          const unsigned bn = __ballot_sync(SFMM_FULL, near), bf = __ballot_sync(SFMM_FULL, valid && !near);
-          if (near) {
-            const int q = nnear + __popc(bn & lt);
-            s_near[warp][q] = v;
-            s_nhinv[warp][q] = R(1) / h;
-            s_nh2[warp][q] = R(4) * h * h;
-            s_nidx[warp][q] = fS + j;
-          } else if (valid) {
-            s_far[warp][nfar + __popc(bf & lt)] = v;
-          }
-          nnear += __popc(bn);
-          nfar += __popc(bf);
+        int incl = nS;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(SFMM_FULL, incl, o);
+          if (lane >= o) incl += y;
         }
-        ++e;
+        cum = incl - nS;
+        tot = __shfl_sync(SFMM_FULL, incl, 31);
+        pdone = 0;
+        e += 32;
       }
-      if (nfar == 0 && nnear == 0) break;
+      if (stream_left) {
+        // stage one window of up to 32 particles of the stream
+        const int p = pdone + lane;
+        const bool valid = p < tot;
+        int l = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int c = __shfl_sync(SFMM_FULL, cum, l + step);
+          if (c <= p) l += step;
+        }
+        const int c_l = __shfl_sync(SFMM_FULL, cum, l);
+        const int f_l = __shfl_sync(SFMM_FULL, fS, l);
+        const R ox_l = __shfl_sync(SFMM_FULL, ox, l), oy_l = __shfl_sync(SFMM_FULL, oy, l),
+                oz_l = __shfl_sync(SFMM_FULL, oz, l);
+        V v;
+        V2 hh;
+        int i = 0;
+        if (valid) {
+          i = f_l + (p - c_l);
+          if constexpr (F32) {
+            const float4 q = a.prel[i];
+            v = make_float4(q.x + ox_l, q.y + oy_l, q.z + oz_l, q.w);
+            hh = a.phh[i];
+          } else {
+            const double h = a.ph[i];
+            v = make_double4(a.px[i], a.py[i], a.pz[i], a.pm[i]);
+            hh = make_double2(1.0 / h, 4.0 * h * h);
+          }
+        } else {
+          v.x = v.y = v.z = v.w = R(0);
+          hh.x = hh.y = R(0);
+        }
+        R rx = v.x, ry = v.y, rz = v.z;
+        if constexpr (!F32) {
+          rx -= cLx;
+          ry -= cLy;
+          rz -= cLz;
+        }
+        // reach^2 = (l_L + 2 max(h_L, h_j))^2, with h_j from (2h_j)^2
+        // 2 h_j = sqrt((2 h_j)^2) via rsqrt: the 1.0001 factor covers its error
+        const R reach = lL + fmax(R(2) * hL, valid ? hh.y * rsq(hh.y) * R(1.0001) : R(0));
+        const bool near = valid && (fma(rx, rx, fma(ry, ry, rz * rz)) < reach * reach);
+        const unsigned bn = __ballot_sync(SFMM_FULL, near), bf = __ballot_sync(SFMM_FULL, valid && !near);
+        if (near) {
+          const int q = nnear + __popc(bn & lt);
+          s_near[warp][q] = v;
+          s_nhh[warp][q] = hh;
+          s_nidx[warp][q] = i;
+        } else if (valid) {
+          s_far[warp][nfar + __popc(bf & lt)] = v;
+        }
+        nnear += __popc(bn);
+        nfar += __popc(bf);
+        pdone += min(32, tot - pdone);
+      }
+      const bool last = !((pdone < tot) || (e < cnt));
+      if (!(nfar > SB - 32 || nnear > SB - 32 || last)) continue;
       __syncwarp();
-      // unsoftened sources
       if (lane_on) {
+        // unsoftened sources
         int j = ph;
         for (; j + nph < nfar; j += 2 * nph) {
           const V s0 = s_far[warp][j], s1 = s_far[warp][j + nph];
@@ -263,102 +298,19 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
           pair_far<R>(xi0, yi0, zi0, s0, ax0, ay0, az0, pt0);
           if (nL > 32) pair_far<R>(xi1, yi1, zi1, s0, ax1, ay1, az1, pt1);
         }
-      }
-      // one full batch of queued softened pairs, one per lane (queue <= 63)
-      auto drain32 = [&]() {
-        __syncwarp();
-        // one full batch: each lane one queued softened pair
-        const int qv = s_q[warp][nqp - 32 + lane];
-        __syncwarp();
-        const int tq = qv >> 16, jq = qv & 0xffff;
-        const V T = s_tgt[warp][tq];
-        const V S = s_near[warp][jq];
-        const R ddx = T.x - S.x, ddy = T.y - S.y, ddz = T.z - S.z;
-        R gb, pb;
-        pair_soft<R>(fma(ddx, ddx, fma(ddy, ddy, ddz * ddz)), T.w, s_nhinv[warp][jq], gb, pb);
-        const R mg = S.w * gb;
-        atomicAdd(&s_acc[warp][tq][0], -mg * ddx);
-        atomicAdd(&s_acc[warp][tq][1], -mg * ddy);
-        atomicAdd(&s_acc[warp][tq][2], -mg * ddz);
-        atomicAdd(&s_acc[warp][tq][3], S.w * pb);
-        nqp -= 32;
-      };
-      // candidates: exact per-pair kernel test; pairs outside both kernels take
-      // the unsoftened formula, pairs inside one are queued (self pairs drop out)
-      {
-        const int iters = (nnear + nph - 1) / nph;
-        for (int it = 0; it < iters; ++it) {
-          const int jn = it * nph + ph;
-          const bool vj = lane_on && jn < nnear;
-          const int jj = vj ? jn : 0;
-          const V s0 = s_near[warp][jj];
-          const R h2j = s_nh2[warp][jj];
-          const int ij = s_nidx[warp][jj];
-          bool soft;
-          {
-            const R dx = xi0 - s0.x, dy = yi0 - s0.y, dz = zi0 - s0.z;
-            const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            const bool live = vj && on0 && (ij != fL + t0);
-            soft = live && r2 < fmax(h2i0, h2j);
-            if (live && !soft) {
-              const R ri = rsq(r2);
-              const R mr = s0.w * ri;
-              const R mr3 = mr * (ri * ri);
-              ax0 = fma(-mr3, dx, ax0);
-              ay0 = fma(-mr3, dy, ay0);
-              az0 = fma(-mr3, dz, az0);
-              pt0 -= mr;
-            }
-          }
-          const unsigned bq = __ballot_sync(SFMM_FULL, soft);
-          if (soft) s_q[warp][nqp + __popc(bq & lt)] = (t0 << 16) | jj;
-          nqp += __popc(bq);
-          if (nqp >= 32) drain32();
-          if (nL > 32) {  // second target slot (leaves of 33..64 particles)
-            const R dx = xi1 - s0.x, dy = yi1 - s0.y, dz = zi1 - s0.z;
-            const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            const bool live = vj && on1 && (ij != fL + t1);
-            const bool soft1 = live && r2 < fmax(h2i1, h2j);
-            if (live && !soft1) {
-              const R ri = rsq(r2);
-              const R mr = s0.w * ri;
-              const R mr3 = mr * (ri * ri);
-              ax1 = fma(-mr3, dx, ax1);
-              ay1 = fma(-mr3, dy, ay1);
-              az1 = fma(-mr3, dz, az1);
-              pt1 -= mr;
-            }
-            const unsigned b1 = __ballot_sync(SFMM_FULL, soft1);
-            if (soft1) s_q[warp][nqp + __popc(b1 & lt)] = (t1 << 16) | jj;
-            nqp += __popc(b1);
-            if (nqp >= 32) drain32();
-          }
+        // candidates inside some kernel of the leaf
+        for (int jn = ph; jn < nnear; jn += nph) {
+          const V s0 = s_near[warp][jn];
+          const V2 hh = s_nhh[warp][jn];
+          const int ij = s_nidx[warp][jn];
+          pair_cand<R>(xi0, yi0, zi0, hinvi0, h2i0, ij == fL + t0, s0, hh, ax0, ay0, az0, pt0);
+          if (nL > 32) pair_cand<R>(xi1, yi1, zi1, hinvi1, h2i1, ij == fL + t1, s0, hh, ax1, ay1, az1, pt1);
         }
-      }
-      __syncwarp();
-      // drain the queue before the staged candidates are overwritten
-      if (nqp > 0) {
-        const int qv = (lane < nqp) ? s_q[warp][lane] : 0;
-        __syncwarp();
-        if (lane < nqp) {
-          const int tq = qv >> 16, jq = qv & 0xffff;
-          const V T = s_tgt[warp][tq];
-          const V S = s_near[warp][jq];
-          const R ddx = T.x - S.x, ddy = T.y - S.y, ddz = T.z - S.z;
-          R gb, pb;
-          pair_soft<R>(fma(ddx, ddx, fma(ddy, ddy, ddz * ddz)), T.w, s_nhinv[warp][jq], gb, pb);
-          const R mg = S.w * gb;
-          atomicAdd(&s_acc[warp][tq][0], -mg * ddx);
-          atomicAdd(&s_acc[warp][tq][1], -mg * ddy);
-          atomicAdd(&s_acc[warp][tq][2], -mg * ddz);
-          atomicAdd(&s_acc[warp][tq][3], S.w * pb);
-        }
-        nqp = 0;
       }
       __syncwarp();
       nfar = 0;
       nnear = 0;
-      if (e >= cnt) break;
+      if (last) break;
     }
     if (!on0) { ax0 = ay0 = az0 = pt0 = R(0); }
     if (!on1) { ax1 = ay1 = az1 = pt1 = R(0); }
@@ -377,7 +329,7 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
         R v[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          R sacc = s_acc[warp][t][c];
+          R sacc = R(0);
           for (int q = 0; q < nph; ++q) sacc += s_red[warp][c][q * ntl + lane];
           v[c] = sacc;
         }
@@ -487,6 +439,7 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   a.p2p_cnt = c->p2p_cnt.as<int>();
   a.prel = c->prel.as<float4>();
   a.ph32 = c->ph32.as<float>();
+  a.phh = c->phh.as<float2>();
   a.px = c->px.as<double>();
   a.py = c->py.as<double>();
   a.pz = c->pz.as<double>();
