@@ -166,7 +166,7 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->l2bits, &c->flags, &c->geo_hi, &c->geo_lo, &c->leaf_node, &c->isleaf, &c->Qd,
                     &c->Qf, &c->ring, &c->far, &c->arena, &c->p2p_off, &c->p2p_cnt, &c->counters,
                     &c->red_part, &c->dump, &c->nlu, &c->level_nodes, &c->level_off, &c->level_cur,
-                    &c->cf_arena, &c->cf_off, &c->cf_cnt, &c->Tnode};
+                    &c->cf_arena, &c->cf_off, &c->cf_cnt, &c->Tnode, &c->leaf_order};
   for (DevBuf* b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -234,8 +234,8 @@ int sfmm_build(sfmm_ctx* c, int64_t n, const double* pos, const double* mass, co
   int rc = build_tree(c, pos, mass, h);
   if (rc) return set_error(c, rc, "tree build failed");
   if ((rc = build_levels(c))) return set_error(c, rc, "level lists failed");
-  // level offsets to the host (the tree is at most 96 levels deep: keys and
-  // sorted positions give 95 distinguishing bits)
+  // internal-node level offsets to the host (the tree is at most 96 levels
+  // deep: keys and sorted positions give 95 distinguishing bits)
   const int ncopy = (int)std::min<int64_t>((int64_t)c->nnodes + 1, 130);
   c->h_level_off.assign(ncopy, 0);
   SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_off.data(), c->level_off.p, sizeof(int) * ncopy, cudaMemcpyDeviceToHost,
@@ -246,13 +246,18 @@ int sfmm_build(sfmm_ctx* c, int64_t n, const double* pos, const double* mass, co
   if (bits & (SFMM_ST_NONFINITE | SFMM_ST_NONPOSITIVE))
     return set_error(c, SFMM_ENONFINITE, "non-finite position/mass/h or non-positive mass/h");
   if (bits) return set_error(c, SFMM_ECUDA, "internal consistency check of the tree failed");
+  // internal nodes: nnodes - nleaves of them; the last internal level is the
+  // first depth whose offset reaches that count
+  const int nint = c->nnodes - c->nleaves;
   c->max_depth = -1;
-  for (int d = 0; d + 1 < (int)c->h_level_off.size(); ++d)
-    if (c->h_level_off[d + 1] >= c->nnodes) {
-      c->max_depth = d;
+  for (int d = 0; d < (int)c->h_level_off.size(); ++d)
+    if (c->h_level_off[d] >= nint) {
+      c->max_depth = d - 1;  // deepest level holding an internal node (-1: none)
       break;
     }
-  if (c->max_depth < 0) return set_error(c, SFMM_ESTACK, "tree deeper than 128 levels");
+  if (c->max_depth < -1 || (int)c->h_level_off.size() == 0 ||
+      c->h_level_off[std::min<int>((int)c->h_level_off.size() - 1, c->max_depth + 1)] < nint)
+    return set_error(c, SFMM_ESTACK, "tree deeper than 128 levels");
   c->h_level_off.resize(c->max_depth + 2);
   c->built = true;
   c->stats = sfmm_stats{};

@@ -22,42 +22,30 @@ SFMM_MOMOPS(3)
 SFMM_MOMOPS(4)
 #undef SFMM_MOMOPS
 
-// P2M: one warp per leaf, lanes over the leaf's particles, fixed-order
-// butterfly reduction (deterministic).
+// P2M: one thread per leaf (short FP64 sums; no cross-lane reduction).
 template <int P>
 __global__ void k_p2m(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
                       const int* __restrict__ ncount, const double* __restrict__ px, const double* __restrict__ py,
                       const double* __restrict__ pz, const double* __restrict__ pm, const double* __restrict__ ncx,
                       const double* __restrict__ ncy, const double* __restrict__ ncz, double* __restrict__ Qd) {
   constexpr int NQ = MomOps<P>::NQ;
-  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (w >= nleaves) return;
-  int v = leaf_node[w];
-  int f = nfirst[v], cnt = ncount[v];
-  double sx = ncx[v], sy = ncy[v], sz = ncz[v];
-  double q[NQ];
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nleaves) return;
+  const int v = leaf_node[q];
+  const int f = nfirst[v], cnt = ncount[v];
+  const double sx = ncx[v], sy = ncy[v], sz = ncz[v];
+  double acc[NQ];
 #pragma unroll
-  for (int k = 0; k < NQ; ++k) q[k] = 0.0;
-  for (int j = lane; j < cnt; j += 32) {
-    int i = f + j;
+  for (int k = 0; k < NQ; ++k) acc[k] = 0.0;
+  for (int i = f; i < f + cnt; ++i) {
     double mono[NQ];
     MomOps<P>::mono(px[i] - sx, py[i] - sy, pz[i] - sz, mono);
-    double m = pm[i];
+    const double m = pm[i];
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) q[k] = fma(m, mono[k], q[k]);
+    for (int k = 0; k < NQ; ++k) acc[k] = fma(m, mono[k], acc[k]);
   }
 #pragma unroll
-  for (int k = 0; k < NQ; ++k) {
-    double s = q[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(SFMM_FULL, s, o);
-    q[k] = s;
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NQ; ++k) Qd[(int64_t)v * NQ + k] = q[k];
-  }
+  for (int k = 0; k < NQ; ++k) Qd[(int64_t)v * NQ + k] = acc[k];
 }
 
 // M2M bottom-up: the second child to finish translates both children.
@@ -109,7 +97,7 @@ static int moments_p(sfmm_ctx* c) {
   const int nqs = (NQ + 3) & ~3;
   if ((rc = c->Qf.ensure(sizeof(float) * (size_t)nn * nqs))) return rc;
   cudaStream_t st = c->stream;
-  k_p2m<P><<<(unsigned)(((int64_t)nl * 32 + 127) / 128), 128, 0, st>>>(
+  k_p2m<P><<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(
       nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(), c->py.as<double>(),
       c->pz.as<double>(), c->pm.as<double>(), c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
       c->Qd.as<double>());

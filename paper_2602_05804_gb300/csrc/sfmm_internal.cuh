@@ -38,7 +38,7 @@ struct sfmm_ctx {
   int moments_order = -1;  // order of the cached moments (-1: none)
   int walk_mode = 0;        // 0: per-leaf replay (Algorithm 1), 1: per-node shared pairs
   int max_depth = 0;
-  std::vector<int> h_level_off;  // host copy, max_depth + 2 entries
+  std::vector<int> h_level_off;  // host copy: internal nodes per depth, max_depth + 2 entries
 
   // inputs staged from host (sfmm_solve_host)
   DevBuf in_pos, in_mass, in_h;
@@ -64,7 +64,8 @@ struct sfmm_ctx {
   DevBuf geo_hi, geo_lo;        // float4 walk records
   DevBuf leaf_node, isleaf;
   DevBuf nlu;                   // leaves under each node
-  DevBuf level_nodes, level_off, level_cur;  // nodes grouped by depth
+  DevBuf level_nodes, level_off, level_cur;  // internal nodes grouped by depth
+  DevBuf leaf_order;            // leaves by depth, shallowest first
   DevBuf Qd, Qf;                // scaled moments float64 [nn x NQ], float32 [nn x NQS]
 
   // gravity

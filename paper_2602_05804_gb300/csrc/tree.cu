@@ -447,6 +447,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// One thread per leaf (the FP64 sums of a leaf are short; warp reductions in
+// FP64 would cost more than the sums themselves).
 __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
                             const int* __restrict__ ncount, const double* __restrict__ px,
                             const double* __restrict__ py, const double* __restrict__ pz,
@@ -454,15 +456,13 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
                             double* __restrict__ ncx, double* __restrict__ ncy, double* __restrict__ ncz,
                             double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ pnode,
                             int* __restrict__ nlu) {
-  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (w >= nleaves) return;
-  int v = leaf_node[w];
-  int f = nfirst[v], cnt = ncount[v];
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nleaves) return;
+  const int v = leaf_node[q];
+  const int f = nfirst[v], cnt = ncount[v];
   double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, hm = 0.0;
-  for (int k = lane; k < cnt; k += 32) {
-    int i = f + k;
-    double m = pm[i];
+  for (int i = f; i < f + cnt; ++i) {
+    const double m = pm[i];
     M = dadd(M, m);
     sx = dadd(sx, dmul(m, px[i]));
     sy = dadd(sy, dmul(m, py[i]));
@@ -470,20 +470,12 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
     hm = fmax(hm, ph[i]);
     pnode[i] = v;
   }
-  M = warp_sum_d(M);
-  sx = warp_sum_d(sx);
-  sy = warp_sum_d(sy);
-  sz = warp_sum_d(sz);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) hm = fmax(hm, __shfl_xor_sync(SFMM_FULL, hm, o));
-  if (lane == 0) {
-    nmass[v] = M;
-    ncx[v] = __ddiv_rn(sx, M);
-    ncy[v] = __ddiv_rn(sy, M);
-    ncz[v] = __ddiv_rn(sz, M);
-    nhmax[v] = hm;
-    nlu[v] = 1;
-  }
+  nmass[v] = M;
+  ncx[v] = __ddiv_rn(sx, M);
+  ncy[v] = __ddiv_rn(sy, M);
+  ncz[v] = __ddiv_rn(sz, M);
+  nhmax[v] = hm;
+  nlu[v] = 1;
 }
 
 // Bottom-up: the second child to finish computes its parent.
@@ -588,18 +580,31 @@ __global__ void k_depth(int nn, const int* __restrict__ nparent, int* __restrict
   depth[v] = d;
 }
 
-// Nodes grouped by depth (level lists for the per-node walk).
-__global__ void k_level_count(int nn, const int* __restrict__ depth, uint32_t* __restrict__ cnt) {
+// Internal nodes grouped by depth (level lists for the per-node walk), and
+// the leaves ordered by depth, shallowest first (the per-node walk processes
+// all leaves in one launch; shallow leaves run the longest lowering).
+// Warp-aggregated counting: one atomic per (warp, depth) group.
+__global__ void k_level_count(int nn, const int* __restrict__ depth, const int* __restrict__ nright,
+                              uint32_t* __restrict__ cnt_int, uint32_t* __restrict__ cnt_leaf) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < nn) atomicAdd(&cnt[depth[v]], 1u);
+  const bool ok = v < nn;
+  const int d = ok ? depth[v] : -1;
+  const bool leaf = ok && nright[v] < 0;
+  const int key = ok ? (2 * d + (leaf ? 1 : 0)) : -1;
+  const unsigned grp = __match_any_sync(SFMM_FULL, key);
+  if (ok && (__ffs(grp) - 1) == (int)(threadIdx.x & 31))
+    atomicAdd(leaf ? &cnt_leaf[d] : &cnt_int[d], (unsigned)__popc(grp));
 }
 
-__global__ void k_level_scatter(int nn, const int* __restrict__ depth, const uint32_t* __restrict__ off,
-                                uint32_t* __restrict__ cur, int* __restrict__ level_nodes) {
+__global__ void k_level_scatter(int nn, const int* __restrict__ depth, const int* __restrict__ nright,
+                                const uint32_t* __restrict__ off_int, const uint32_t* __restrict__ off_leaf,
+                                uint32_t* __restrict__ cur_int, uint32_t* __restrict__ cur_leaf,
+                                int* __restrict__ level_nodes, int* __restrict__ leaf_order) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nn) return;
-  int d = depth[v];
-  level_nodes[off[d] + atomicAdd(&cur[d], 1u)] = v;
+  const int d = depth[v];
+  if (nright[v] < 0) leaf_order[off_leaf[d] + atomicAdd(&cur_leaf[d], 1u)] = v;
+  else level_nodes[off_int[d] + atomicAdd(&cur_int[d], 1u)] = v;
 }
 
 static inline unsigned nblk(int64_t n, int nt) { return (unsigned)((n + nt - 1) / nt); }
@@ -608,19 +613,25 @@ int build_levels(sfmm_ctx* c) {
   const int nn = c->nnodes;
   int rc;
   if ((rc = compute_depth(c))) return rc;
-  // depth < nn always; counts sized for the worst case
-  if ((rc = c->level_off.ensure(sizeof(uint32_t) * ((size_t)nn + 2)))) return rc;
-  if ((rc = c->level_cur.ensure(sizeof(uint32_t) * ((size_t)nn + 2)))) return rc;
+  // depth < nn always; counts sized for the worst case.  Layout of level_off:
+  // [0, nn + 1) internal-node offsets by depth, [nn + 1, 2 nn + 2) leaf offsets
+  const size_t nc = (size_t)nn + 1;
+  if ((rc = c->level_off.ensure(sizeof(uint32_t) * 2 * (nc + 1)))) return rc;
+  if ((rc = c->level_cur.ensure(sizeof(uint32_t) * 2 * (nc + 1)))) return rc;
   if ((rc = c->level_nodes.ensure(sizeof(int) * (size_t)nn))) return rc;
+  if ((rc = c->leaf_order.ensure(sizeof(int) * (size_t)c->nleaves))) return rc;
   cudaStream_t st = c->stream;
-  SFMM_CUDA_TRY(cudaMemsetAsync(c->level_off.p, 0, sizeof(uint32_t) * ((size_t)nn + 2), st));
-  SFMM_CUDA_TRY(cudaMemsetAsync(c->level_cur.p, 0, sizeof(uint32_t) * ((size_t)nn + 2), st));
-  k_level_count<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->level_off.as<uint32_t>());
+  uint32_t* off = c->level_off.as<uint32_t>();
+  uint32_t* cur = c->level_cur.as<uint32_t>();
+  SFMM_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(uint32_t) * 2 * (nc + 1), st));
+  SFMM_CUDA_TRY(cudaMemsetAsync(cur, 0, sizeof(uint32_t) * 2 * (nc + 1), st));
+  k_level_count<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->nright.as<int>(), off, off + nc);
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
-  if ((rc = exclusive_scan_u32(c, c->level_off.as<uint32_t>(), (int64_t)nn + 1, nullptr))) return rc;
-  k_level_scatter<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->level_off.as<uint32_t>(),
-                                                 c->level_cur.as<uint32_t>(), c->level_nodes.as<int>());
+  if ((rc = exclusive_scan_u32(c, off, (int64_t)nc, nullptr))) return rc;
+  if ((rc = exclusive_scan_u32(c, off + nc, (int64_t)nc, nullptr))) return rc;
+  k_level_scatter<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->nright.as<int>(), off, off + nc, cur,
+                                                 cur + nc, c->level_nodes.as<int>(), c->leaf_order.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   return SFMM_OK;
@@ -773,7 +784,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   const int nl = c->nleaves;
 
   // S4 geometry
-  k_leaf_geom<<<nblk((int64_t)nl * 32, 256), 256, 0, st>>>(
+  k_leaf_geom<<<nblk(nl, 128), 128, 0, st>>>(
       nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
       c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
       c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),

@@ -24,7 +24,7 @@ struct LevelArgs {
   const int* nparent;
   const int* nlu;
   const uint32_t* leaf_index;  // exclusive scan of leaf flags: leaf number of a leaf node
-  const int* cf_in;            // child frontiers written by the previous level
+  const int* cf_in;            // opened lists of the internal nodes
   const long long* cf_off;
   const int* cf_cnt;
   int* cf_out;
@@ -381,19 +381,20 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     long long arena_cap = c->list_capacity > 0 ? c->list_capacity : (long long)nl * 96 + 1024;
     if ((rc = c->arena.ensure(sizeof(int) * (size_t)arena_cap))) return rc;
     arena_cap = (long long)(c->arena.bytes / sizeof(int));
-    long long cf_cap = c->cf_capacity > 0 ? c->cf_capacity : (long long)nn * 64 + 4096;
-    if ((rc = c->cf_arena.ensure(sizeof(int) * 2 * (size_t)cf_cap))) return rc;
-    cf_cap = (long long)(c->cf_arena.bytes / sizeof(int) / 2);
-    if ((rc = c->cf_off.ensure(sizeof(long long) * 2 * (size_t)nn))) return rc;
-    if ((rc = c->cf_cnt.ensure(sizeof(int) * 2 * (size_t)nn))) return rc;
+    // the opened lists of every internal node are kept until the leaves run
+    long long cf_cap = c->cf_capacity > 0 ? c->cf_capacity : (long long)nn * 256 + 4096;
+    if ((rc = c->cf_arena.ensure(sizeof(int) * (size_t)cf_cap))) return rc;
+    cf_cap = (long long)(c->cf_arena.bytes / sizeof(int));
+    if ((rc = c->cf_off.ensure(sizeof(long long) * (size_t)nn))) return rc;
+    if ((rc = c->cf_cnt.ensure(sizeof(int) * (size_t)nn))) return rc;
     if ((rc = c->Tnode.ensure((F32 ? 2 * sizeof(float) : sizeof(double)) * (size_t)nn * tstride))) return rc;
     if ((rc = c->p2p_off.ensure(sizeof(long long) * (size_t)nl))) return rc;
     if ((rc = c->p2p_cnt.ensure(sizeof(int) * (size_t)nl))) return rc;
-    const int nlev = c->max_depth + 1;
-    if ((rc = c->counters.ensure(sizeof(unsigned long long) * (16 + 2 * (size_t)nlev)))) return rc;
+    const int nlev = c->max_depth + 1;  // levels holding internal nodes
+    if ((rc = c->counters.ensure(sizeof(unsigned long long) * (20 + 2 * (size_t)nlev)))) return rc;
     if ((rc = c->far.ensure((F32 ? sizeof(float4) : 4 * sizeof(double)) * (size_t)c->n))) return rc;
     unsigned long long* ctr = c->counters.as<unsigned long long>();
-    SFMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * (16 + 2 * (size_t)nlev), c->stream));
+    SFMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * (20 + 2 * (size_t)nlev), c->stream));
 
     LevelArgs la{};
     WalkArgs& a = la.w;
@@ -430,7 +431,6 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     a.theta = theta;
     a.theta_f = (float)theta;
     a.theta2_f = (float)(theta * theta);
-    la.level_nodes = c->level_nodes.as<int>();
     la.nparent = c->nparent.as<int>();
     la.nlu = c->nlu.as<int>();
     la.leaf_index = c->isleaf.as<uint32_t>();
@@ -438,23 +438,29 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     la.T32 = c->Tnode.as<float>();
     la.T64 = c->Tnode.as<double>();
     la.tstride = tstride;
-    int* cfa = c->cf_arena.as<int>();
-    long long* cfo = c->cf_off.as<long long>();
-    int* cfc = c->cf_cnt.as<int>();
-    for (int k = 0; k < nlev; ++k) {
-      const int pin = (k + 1) & 1, pout = k & 1;
+    la.cf_in = c->cf_arena.as<int>();
+    la.cf_off = c->cf_off.as<long long>();
+    la.cf_cnt = c->cf_cnt.as<int>();
+    la.cf_out = c->cf_arena.as<int>();
+    la.cf_off_out = c->cf_off.as<long long>();
+    la.cf_cnt_out = c->cf_cnt.as<int>();
+    la.cf_counter = ctr + 16;
+    // internal nodes level by level (each needs its parent's opened list and
+    // coefficients), then every leaf in one launch, shallowest first
+    for (int k = 0; k <= nlev; ++k) {
+      const bool leaves = (k == nlev);
       la.level = k;
-      la.level_begin = c->h_level_off[k];
-      la.level_count = c->h_level_off[k + 1] - c->h_level_off[k];
+      if (leaves) {
+        la.level_nodes = c->leaf_order.as<int>();
+        la.level_begin = 0;
+        la.level_count = nl;
+      } else {
+        la.level_nodes = c->level_nodes.as<int>();
+        la.level_begin = c->h_level_off[k];
+        la.level_count = c->h_level_off[k + 1] - c->h_level_off[k];
+      }
       if (la.level_count <= 0) continue;
-      la.cf_in = cfa + (size_t)pin * cf_cap;
-      la.cf_off = cfo + (size_t)pin * nn;
-      la.cf_cnt = cfc + (size_t)pin * nn;
-      la.cf_out = cfa + (size_t)pout * cf_cap;
-      la.cf_off_out = cfo + (size_t)pout * nn;
-      la.cf_cnt_out = cfc + (size_t)pout * nn;
-      la.cf_counter = ctr + 16 + 2 * k;
-      a.leaf_counter = reinterpret_cast<int*>(ctr + 16 + 2 * k + 1);
+      a.leaf_counter = reinterpret_cast<int*>(ctr + 18 + 2 * k);
       const int blocks = min(max_blocks, (la.level_count + WALK_WARPS - 1) / WALK_WARPS);
       k_walk_level<P, F32><<<blocks, WALK_NT, 0, c->stream>>>(la);
       ++c->nlaunch;
