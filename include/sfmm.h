@@ -104,11 +104,11 @@ int sfmm_set_stream(sfmm_ctx* ctx, void* stream);
  *                    default 0 (sum over j != i as in Eq. directsum)
  *   "ring_capacity"  walk frontier entries per warp (power of two, >= 256)
  *   "list_capacity"  P2P list arena entries (0 = automatic)
- *   "walk"           0 (default): each leaf replays the walk of its branch
- *                    (Algorithm 1 as printed); 1: each node's pairs are
- *                    evaluated once and shared by the leaves below it (the
- *                    caching of shared interactions proposed in Sect. 5);
- *                    same interactions, same results up to summation order
+ *   "walk"           1 (default): each node's pairs are evaluated once and
+ *                    shared by the leaves below it (the caching of shared
+ *                    interactions proposed in Sect. 5); 0: each leaf replays
+ *                    the walk of its branch (Algorithm 1 as printed); same
+ *                    interactions, same results up to summation order
  *   "profile"        1 records per-stage device times into the stats
  * Errors: EINVAL (unknown key or out-of-range value). */
 int sfmm_set_option(sfmm_ctx* ctx, const char* key, double value);

@@ -36,7 +36,7 @@ struct sfmm_ctx {
   int leaf_size = 0;
   int32_t nnodes = 0, nleaves = 0;
   int moments_order = -1;  // order of the cached moments (-1: none)
-  int walk_mode = 0;        // 0: per-leaf replay (Algorithm 1), 1: per-node shared pairs
+  int walk_mode = 1;        // 1: per-node shared pairs (default), 0: per-leaf replay (Algorithm 1)
   int max_depth = 0;
   std::vector<int> h_level_off;  // host copy: internal nodes per depth, max_depth + 2 entries
 
