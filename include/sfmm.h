@@ -142,6 +142,31 @@ int sfmm_build(sfmm_ctx* ctx, int64_t n, const double* pos, const double* mass, 
  * Errors: ESTATE (no build), EINVAL, ESTACK, ECAPACITY, ENOMEM, ECUDA. */
 int sfmm_gravity(sfmm_ctx* ctx, double theta, int order, double* acc, double* pot);
 
+/* Build one tree over a batch of nsys independent particle systems packed
+ * back to back (survey row S10; not in the paper): system s owns particles
+ * [offsets[s], offsets[s+1]).  Each system gets its own bounding box, Morton
+ * keys and leaf size; the combined sort orders particles by (system, key,
+ * input index) and nodes spanning several systems are always split and never
+ * walked, so each system's subtree equals the tree sfmm_build would give it
+ * and systems never interact.  All later calls then treat every system in
+ * the same kernel launches.
+ *   nsys in [1, 65536];  offsets HOST, nsys + 1 int64, offsets[0] = 0,
+ *   strictly increasing, offsets[nsys] = total n <= 2^31 - 2;
+ *   pos/mass/h device, packed as for sfmm_build;
+ *   leaf_size HOST, nsys ints in [1, 64], or NULL for 16 everywhere.
+ * Errors: as sfmm_build. */
+int sfmm_build_batch(sfmm_ctx* ctx, int nsys, const int64_t* offsets, const double* pos, const double* mass,
+                     const double* h, const int* leaf_size);
+
+/* Gravity of every system of the last build (batch or single), same
+ * arguments, layout (packed caller order) and errors as sfmm_gravity. */
+int sfmm_gravity_batch(sfmm_ctx* ctx, double theta, int order, double* acc, double* pot);
+
+/* Per-system sums of the last gravity call into HOST out[nsys x 5]:
+ * sum m a (3), sum |m a| (componentwise), W = 1/2 sum m Phi.
+ * Errors: ESTATE, EINVAL (nsys differs from the build). */
+int sfmm_batch_sums(const sfmm_ctx* ctx, int nsys, double* out);
+
 /* Whole solve from HOST buffers: copies the inputs to the device, builds,
  * runs the gravity and copies the results back, all on the context's stream.
  * Same arguments and errors as sfmm_build + sfmm_gravity, but every pointer

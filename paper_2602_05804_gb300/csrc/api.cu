@@ -166,7 +166,8 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->l2bits, &c->flags, &c->geo_hi, &c->geo_lo, &c->leaf_node, &c->isleaf, &c->Qd,
                     &c->Qf, &c->ring, &c->far, &c->arena, &c->p2p_off, &c->p2p_cnt, &c->counters,
                     &c->red_part, &c->dump, &c->nlu, &c->level_nodes, &c->level_off, &c->level_cur,
-                    &c->cf_arena, &c->cf_off, &c->cf_cnt, &c->Tnode, &c->leaf_order};
+                    &c->cf_arena, &c->cf_off, &c->cf_cnt, &c->Tnode, &c->leaf_order, &c->sys_off,
+                    &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_leaf_off, &c->sys_sums};
   for (DevBuf* b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -220,52 +221,106 @@ int sfmm_set_option(sfmm_ctx* c, const char* key, double v) {
   return SFMM_OK;
 }
 
-int sfmm_build(sfmm_ctx* c, int64_t n, const double* pos, const double* mass, const double* h, int leaf_size) {
-  if (check_ctx(c)) return SFMM_EINVAL;
-  if (n < 1 || n > ((int64_t)1 << 31) - 2) return set_error(c, SFMM_EINVAL, "n must be in [1, 2^31 - 2]");
-  if (!pos || !mass || !h) return set_error(c, SFMM_EINVAL, "NULL input pointer");
-  if (leaf_size < 1 || leaf_size > 64) return set_error(c, SFMM_EINVAL, "leaf_size must be in [1, 64]");
-  DeviceGuard g(c->device);
+}  // extern "C"
+
+namespace {
+
+// Build for nsys >= 1 systems packed back to back (h_sys_off / h_sys_lsz set).
+int build_common(sfmm_ctx* c, const double* pos, const double* mass, const double* h) {
   c->built = false;
   c->moments_order = -1;
-  c->n = n;
-  c->leaf_size = leaf_size;
+  int rc;
+  if ((rc = c->sys_off.ensure(sizeof(int) * ((size_t)c->nsys + 1))) ||
+      (rc = c->sys_lsz.ensure(sizeof(int) * (size_t)c->nsys)))
+    return set_error(c, rc, "allocation failed");
+  {
+    std::vector<int> off32(c->h_sys_off.begin(), c->h_sys_off.end());
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->sys_off.p, off32.data(), sizeof(int) * off32.size(), cudaMemcpyHostToDevice,
+                                  c->stream));
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->sys_lsz.p, c->h_sys_lsz.data(), sizeof(int) * c->h_sys_lsz.size(),
+                                  cudaMemcpyHostToDevice, c->stream));
+    // the host vectors must live until the copies have run: synchronise below
+    SFMM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
   if (c->profile) cudaEventRecord(c->ev[0], c->stream);
-  int rc = build_tree(c, pos, mass, h);
+  rc = build_tree(c, pos, mass, h);
   if (rc) return set_error(c, rc, "tree build failed");
   if ((rc = build_levels(c))) return set_error(c, rc, "level lists failed");
-  // internal-node level offsets to the host (the tree is at most 96 levels
-  // deep: keys and sorted positions give 95 distinguishing bits)
+  // walkable internal-node level offsets to the host (the tree is at most 128
+  // levels deep: system, key and position bits distinguish every particle)
   const int ncopy = (int)std::min<int64_t>((int64_t)c->nnodes + 1, 130);
   c->h_level_off.assign(ncopy, 0);
+  uint32_t h_tot = 0;
   SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_off.data(), c->level_off.p, sizeof(int) * ncopy, cudaMemcpyDeviceToHost,
                                 c->stream));
+  SFMM_CUDA_TRY(cudaMemcpyAsync(&h_tot, c->level_off.as<uint32_t>() + 2 * ((size_t)c->nnodes + 1), sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, c->stream));
   if (c->profile) cudaEventRecord(c->ev[1], c->stream);
   int bits = 0;
   if ((rc = sync_status(c, &bits))) return rc;
   if (bits & (SFMM_ST_NONFINITE | SFMM_ST_NONPOSITIVE))
     return set_error(c, SFMM_ENONFINITE, "non-finite position/mass/h or non-positive mass/h");
   if (bits) return set_error(c, SFMM_ECUDA, "internal consistency check of the tree failed");
-  // internal nodes: nnodes - nleaves of them; the last internal level is the
-  // first depth whose offset reaches that count
-  const int nint = c->nnodes - c->nleaves;
-  c->max_depth = -1;
+  // deepest level holding a walkable internal node (-1: none)
+  const int nint = (int)h_tot;
+  c->max_depth = -2;
   for (int d = 0; d < (int)c->h_level_off.size(); ++d)
     if (c->h_level_off[d] >= nint) {
-      c->max_depth = d - 1;  // deepest level holding an internal node (-1: none)
+      c->max_depth = d - 1;
       break;
     }
-  if (c->max_depth < -1 || (int)c->h_level_off.size() == 0 ||
-      c->h_level_off[std::min<int>((int)c->h_level_off.size() - 1, c->max_depth + 1)] < nint)
-    return set_error(c, SFMM_ESTACK, "tree deeper than 128 levels");
+  if (c->max_depth < -1) return set_error(c, SFMM_ESTACK, "tree deeper than 128 levels");
   c->h_level_off.resize(c->max_depth + 2);
   c->built = true;
   c->stats = sfmm_stats{};
-  c->stats.n = n;
+  c->stats.n = c->n;
   c->stats.nnodes = c->nnodes;
   c->stats.nleaves = c->nleaves;
   if (c->profile) c->stats.ms_build = elapsed(c->ev[0], c->ev[1]);
   return SFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfmm_build(sfmm_ctx* c, int64_t n, const double* pos, const double* mass, const double* h, int leaf_size) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (n < 1 || n > ((int64_t)1 << 31) - 2) return set_error(c, SFMM_EINVAL, "n must be in [1, 2^31 - 2]");
+  if (!pos || !mass || !h) return set_error(c, SFMM_EINVAL, "NULL input pointer");
+  if (leaf_size < 1 || leaf_size > 64) return set_error(c, SFMM_EINVAL, "leaf_size must be in [1, 64]");
+  DeviceGuard g(c->device);
+  c->n = n;
+  c->leaf_size = leaf_size;
+  c->nsys = 1;
+  c->h_sys_off.assign({0, n});
+  c->h_sys_lsz.assign({leaf_size});
+  return build_common(c, pos, mass, h);
+}
+
+int sfmm_build_batch(sfmm_ctx* c, int nsys, const int64_t* offsets, const double* pos, const double* mass,
+                     const double* h, const int* leaf_size) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (nsys < 1 || nsys > 65536 || !offsets) return set_error(c, SFMM_EINVAL, "nsys must be in [1, 65536]");
+  if (!pos || !mass || !h) return set_error(c, SFMM_EINVAL, "NULL input pointer");
+  if (offsets[0] != 0) return set_error(c, SFMM_EINVAL, "offsets[0] must be 0");
+  for (int s = 0; s < nsys; ++s)
+    if (offsets[s + 1] <= offsets[s]) return set_error(c, SFMM_EINVAL, "every system needs at least one particle");
+  const int64_t n = offsets[nsys];
+  if (n > ((int64_t)1 << 31) - 2) return set_error(c, SFMM_EINVAL, "total n must be <= 2^31 - 2");
+  std::vector<int> lsz(nsys, 16);
+  if (leaf_size)
+    for (int s = 0; s < nsys; ++s) {
+      if (leaf_size[s] < 1 || leaf_size[s] > 64) return set_error(c, SFMM_EINVAL, "leaf sizes must be in [1, 64]");
+      lsz[s] = leaf_size[s];
+    }
+  DeviceGuard g(c->device);
+  c->n = n;
+  c->leaf_size = *std::max_element(lsz.begin(), lsz.end());
+  c->nsys = nsys;
+  c->h_sys_off.assign(offsets, offsets + nsys + 1);
+  c->h_sys_lsz = lsz;
+  return build_common(c, pos, mass, h);
 }
 
 int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot) {
@@ -288,6 +343,7 @@ int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot)
   if (c->profile) cudaEventRecord(c->ev[5], st);
   double* red = nullptr;
   if ((rc = run_reduce(c, &red))) return set_error(c, rc, "reduction failed");
+  if (c->nsys > 1 && (rc = run_reduce_systems(c))) return set_error(c, rc, "reduction failed");
   if (c->profile) cudaEventRecord(c->ev[6], st);
   cudaError_t e = cudaMemcpyAsync(c->h_scalars + 16, red, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return set_error(c, SFMM_ECUDA, cudaGetErrorString(e));
@@ -307,6 +363,30 @@ int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot)
     c->stats.ms_reduce = elapsed(c->ev[5], c->ev[6]);
     c->stats.ms_gravity = elapsed(c->ev[2], c->ev[6]);
   }
+  return SFMM_OK;
+}
+
+int sfmm_gravity_batch(sfmm_ctx* c, double theta, int order, double* acc, double* pot) {
+  return sfmm_gravity(c, theta, order, acc, pot);
+}
+
+int sfmm_batch_sums(const sfmm_ctx* cc, int nsys, double* out) {
+  sfmm_ctx* c = const_cast<sfmm_ctx*>(cc);
+  if (check_ctx(c) || !out) return SFMM_EINVAL;
+  if (!c->built) return SFMM_ESTATE;
+  if (nsys != c->nsys) return set_error(c, SFMM_EINVAL, "nsys differs from the built batch");
+  DeviceGuard g(c->device);
+  SFMM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (c->nsys == 1) {
+    out[0] = c->stats.momentum[0];
+    out[1] = c->stats.momentum[1];
+    out[2] = c->stats.momentum[2];
+    out[3] = c->stats.abs_momentum;
+    out[4] = c->stats.W;
+    return SFMM_OK;
+  }
+  if (!c->sys_sums.p) return SFMM_ESTATE;
+  SFMM_CUDA_TRY(cudaMemcpy(out, c->sys_sums.p, sizeof(double) * 5 * (size_t)nsys, cudaMemcpyDeviceToHost));
   return SFMM_OK;
 }
 

@@ -421,6 +421,37 @@ __global__ void k_reduce_final(int nparts, const double* __restrict__ part, doub
   if (threadIdx.x < 5) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// Per-system sums of a batch: one block per system over its leaf range.
+__global__ void k_reduce_sys(const int* __restrict__ sys_leaf_off, const double* __restrict__ leafsum,
+                             double* __restrict__ out) {
+  __shared__ double sh[5][RED_NT];
+  const int sys = blockIdx.x;
+  const int lo = sys_leaf_off[sys], hi = sys_leaf_off[sys + 1];
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int q = lo + threadIdx.x; q < hi; q += RED_NT)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) s[c] += leafsum[5 * (size_t)q + c];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = s[c];
+  __syncthreads();
+  for (int w = RED_NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) out[5 * (size_t)sys + threadIdx.x] = (threadIdx.x == 4) ? 0.5 * sh[4][0] : sh[threadIdx.x][0];
+}
+
+int run_reduce_systems(sfmm_ctx* c) {
+  int rc;
+  if ((rc = c->sys_sums.ensure(sizeof(double) * 5 * (size_t)c->nsys))) return rc;
+  k_reduce_sys<<<c->nsys, RED_NT, 0, c->stream>>>(c->sys_leaf_off.as<int>(), c->red_part.as<double>(),
+                                                 c->sys_sums.as<double>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
+  return SFMM_OK;
+}
+
 int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   const int nl = c->nleaves;
   int rc;

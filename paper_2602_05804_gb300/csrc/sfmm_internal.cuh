@@ -34,6 +34,14 @@ struct sfmm_ctx {
   bool built = false;
   int64_t n = 0;
   int leaf_size = 0;
+  // systems of a batch (nsys = 1 for a single particle set): particle offsets
+  // and leaf sizes on host and device; the system of each particle; the root
+  // node of each system; each node's parent for the walk (-1 at a system
+  // root, -2 for nodes spanning several systems); leaf offsets per system
+  int nsys = 1;
+  std::vector<int64_t> h_sys_off;
+  std::vector<int> h_sys_lsz;
+  DevBuf sys_off, sys_lsz, psys, sys_root, wparent, sys_leaf_off, sys_sums;
   int32_t nnodes = 0, nleaves = 0;
   int moments_order = -1;  // order of the cached moments (-1: none)
   int walk_mode = 1;        // 1: per-node shared pairs (default), 0: per-leaf replay (Algorithm 1)
@@ -107,6 +115,7 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
 // p2p.cu
 int run_p2p(sfmm_ctx* c, double* acc, double* pot);
 int run_reduce(sfmm_ctx* c, double** out_dev);  // device pointer of the 5 sums
+int run_reduce_systems(sfmm_ctx* c);             // per-system sums (batches)
 
 int check_status(sfmm_ctx* c);
 int sync_status(sfmm_ctx* c, int* bits);

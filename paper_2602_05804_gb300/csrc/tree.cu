@@ -145,6 +145,73 @@ __global__ void k_bbox_partial(const double* __restrict__ pos, const double* __r
   if (bad) atomicOr(status, bad);
 }
 
+// Per-system bounding boxes for a batch: one block per system; bbox[8 s ..].
+__global__ void k_bbox_seg(const double* __restrict__ pos, const double* __restrict__ mass,
+                           const double* __restrict__ h, const int* __restrict__ off, double* __restrict__ bbox,
+                           int* __restrict__ status) {
+  const int sys = blockIdx.x;
+  const int lo = off[sys], hi = off[sys + 1];
+  double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  int bad = 0;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double v = pos[3 * (int64_t)i + c];
+      if (!isfinite(v)) bad |= SFMM_ST_NONFINITE;
+      mn[c] = fmin(mn[c], v);
+      mx[c] = fmax(mx[c], v);
+    }
+    double m = mass[i], hh = h[i];
+    if (!isfinite(m) || !isfinite(hh)) bad |= SFMM_ST_NONFINITE;
+    if (!(m > 0.0) || !(hh > 0.0)) bad |= SFMM_ST_NONPOSITIVE;
+  }
+  __shared__ double s[6][BB_NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[c] = fmin(mn[c], __shfl_xor_sync(SFMM_FULL, mn[c], o));
+      mx[c] = fmax(mx[c], __shfl_xor_sync(SFMM_FULL, mx[c], o));
+    }
+    if (lane == 0) {
+      s[c][warp] = mn[c];
+      s[3 + c][warp] = mx[c];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double E = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      double a = s[c][0], b = s[3 + c][0];
+      for (int w = 1; w < BB_NT / 32; ++w) {
+        a = fmin(a, s[c][w]);
+        b = fmax(b, s[3 + c][w]);
+      }
+      bbox[8 * sys + c] = a;
+      bbox[8 * sys + 3 + c] = b;
+      double e = dsub(b, a);
+      if (e > E) E = e;
+    }
+    bbox[8 * sys + 6] = E;
+    bbox[8 * sys + 7] = (E > 0.0) ? __ddiv_rn(2097152.0, E) : 0.0;
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+// System of every particle (sorted and input positions of a system coincide:
+// systems are packed back to back and the sort keeps them in order).
+__global__ void k_fill_psys(int n, int nsys, const int* __restrict__ off, int* __restrict__ psys) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = nsys;  // largest s with off[s] <= i
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  psys[i] = lo;
+}
+
 // bbox[0..2] min, [3..5] max, [6] cube extent E, [7] key scale 2^21 / E (0 if E == 0)
 __global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ bbox) {
   const int lane = threadIdx.x;  // one warp
@@ -190,10 +257,11 @@ __device__ __forceinline__ uint64_t quantise(double x, double mn, double scale) 
   return k > 2097151ull ? 2097151ull : k;
 }
 
-__global__ void k_morton(const double* __restrict__ pos, int n, const double* __restrict__ bbox,
-                         uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+__global__ void k_morton(const double* __restrict__ pos, int n, const double* __restrict__ bbox0,
+                         const int* __restrict__ psys, uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double* bbox = bbox0 + (psys ? 8 * psys[i] : 0);
   double scale = bbox[7];
   uint64_t kx = quantise(pos[3 * (int64_t)i], bbox[0], scale);
   uint64_t ky = quantise(pos[3 * (int64_t)i + 1], bbox[1], scale);
@@ -210,8 +278,17 @@ __global__ void k_morton(const double* __restrict__ pos, int n, const double* __
 #define RS_TILE (RS_NT * RS_ITEMS)
 #define RS_WARPS (RS_NT / 32)
 
-__global__ void __launch_bounds__(RS_NT) k_rs_hist(const uint64_t* __restrict__ keys, int n, int shift,
-                                                   uint32_t* __restrict__ counts, int ntiles) {
+// Digit of element i: bits [shift, shift+8) of its key, or of its system id
+// (psys of the carried input index) for the final passes of a batch sort.
+__device__ __forceinline__ unsigned rs_digit(const uint64_t* keys, const uint32_t* vals, const int* psys, int64_t i,
+                                             int shift) {
+  if (psys) return ((unsigned)psys[vals[i]] >> shift) & 255u;
+  return (unsigned)(keys[i] >> shift) & 255u;
+}
+
+__global__ void __launch_bounds__(RS_NT) k_rs_hist(const uint64_t* __restrict__ keys,
+                                                   const uint32_t* __restrict__ vals, const int* __restrict__ psys,
+                                                   int n, int shift, uint32_t* __restrict__ counts, int ntiles) {
   __shared__ uint32_t hw[RS_WARPS][256];
   const int warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_NT) (&hw[0][0])[t] = 0;
@@ -219,7 +296,7 @@ __global__ void __launch_bounds__(RS_NT) k_rs_hist(const uint64_t* __restrict__ 
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
   for (int k = 0; k < RS_ITEMS; ++k) {
     int64_t i = base + (int64_t)k * RS_NT + threadIdx.x;
-    if (i < n) atomicAdd(&hw[warp][(unsigned)(keys[i] >> shift) & 255u], 1u);
+    if (i < n) atomicAdd(&hw[warp][rs_digit(keys, vals, psys, i, shift)], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += RS_NT) {
@@ -232,8 +309,8 @@ __global__ void __launch_bounds__(RS_NT) k_rs_hist(const uint64_t* __restrict__ 
 __global__ void __launch_bounds__(RS_NT) k_rs_scatter(const uint64_t* __restrict__ kin,
                                                       const uint32_t* __restrict__ vin,
                                                       uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                      int n, int shift, const uint32_t* __restrict__ offs,
-                                                      int ntiles) {
+                                                      const int* __restrict__ psys, int n, int shift,
+                                                      const uint32_t* __restrict__ offs, int ntiles) {
   __shared__ uint32_t run[256];
   __shared__ uint32_t wc[RS_WARPS][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -245,7 +322,7 @@ __global__ void __launch_bounds__(RS_NT) k_rs_scatter(const uint64_t* __restrict
     int64_t i = base + (int64_t)r * RS_NT + threadIdx.x;
     bool valid = i < n;
     uint64_t key = valid ? kin[i] : 0ull;
-    int d = valid ? (int)((key >> shift) & 255u) : 256;
+    int d = valid ? (int)rs_digit(kin, vin, psys, i, shift) : 256;
     unsigned peers = __match_any_sync(SFMM_FULL, d);
     unsigned rank = __popc(peers & lanemask_lt());
     bool leader = (__ffs(peers) - 1) == lane;
@@ -292,32 +369,46 @@ __global__ void k_gather(const double* __restrict__ pos, const double* __restric
 // S3: binary radix tree over the augmented keys (key, sorted position)
 // (Karras 2012 construction; split at the highest differing bit)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int prefix_len(const uint64_t* __restrict__ keys, int n, int i, int64_t j) {
+// Common prefix length of the augmented keys (system, Morton key, position
+// within the system) of sorted elements i and j (-1 outside [0, n)).
+struct SysView {
+  const int* psys;  // null: one system
+  const int* off;
+};
+__device__ __forceinline__ int prefix_len(const uint64_t* __restrict__ keys, int n, int i, int64_t j,
+                                          const SysView sv) {
   if (j < 0 || j >= n) return -1;
+  int si = 0, sj = 0, oi = 0;
+  if (sv.psys) {
+    si = sv.psys[i];
+    sj = sv.psys[j];
+    if (si != sj) return __clz(si ^ sj);
+    oi = sv.off[si];
+  }
   uint64_t a = keys[i], b = keys[j];
-  if (a != b) return __clzll((long long)(a ^ b));
-  return 64 + __clz(i ^ (int)j);
+  if (a != b) return 32 + __clzll((long long)(a ^ b));
+  return 96 + __clz((i - oi) ^ ((int)j - oi));
 }
 
 // Children encoding: >= 0 internal node index, < 0 leaf (particle) ~index.
-__global__ void k_radix_tree(const uint64_t* __restrict__ keys, int n, int* __restrict__ kl,
+__global__ void k_radix_tree(const uint64_t* __restrict__ keys, int n, const SysView sv, int* __restrict__ kl,
                              int* __restrict__ kr, int* __restrict__ kf, int* __restrict__ kla,
                              int* __restrict__ par_int, int* __restrict__ par_leaf) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
-  int d = (prefix_len(keys, n, i, i + 1) - prefix_len(keys, n, i, i - 1)) >= 0 ? 1 : -1;
-  int dmin = prefix_len(keys, n, i, (int64_t)i - d);
+  int d = (prefix_len(keys, n, i, i + 1, sv) - prefix_len(keys, n, i, i - 1, sv)) >= 0 ? 1 : -1;
+  int dmin = prefix_len(keys, n, i, (int64_t)i - d, sv);
   int64_t lmax = 2;
-  while (prefix_len(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  while (prefix_len(keys, n, i, i + lmax * d, sv) > dmin) lmax <<= 1;
   int64_t l = 0;
   for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-    if (prefix_len(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    if (prefix_len(keys, n, i, i + (l + t) * d, sv) > dmin) l += t;
   int64_t j = i + l * d;
-  int dnode = prefix_len(keys, n, i, j);
+  int dnode = prefix_len(keys, n, i, j, sv);
   int64_t s = 0, t = l;
   do {
     t = (t + 1) >> 1;
-    if (prefix_len(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    if (prefix_len(keys, n, i, i + (s + t) * d, sv) > dnode) s += t;
   } while (t > 1);
   int gamma = (int)(i + s * d + (d < 0 ? -1 : 0));
   int first = (int)min((int64_t)i, j), last = (int)max((int64_t)i, j);
@@ -332,35 +423,51 @@ __global__ void k_radix_tree(const uint64_t* __restrict__ keys, int n, int* __re
   if (i == 0) par_int[0] = -1;
 }
 
+// A node is split (internal) when it holds more than its system's leaf size
+// or particles of more than one system.
+struct LeafRule {
+  const int* psys;  // null: one system
+  const int* lsz;
+  int leaf_size;
+  __device__ __forceinline__ bool splits(int first, int last) const {
+    if (psys) {
+      const int sf = psys[first];
+      if (sf != psys[last]) return true;
+      return last - first + 1 > lsz[sf];
+    }
+    return last - first + 1 > leaf_size;
+  }
+};
+
 // Tree nodes of the collapsed tree: the root and every child of a node with
 // more than leaf_size particles.  chain[f] counts the tree nodes whose range
 // starts at f (a nested chain: each is the left child of the previous).
-__global__ void k_mark(int n, int leaf_size, const int* __restrict__ kf, const int* __restrict__ kla,
+__global__ void k_mark(int n, const LeafRule lr, const int* __restrict__ kf, const int* __restrict__ kla,
                        const int* __restrict__ par_int, const int* __restrict__ par_leaf,
                        uint32_t* __restrict__ chain) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n - 1) {
     int p = par_int[i];
-    bool tree = (i == 0) || (kla[p] - kf[p] + 1 > leaf_size);
+    bool tree = (i == 0) || lr.splits(kf[p], kla[p]);
     if (tree) atomicAdd(&chain[kf[i]], 1u);
   }
   if (i < n) {
     int p = par_leaf[i];
-    bool tree = (kla[p] - kf[p] + 1 > leaf_size);
+    bool tree = lr.splits(kf[p], kla[p]);
     if (tree) atomicAdd(&chain[i], 1u);
   }
 }
 
 // Pre-order index = (# tree nodes starting before) + (# tree ancestors
 // starting at the same particle).
-__global__ void k_preorder(int n, int leaf_size, const int* __restrict__ kf, const int* __restrict__ kla,
+__global__ void k_preorder(int n, const LeafRule lr, const int* __restrict__ kf, const int* __restrict__ kla,
                            const int* __restrict__ par_int, const int* __restrict__ par_leaf,
                            const uint32_t* __restrict__ base, int* __restrict__ pre_int,
                            int* __restrict__ pre_leaf) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n - 1) {
     int p = par_int[i];
-    bool tree = (i == 0) || (kla[p] - kf[p] + 1 > leaf_size);
+    bool tree = (i == 0) || lr.splits(kf[p], kla[p]);
     int v = -1;
     if (tree) {
       int f = kf[i], r = 0, u = i;
@@ -376,7 +483,7 @@ __global__ void k_preorder(int n, int leaf_size, const int* __restrict__ kf, con
   }
   if (i < n) {
     int p = par_leaf[i];
-    bool tree = (kla[p] - kf[p] + 1 > leaf_size);
+    bool tree = lr.splits(kf[p], kla[p]);
     int v = -1;
     if (tree) {
       int r = 0, u = p;
@@ -390,7 +497,7 @@ __global__ void k_preorder(int n, int leaf_size, const int* __restrict__ kf, con
   }
 }
 
-__global__ void k_fill_nodes(int n, int leaf_size, const int* __restrict__ kl, const int* __restrict__ kr,
+__global__ void k_fill_nodes(int n, const LeafRule lr, const int* __restrict__ kl, const int* __restrict__ kr,
                              const int* __restrict__ kf, const int* __restrict__ kla,
                              const int* __restrict__ par_int, const int* __restrict__ par_leaf,
                              const int* __restrict__ pre_int, const int* __restrict__ pre_leaf,
@@ -404,7 +511,7 @@ __global__ void k_fill_nodes(int n, int leaf_size, const int* __restrict__ kl, c
       nfirst[v] = kf[i];
       ncount[v] = cnt;
       nparent[v] = (i == 0) ? -1 : pre_int[par_int[i]];
-      if (cnt <= leaf_size) {
+      if (!lr.splits(kf[i], kla[i])) {
         nright[v] = -1;
         isleaf[v] = 1u;
       } else {
@@ -427,6 +534,45 @@ __global__ void k_fill_nodes(int n, int leaf_size, const int* __restrict__ kl, c
       isleaf[v] = 1u;
     }
   }
+}
+
+// Walk parent of every node: the parent, -1 at a system's root, -2 for nodes
+// spanning several systems (never walked); the root node of each system.
+__global__ void k_sysroots(int nn, const int* __restrict__ psys, const int* __restrict__ nfirst,
+                           const int* __restrict__ ncount, const int* __restrict__ nparent, int* __restrict__ wparent,
+                           int* __restrict__ sys_root) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nn) return;
+  const int f = nfirst[v], l = f + ncount[v] - 1;
+  const int p = nparent[v];
+  if (!psys) {
+    wparent[v] = p;
+    if (p < 0) sys_root[0] = v;
+    return;
+  }
+  const int sv = psys[f];
+  if (sv != psys[l]) {
+    wparent[v] = -2;
+    return;
+  }
+  const bool root = (p < 0) || (psys[nfirst[p]] != psys[nfirst[p] + ncount[p] - 1]);
+  wparent[v] = root ? -1 : p;
+  if (root) sys_root[sv] = v;
+}
+
+// First leaf of every system (leaves are in (system, key) order).
+__global__ void k_sys_leaf_off(int nleaves, int nsys, const int* __restrict__ psys,
+                               const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
+                               int* __restrict__ sys_leaf_off) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q > nleaves) return;
+  if (q == nleaves) {
+    sys_leaf_off[nsys] = nleaves;
+    return;
+  }
+  const int s = psys ? psys[nfirst[leaf_node[q]]] : 0;
+  const int sp = (q == 0) ? -1 : (psys ? psys[nfirst[leaf_node[q - 1]]] : 0);
+  if (s != sp) sys_leaf_off[s] = q;
 }
 
 // isleaf has been exclusive-scanned into leaf indices; record the leaves.
@@ -506,7 +652,7 @@ __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const i
 // node combine their squared distances, one atomic max per group.
 __global__ void k_size(int n, const double* __restrict__ px, const double* __restrict__ py,
                        const double* __restrict__ pz, const int* __restrict__ pnode,
-                       const int* __restrict__ nparent, const double* __restrict__ ncx,
+                       const int* __restrict__ wparent, const double* __restrict__ ncx,
                        const double* __restrict__ ncy, const double* __restrict__ ncz,
                        unsigned long long* __restrict__ l2bits) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -530,7 +676,7 @@ __global__ void k_size(int n, const double* __restrict__ px, const double* __res
       unsigned mhi = __reduce_max_sync(grp, hi);
       unsigned mlo = __reduce_max_sync(grp, hi == mhi ? lo : 0u);
       if ((__ffs(grp) - 1) == lane) atomicMax(&l2bits[v], ((unsigned long long)mhi << 32) | mlo);
-      v = nparent[v];
+      v = wparent[v];  // stops after the system root (-1)
     }
   }
 }
@@ -585,9 +731,10 @@ __global__ void k_depth(int nn, const int* __restrict__ nparent, int* __restrict
 // all leaves in one launch; shallow leaves run the longest lowering).
 // Warp-aggregated counting: one atomic per (warp, depth) group.
 __global__ void k_level_count(int nn, const int* __restrict__ depth, const int* __restrict__ nright,
-                              uint32_t* __restrict__ cnt_int, uint32_t* __restrict__ cnt_leaf) {
+                              const int* __restrict__ wparent, uint32_t* __restrict__ cnt_int,
+                              uint32_t* __restrict__ cnt_leaf) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool ok = v < nn;
+  const bool ok = v < nn && wparent[v] != -2;
   const int d = ok ? depth[v] : -1;
   const bool leaf = ok && nright[v] < 0;
   const int key = ok ? (2 * d + (leaf ? 1 : 0)) : -1;
@@ -597,11 +744,12 @@ __global__ void k_level_count(int nn, const int* __restrict__ depth, const int* 
 }
 
 __global__ void k_level_scatter(int nn, const int* __restrict__ depth, const int* __restrict__ nright,
-                                const uint32_t* __restrict__ off_int, const uint32_t* __restrict__ off_leaf,
-                                uint32_t* __restrict__ cur_int, uint32_t* __restrict__ cur_leaf,
-                                int* __restrict__ level_nodes, int* __restrict__ leaf_order) {
+                                const int* __restrict__ wparent, const uint32_t* __restrict__ off_int,
+                                const uint32_t* __restrict__ off_leaf, uint32_t* __restrict__ cur_int,
+                                uint32_t* __restrict__ cur_leaf, int* __restrict__ level_nodes,
+                                int* __restrict__ leaf_order) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nn) return;
+  if (v >= nn || wparent[v] == -2) return;
   const int d = depth[v];
   if (nright[v] < 0) leaf_order[off_leaf[d] + atomicAdd(&cur_leaf[d], 1u)] = v;
   else level_nodes[off_int[d] + atomicAdd(&cur_int[d], 1u)] = v;
@@ -625,12 +773,15 @@ int build_levels(sfmm_ctx* c) {
   uint32_t* cur = c->level_cur.as<uint32_t>();
   SFMM_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(uint32_t) * 2 * (nc + 1), st));
   SFMM_CUDA_TRY(cudaMemsetAsync(cur, 0, sizeof(uint32_t) * 2 * (nc + 1), st));
-  k_level_count<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->nright.as<int>(), off, off + nc);
+  k_level_count<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->nright.as<int>(), c->wparent.as<int>(),
+                                               off, off + nc);
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
-  if ((rc = exclusive_scan_u32(c, off, (int64_t)nc, nullptr))) return rc;
-  if ((rc = exclusive_scan_u32(c, off + nc, (int64_t)nc, nullptr))) return rc;
-  k_level_scatter<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->nright.as<int>(), off, off + nc, cur,
+  // totals (walkable internal nodes, leaves) land in the two spare slots
+  if ((rc = exclusive_scan_u32(c, off, (int64_t)nc, off + 2 * nc))) return rc;
+  if ((rc = exclusive_scan_u32(c, off + nc, (int64_t)nc, off + 2 * nc + 1))) return rc;
+  k_level_scatter<<<nblk(nn, 256), 256, 0, st>>>(nn, c->ndepth.as<int>(), c->nright.as<int>(), c->wparent.as<int>(),
+                                                 off, off + nc, cur,
                                                  cur + nc, c->level_nodes.as<int>(), c->leaf_order.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
@@ -660,7 +811,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ENS(keys_b, sizeof(uint64_t) * n);
   ENS(idx_a, sizeof(uint32_t) * n);
   ENS(idx_b, sizeof(uint32_t) * n);
-  ENS(misc, 256);
+  ENS(misc, 256 + 64 * (size_t)c->nsys);
   ENS(px, sizeof(double) * n);
   ENS(py, sizeof(double) * n);
   ENS(pz, sizeof(double) * n);
@@ -700,15 +851,31 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   const int nbb = 2 * num_sms(c->device);
   ENS(bbox_part, sizeof(double) * 6 * nbb);
 #undef ENS
-  double* bbox = c->misc.as<double>();           // 8 doubles
-  uint32_t* totals = (uint32_t*)(bbox + 8);      // scan totals
+  const int nsys = c->nsys;
+  double* bbox = c->misc.as<double>();             // 8 doubles per system
+  uint32_t* totals = (uint32_t*)(bbox + 8 * nsys);  // scan totals
+  const int* psys = nullptr;                       // system of each particle (batches only)
+  if (nsys > 1) {
+    if ((rc = c->psys.ensure(sizeof(int) * (size_t)n))) return rc;
+    k_fill_psys<<<nblk(n, 256), 256, 0, st>>>(n, nsys, c->sys_off.as<int>(), c->psys.as<int>());
+    ++c->nlaunch;
+    psys = c->psys.as<int>();
+  }
+  if ((rc = c->sys_root.ensure(sizeof(int) * (size_t)nsys))) return rc;
+  if ((rc = c->sys_leaf_off.ensure(sizeof(int) * ((size_t)nsys + 1)))) return rc;
+  if ((rc = c->wparent.ensure(sizeof(int) * nn_max))) return rc;
 
-  // S1: bounding box, validation, Morton keys
-  k_bbox_partial<<<nbb, BB_NT, 0, st>>>(pos, mass, h, n, c->bbox_part.as<double>(), c->d_status);
-  ++c->nlaunch;
-  k_bbox_final<<<1, 32, 0, st>>>(c->bbox_part.as<double>(), nbb, bbox);
-  ++c->nlaunch;
-  k_morton<<<nblk(n, 256), 256, 0, st>>>(pos, n, bbox, c->keys_a.as<uint64_t>(), c->idx_a.as<uint32_t>());
+  // S1: bounding box (per system), validation, Morton keys
+  if (nsys == 1) {
+    k_bbox_partial<<<nbb, BB_NT, 0, st>>>(pos, mass, h, n, c->bbox_part.as<double>(), c->d_status);
+    ++c->nlaunch;
+    k_bbox_final<<<1, 32, 0, st>>>(c->bbox_part.as<double>(), nbb, bbox);
+    ++c->nlaunch;
+  } else {
+    k_bbox_seg<<<nsys, BB_NT, 0, st>>>(pos, mass, h, c->sys_off.as<int>(), bbox, c->d_status);
+    ++c->nlaunch;
+  }
+  k_morton<<<nblk(n, 256), 256, 0, st>>>(pos, n, bbox, psys, c->keys_a.as<uint64_t>(), c->idx_a.as<uint32_t>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
 
@@ -717,18 +884,26 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   if ((rc = c->sort_counts.ensure(sizeof(uint32_t) * 256 * (size_t)ntiles)) != SFMM_OK) return rc;
   uint64_t *ka = c->keys_a.as<uint64_t>(), *kb = c->keys_b.as<uint64_t>();
   uint32_t *va = c->idx_a.as<uint32_t>(), *vb = c->idx_b.as<uint32_t>();
-  for (int shift = 0; shift < 64; shift += 8) {
-    k_rs_hist<<<ntiles, RS_NT, 0, st>>>(ka, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
+  // Morton passes, then (batches) the system id as the most significant digits:
+  // the result is ordered by (system, key, input index)
+  int sys_bits = 0;
+  while ((1 << sys_bits) < nsys) ++sys_bits;
+  const int npass = 8 + (sys_bits + 7) / 8;
+  for (int pass = 0; pass < npass; ++pass) {
+    const bool by_sys = pass >= 8;
+    const int shift = by_sys ? 8 * (pass - 8) : 8 * pass;
+    const int* dsys = by_sys ? psys : nullptr;
+    k_rs_hist<<<ntiles, RS_NT, 0, st>>>(ka, va, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
     ++c->nlaunch;
     SFMM_CUDA_TRY(cudaGetLastError());
     if ((rc = exclusive_scan_u32(c, c->sort_counts.as<uint32_t>(), (int64_t)256 * ntiles, nullptr))) return rc;
-    k_rs_scatter<<<ntiles, RS_NT, 0, st>>>(ka, va, kb, vb, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
+    k_rs_scatter<<<ntiles, RS_NT, 0, st>>>(ka, va, kb, vb, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
     ++c->nlaunch;
     SFMM_CUDA_TRY(cudaGetLastError());
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  // after 8 passes the sorted data is back in keys_a / idx_a
+  // the sorted data is in ka / va
   k_gather<<<nblk(n, 256), 256, 0, st>>>(pos, mass, h, va, n, c->px.as<double>(), c->py.as<double>(),
                                          c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(),
                                          c->perm.as<int>());
@@ -747,17 +922,19 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     c->nnodes = 1;
     c->nleaves = 1;
   } else {
-    k_radix_tree<<<nblk(n - 1, 256), 256, 0, st>>>(ka, n, c->k_left.as<int>(), c->k_right.as<int>(),
+    const SysView sv{psys, c->sys_off.as<int>()};
+    const LeafRule lr{psys, c->sys_lsz.as<int>(), c->leaf_size};
+    k_radix_tree<<<nblk(n - 1, 256), 256, 0, st>>>(ka, n, sv, c->k_left.as<int>(), c->k_right.as<int>(),
                                                      c->k_first.as<int>(), c->k_last.as<int>(),
                                                      c->par_int.as<int>(), c->par_leaf.as<int>());
     ++c->nlaunch;
     SFMM_CUDA_TRY(cudaMemsetAsync(c->chain.p, 0, sizeof(uint32_t) * (n + 1), st));
-    k_mark<<<nblk(n, 256), 256, 0, st>>>(n, c->leaf_size, c->k_first.as<int>(), c->k_last.as<int>(),
+    k_mark<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_first.as<int>(), c->k_last.as<int>(),
                                          c->par_int.as<int>(), c->par_leaf.as<int>(), c->chain.as<uint32_t>());
     ++c->nlaunch;
     SFMM_CUDA_TRY(cudaGetLastError());
     if ((rc = exclusive_scan_u32(c, c->chain.as<uint32_t>(), n, totals))) return rc;
-    k_preorder<<<nblk(n, 256), 256, 0, st>>>(n, c->leaf_size, c->k_first.as<int>(), c->k_last.as<int>(),
+    k_preorder<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_first.as<int>(), c->k_last.as<int>(),
                                              c->par_int.as<int>(), c->par_leaf.as<int>(),
                                              c->chain.as<uint32_t>(), c->pre_int.as<int>(), c->pre_leaf.as<int>());
     ++c->nlaunch;
@@ -767,7 +944,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     SFMM_CUDA_TRY(cudaStreamSynchronize(st));
     nnodes = (int)h_tot;
     c->nnodes = nnodes;
-    k_fill_nodes<<<nblk(n, 256), 256, 0, st>>>(n, c->leaf_size, c->k_left.as<int>(), c->k_right.as<int>(),
+    k_fill_nodes<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_left.as<int>(), c->k_right.as<int>(),
                                                c->k_first.as<int>(), c->k_last.as<int>(), c->par_int.as<int>(),
                                                c->par_leaf.as<int>(), c->pre_int.as<int>(), c->pre_leaf.as<int>(),
                                                c->nfirst.as<int>(), c->ncount.as<int>(), c->nright.as<int>(),
@@ -782,6 +959,14 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     c->nleaves = (nnodes + 1) / 2;  // full binary tree
   }
   const int nl = c->nleaves;
+  // walk parents, system roots and leaf ranges of the systems
+  k_sysroots<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, psys, c->nfirst.as<int>(), c->ncount.as<int>(),
+                                                c->nparent.as<int>(), c->wparent.as<int>(), c->sys_root.as<int>());
+  ++c->nlaunch;
+  k_sys_leaf_off<<<nblk(nl + 1, 256), 256, 0, st>>>(nl, nsys, psys, c->leaf_node.as<int>(), c->nfirst.as<int>(),
+                                                    c->sys_leaf_off.as<int>());
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
 
   // S4 geometry
   k_leaf_geom<<<nblk(nl, 128), 128, 0, st>>>(
@@ -798,7 +983,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaMemsetAsync(c->l2bits.p, 0, sizeof(unsigned long long) * nnodes, st));
   k_size<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
-                                       c->pnode.as<int>(), c->nparent.as<int>(), c->ncx.as<double>(),
+                                       c->pnode.as<int>(), c->wparent.as<int>(), c->ncx.as<double>(),
                                        c->ncy.as<double>(), c->ncz.as<double>(),
                                        c->l2bits.as<unsigned long long>());
   ++c->nlaunch;

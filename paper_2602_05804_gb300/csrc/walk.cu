@@ -67,12 +67,12 @@ __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
       Tn[b] = R(0);
       Tl[b] = 0.0f;
     }
-    int Aid = 0, prevA = 0;
+    int Aid = a.sys_root[a.psys ? a.psys[fL] : 0], prevA = 0;  // the walk starts at the system's root
     float4 hiP = make_float4(0.f, 0.f, 0.f, 0.f), loP = hiP;
     double cPx = 0.0, cPy = 0.0, cPz = 0.0;
     int* cur = bufA;
     int* nxt = bufB;
-    if (lane == 0) cur[0] = 0;
+    if (lane == 0) cur[0] = Aid;
     __syncwarp();
     int head = 0, tail = 1, nn = 0, k = 0;
     bool bad = false;
@@ -444,6 +444,8 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
     a.theta = theta;
     a.theta_f = (float)theta;
     a.theta2_f = (float)(theta * theta);
+    a.psys = c->nsys > 1 ? c->psys.as<int>() : nullptr;
+    a.sys_root = c->sys_root.as<int>();
     if (dump) {
       // counting pass, then the writing pass at the scanned offsets
       if ((rc = c->dump.ensure(sizeof(int) * (size_t)(nl + 1) + sizeof(long long) * (size_t)(nl + 1)))) return rc;
@@ -516,6 +518,8 @@ int run_walk_dump_write(sfmm_ctx* c, double theta, const long long* d_off, int* 
   a.theta = theta;
   a.theta_f = (float)theta;
   a.theta2_f = (float)(theta * theta);
+  a.psys = c->nsys > 1 ? c->psys.as<int>() : nullptr;
+  a.sys_root = c->sys_root.as<int>();
   a.m2l_off = d_off;
   a.dump_level = d_level;
   a.dump_src = d_src;

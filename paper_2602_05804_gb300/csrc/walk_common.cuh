@@ -52,6 +52,8 @@ struct WalkArgs {
   double theta;
   float theta_f;
   float theta2_f;
+  const int* psys;            // system of each particle (null: one system)
+  const int* sys_root;        // root node of each system
   int* m2l_cnt;               // MODE_COUNT
   const long long* m2l_off;   // MODE_WRITE
   int* dump_level;

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_level(const LevelArgs la) {
       cAy = a.ncy[A];
       cAz = a.ncz[A];
     }
-    // the opened list inherited from the parent (the root starts from itself)
+    // the opened list inherited from the parent (a system's root starts from itself)
     const int* fin = nullptr;
     int nF = 1;
     if (par >= 0) {
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_level(const LevelArgs la) {
       // lowering mutates the list: copy it to the warp's stack
       if (nF > cap) bad = true;
       else {
-        for (int t = lane; t < nF; t += 32) stk[t] = fin ? fin[t] : 0;
+        for (int t = lane; t < nF; t += 32) stk[t] = fin ? fin[t] : A;
       }
       __syncwarp();
     }
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_level(const LevelArgs la) {
         const int cnt = min(32, tail - head);
         int s;
         if (!leafA) {
-          s = (lane < cnt) ? (fin ? fin[head + lane] : 0) : -1;
+          s = (lane < cnt) ? (fin ? fin[head + lane] : A) : -1;
           head += cnt;
         } else {
           s = (lane < cnt) ? stk[tail - cnt + lane] : -1;
@@ -431,7 +431,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     a.theta = theta;
     a.theta_f = (float)theta;
     a.theta2_f = (float)(theta * theta);
-    la.nparent = c->nparent.as<int>();
+    la.nparent = c->wparent.as<int>();  // -1 at system roots
     la.nlu = c->nlu.as<int>();
     la.leaf_index = c->isleaf.as<uint32_t>();
     la.cf_cap = cf_cap;

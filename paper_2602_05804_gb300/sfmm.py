@@ -22,7 +22,8 @@ SFMM_FP64, SFMM_FP32 = 0, 1
 # every symbol include/sfmm.h declares
 EXPORTS = ("sfmm_create", "sfmm_destroy", "sfmm_set_stream", "sfmm_set_option", "sfmm_build", "sfmm_gravity",
            "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
-           "sfmm_lists", "sfmm_strerror", "sfmm_last_error", "sfmm_version", "sfmm_reduce_noalloc")
+           "sfmm_lists", "sfmm_strerror", "sfmm_last_error", "sfmm_version", "sfmm_reduce_noalloc",
+           "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums")
 SFMM_NOALLOC_MAX_N = 67108864
 
 
@@ -77,11 +78,14 @@ def load(path: str = LIB_PATH):
     lib.sfmm_last_error.argtypes = [P]
     lib.sfmm_last_error.restype = ctypes.c_char_p
     lib.sfmm_version.restype = ctypes.c_char_p
+    lib.sfmm_build_batch.argtypes = [P, i32, P, P, P, P, P]
+    lib.sfmm_gravity_batch.argtypes = [P, dbl, i32, P, P]
+    lib.sfmm_batch_sums.argtypes = [P, i32, P]
     lib.sfmm_reduce_noalloc.argtypes = [i64, P, P, P, P, P]
     lib.sfmm_reduce_noalloc.restype = i32
     for name in ("sfmm_create", "sfmm_set_stream", "sfmm_set_option", "sfmm_build", "sfmm_gravity",
                  "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
-                 "sfmm_lists"):
+                 "sfmm_lists", "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -182,6 +186,22 @@ def sfmm_lists(ctx, theta):
     return mo, lv[:mo[-1]], src[:mo[-1]], po, ps[:po[-1]]
 
 
+def sfmm_build_batch(ctx, offsets, pos, mass, h, leaf_size=None):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    ls = None if leaf_size is None else np.ascontiguousarray(leaf_size, dtype=np.int32)
+    _check(load().sfmm_build_batch(ctx, len(off) - 1, _ptr(off), _ptr(pos), _ptr(mass), _ptr(h), _ptr(ls)), ctx)
+
+
+def sfmm_gravity_batch(ctx, theta, order, acc, pot):
+    _check(load().sfmm_gravity_batch(ctx, float(theta), int(order), _ptr(acc), _ptr(pot)), ctx)
+
+
+def sfmm_batch_sums(ctx, nsys):
+    out = np.empty((nsys, 5))
+    _check(load().sfmm_batch_sums(ctx, int(nsys), _ptr(out)), ctx)
+    return out
+
+
 def sfmm_reduce_noalloc(n, mass, acc, pot, out, stream=None):
     """Momentum/energy sums over device arrays without any device allocation
     (see include/sfmm.h); ``out`` is a device buffer of 5 float64."""
@@ -257,6 +277,17 @@ class Solver:
             pot = t.empty((self.n,), dtype=t.float64, device="cuda:%d" % self.device)
         sfmm_gravity(self.ctx, theta, order, acc, pot)
         return acc, pot
+
+    def build_batch(self, offsets, pos, mass, h, leaf_size=None):
+        """Packed systems: offsets (nsys + 1), per-system leaf sizes or None."""
+        n = int(offsets[-1])
+        self._inputs = (self._dev(pos, (n, 3)), self._dev(mass, (n,)), self._dev(h, (n,)))
+        sfmm_build_batch(self.ctx, offsets, *self._inputs, leaf_size)
+        self.n = n
+        self.nsys = len(offsets) - 1
+
+    def batch_sums(self):
+        return sfmm_batch_sums(self.ctx, self.nsys)
 
     def solve_host(self, pos, mass, h, leaf_size, theta, order, acc, pot):
         """Host (numpy or pinned torch CPU) buffers in and out."""
