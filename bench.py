@@ -222,6 +222,61 @@ def time_steps(torch, solver, pos_d, m_d, h_d, acc, pot, w, theta, steps, warmup
     return ms, st
 
 
+def ensemble_block(torch, local, flush, steps):
+    """Batched ensemble: 256 independent systems (sizes log-uniform in
+    [10^3, 10^5], alternating Plummer / uniform sphere), theta 0.5, p 2:
+    the FP32 form over the whole batch in the same launches, with autotuned
+    leaf sizes, against the FP64 form run system by system."""
+    import workloads
+    from paper_2602_05804_gb300 import sfmm
+    from paper_2602_05804_gb300.autotune import Autotuner
+
+    pos, m, h, off = workloads.ensemble(1004)
+    sizes = np.diff(off)
+    nsys, ntot = len(sizes), int(off[-1])
+    profiles = ["plummer" if k % 2 == 0 else "uniform" for k in range(nsys)]
+    tuner = Autotuner()
+    leaf = np.array(tuner.leaf_sizes(sizes, profiles, 0.5, 2, "fp32"), np.int32)
+    dev = torch.device("cuda", local)
+    pd, md, hd = (torch.from_numpy(x).to(dev) for x in (pos, m, h))
+    acc = torch.empty((ntot, 3), dtype=torch.float64, device=dev)
+    pot = torch.empty(ntot, dtype=torch.float64, device=dev)
+    sb = sfmm.Solver(local, "fp32")
+    for _ in range(2):
+        sfmm.sfmm_build_batch(sb.ctx, off, pd, md, hd, leaf)
+        sfmm.sfmm_gravity_batch(sb.ctx, 0.5, 2, acc, pot)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        _flush(flush)
+        ev[k][0].record(sb.stream)
+        sfmm.sfmm_build_batch(sb.ctx, off, pd, md, hd, leaf)
+        sfmm.sfmm_gravity_batch(sb.ctx, 0.5, 2, acc, pot)
+        ev[k][1].record(sb.stream)
+    torch.cuda.synchronize()
+    ms_b = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    sums = sfmm.sfmm_batch_sums(sb.ctx, nsys)
+    sb.close()
+    # FP64 form, one system at a time
+    s64 = sfmm.Solver(local, "fp64")
+    sfmm.sfmm_build(s64.ctx, int(sizes[0]), pd[:sizes[0]], md[:sizes[0]], hd[:sizes[0]], 16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(nsys):
+        a, b = int(off[k]), int(off[k + 1])
+        sfmm.sfmm_build(s64.ctx, b - a, pd[a:b], md[a:b], hd[a:b], 16)
+        sfmm.sfmm_gravity(s64.ctx, 0.5, 2, acc[a:b], pot[a:b])
+    torch.cuda.synchronize()
+    ms_s = 1e3 * (time.perf_counter() - t0)
+    s64.close()
+    mom = np.linalg.norm(sums[:, :3], axis=1) / sums[:, 3]
+    hist = {str(v): int((leaf == v).sum()) for v in sorted(set(leaf.tolist()))}
+    return {"systems": nsys, "n_total": ntot, "n_min": int(sizes.min()), "n_max": int(sizes.max()),
+            "batched_fp32": {"particles_per_s": ntot / (ms_b * 1e-3), "ms_per_step": ms_b, "steps": steps,
+                             "leaf_sizes": hist, "max_momentum_residual": float(mom.max())},
+            "sequential_fp64": {"particles_per_s": ntot / (ms_s * 1e-3), "ms_per_step": ms_s},
+            "speedup": ms_s / ms_b}
+
+
 def run_gpu(args):
     import torch
 
@@ -302,6 +357,10 @@ def run_gpu(args):
                                "p2p": st_o["ms_p2p"]},
                   "m2l": st_o["m2l"], "m2l_unique": st_o["m2l_unique"], "p2p_pairs": st_o["p2p_pairs"]}
 
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = ensemble_block(torch, local, flush, max(1, min(args.steps, 5)))
+
     # e2e through the C ABI with HOST buffers (pinned), copies inside the region
     pos_h = torch.from_numpy(pos).pin_memory()
     m_h = torch.from_numpy(m).pin_memory()
@@ -368,6 +427,7 @@ def run_gpu(args):
                               "fp64": float(np.linalg.norm(st64["momentum"]) / st64["abs_momentum"])},
         "theta_sweep_fp32": sweep,
         "other_walk_fp32": other_walk,
+        "ensemble_256": ensemble,
         "e2e": {"value": ws * w["n"] / (e2e_ms * 1e-3), "unit": "particles/s",
                 "h2d_bytes_per_step": int(w["n"] * 40), "d2h_bytes_per_step": int(w["n"] * 32)},
         "gpu_launches": int(st32["kernel_launches_per_step"] * args.steps),
@@ -393,12 +453,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--n", type=int, default=None, help="particle count (default: the workload's 10^6)")
+    ap.add_argument("--leaf", type=int, default=None, help="leaf size (default: the workload's 16)")
     ap.add_argument("--walk", type=int, default=1, choices=[0, 1],
                     help="headline walk: 1 per-node shared pairs (default), 0 per-leaf replay (Algorithm 1)")
     ap.add_argument("--only", default="all", choices=["all", "fp32"],
                     help="fp32: time the headline FP32 step only (for profiler launch lists)")
     args = ap.parse_args()
+    if args.leaf:
+        WORKLOAD["leaf_size"] = int(args.leaf)
     if args.n:
         WORKLOAD["n"] = int(args.n)
         WORKLOAD["name"] = "plummer_%d" % args.n
