@@ -188,6 +188,26 @@ def run_reference(args):
     return 0
 
 
+def rank_workload(w, rank):
+    """The particle set of one rank: every rank solves its own seeded system
+    (weak scaling; no data-path exchange between ranks)."""
+    return dict(w, seed=w["seed"] + rank)
+
+
+def reduce_timing(dist, step_ms, n_local, device=None):
+    """Whole-job throughput: the slowest rank's step time and the particles of
+    all ranks.  Returns (max step ms over ranks, total particles)."""
+    if dist is None:
+        return step_ms, n_local
+    import torch
+
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(n_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 def _flush(buf):
     buf.add_(1)
 
@@ -291,7 +311,8 @@ def run_gpu(args):
     from paper_2602_05804_gb300 import sfmm
 
     w = WORKLOAD
-    pos, m, h = workloads.plummer(w["n"], w["seed"] + rank)
+    wr = rank_workload(w, rank)
+    pos, m, h = workloads.plummer(wr["n"], wr["seed"])
     dev = torch.device("cuda", local)
     pos_d = torch.from_numpy(pos).to(dev)
     m_d = torch.from_numpy(m).to(dev)
@@ -315,12 +336,8 @@ def run_gpu(args):
         ms32, st32 = time_steps(torch, s32, pos_d, m_d, h_d, acc, pot, w, w["theta"], args.steps, args.warmup, flush)
         barrier()
         t_wall = time.perf_counter() - t_wall0
-    step_ms = float(np.mean(ms32))
-    if dist is not None:
-        tt = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        step_ms = float(tt.item())
-    value = ws * w["n"] / (step_ms * 1e-3)
+    step_ms, n_all = reduce_timing(dist, float(np.mean(ms32)), w["n"], dev)
+    value = n_all / (step_ms * 1e-3)
     inter = st32["p2p_pairs"] + st32["m2l_unique"]
 
     if args.only == "fp32":
