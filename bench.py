@@ -297,6 +297,61 @@ def ensemble_block(torch, local, flush, steps):
             "speedup": ms_s / ms_b}
 
 
+M2L_FLOPS_P2 = 136       # FP32 M2L at p = 2 without the dipole terms (counted from the kernel source)
+NCOEF_P2 = 10
+
+
+def stage_rooflines(st, n, fp32_peak, hbm_peak):
+    """Achieved fraction of each stage's roofline from live CUDA-event stage
+    times: build and moments against HBM (algorithmic bytes), the walk (M2L)
+    and P2P against the FP32 FMA units (algorithmic flops)."""
+    nn = st["nnodes"]
+    b_build = n * (40 + 40 + 16) + nn * (16 + NCOEF_P2) * 8
+    b_mom = n * 32 + nn * (NCOEF_P2 + 4) * 8
+    out = {}
+    for key, ms, work, unit, peak in (
+            ("build", st["ms_build"], b_build / 1e9, "GB/s", hbm_peak),
+            ("moments", st["ms_moments"], b_mom / 1e9, "GB/s", hbm_peak),
+            ("walk_m2l", st["ms_walk"], st["m2l_unique"] * M2L_FLOPS_P2 / 1e12, "TFLOP/s", fp32_peak),
+            ("p2p", st["ms_p2p"], st["p2p_pairs"] * FLOPS_PER_PAIR / 1e12, "TFLOP/s", fp32_peak)):
+        ach = work / (ms * 1e-3) if ms > 0 else 0.0
+        out[key] = {"ms": ms, "achieved": ach, "unit": unit, "peak": peak, "frac": ach / peak}
+    return out
+
+
+def config_block(torch, local, flush, name, steps, fp32_peak, hbm_peak):
+    """One more of the paper's workloads at its full size, FP32 form,
+    theta 0.5, p 2, leaf 16: build + gravity per step (full pipeline) and
+    gravity alone, the stage split and each stage's roofline fraction."""
+    import workloads
+    from paper_2602_05804_gb300 import sfmm
+
+    wk = dict(workloads.WORKLOADS[name], order=2)
+    t0 = time.perf_counter()
+    pos, m, h = workloads.make(name)
+    t_gen = time.perf_counter() - t0
+    n = len(m)
+    dev = torch.device("cuda", local)
+    pd, md, hd = (torch.from_numpy(x).to(dev) for x in (pos, m, h))
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    pot = torch.empty(n, dtype=torch.float64, device=dev)
+    s = sfmm.Solver(local, "fp32", profile=1, walk=1)
+    ms, st = time_steps(torch, s, pd, md, hd, acc, pot, wk, wk["theta"], steps, 2, flush)
+    s.close()
+    step = float(np.mean(ms))
+    grav = st["ms_moments"] + st["ms_walk"] + st["ms_p2p"] + st["ms_reduce"]
+    del pd, md, hd, acc, pot
+    torch.cuda.empty_cache()
+    return {"n": n, "theta": wk["theta"], "leaf_size": wk["leaf_size"], "form": "FP32", "steps": steps,
+            "full_pipeline_particles_per_s": n / (step * 1e-3), "ms_per_step": step,
+            "gravity_particles_per_s": n / (grav * 1e-3),
+            "interactions_per_s": (st["p2p_pairs"] + st["m2l_unique"]) / (step * 1e-3),
+            "counts": {"m2l_unique": st["m2l_unique"], "m2l_replicated": st["m2l"], "p2p_pairs": st["p2p_pairs"],
+                       "nleaves": st["nleaves"], "nnodes": st["nnodes"]},
+            "momentum_residual": float(np.linalg.norm(st["momentum"]) / st["abs_momentum"]),
+            "stage_rooflines": stage_rooflines(st, n, fp32_peak, hbm_peak), "generate_s": t_gen}
+
+
 def run_gpu(args):
     import torch
 
@@ -378,6 +433,15 @@ def run_gpu(args):
     if not args.no_ensemble:
         ensemble = ensemble_block(torch, local, flush, max(1, min(args.steps, 5)))
 
+    peaks, peak_kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, unit counts x max clock
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    configs = None
+    if not args.no_configs:
+        configs = {name: config_block(torch, local, flush, name, max(1, min(args.steps, 5)), fp32_peak, hbm_peak)
+                   for name in ("binary_polytrope_2e6", "clustered_1.6e7")}
+
     # e2e through the C ABI with HOST buffers (pinned), copies inside the region
     pos_h = torch.from_numpy(pos).pin_memory()
     m_h = torch.from_numpy(m).pin_memory()
@@ -402,10 +466,7 @@ def run_gpu(args):
         e2e_ms = float(tt.item())
 
     # roofline of the dominant kernel
-    peaks, peak_kind = _peaks()
     clocks = clk.summary()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, unit counts x max clock
     shares = {"walk": st32["ms_walk"], "p2p": st32["ms_p2p"], "build": st32["ms_build"],
               "moments": st32["ms_moments"]}
     if st32["ms_p2p"] >= st32["ms_walk"]:
@@ -445,6 +506,8 @@ def run_gpu(args):
         "theta_sweep_fp32": sweep,
         "other_walk_fp32": other_walk,
         "ensemble_256": ensemble,
+        "stage_rooflines": stage_rooflines(st32, w["n"], fp32_peak, hbm_peak),
+        "configs": configs,
         "e2e": {"value": ws * w["n"] / (e2e_ms * 1e-3), "unit": "particles/s",
                 "h2d_bytes_per_step": int(w["n"] * 40), "d2h_bytes_per_step": int(w["n"] * 32)},
         "gpu_launches": int(st32["kernel_launches_per_step"] * args.steps),
@@ -471,6 +534,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the binary-polytrope (2e6) and clustered-cloud (1.6e7) measurements")
     ap.add_argument("--n", type=int, default=None, help="particle count (default: the workload's 10^6)")
     ap.add_argument("--leaf", type=int, default=None, help="leaf size (default: the workload's 16)")
     ap.add_argument("--walk", type=int, default=1, choices=[0, 1],

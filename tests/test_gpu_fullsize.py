@@ -1,0 +1,87 @@
+"""Parity at the full benchmark sizes, in the launch configuration the
+benchmark times (needs a GB300; marked gpu).
+
+The GPU solves the whole system; the oracle builds the same tree on the host
+and runs Algorithms 1-2 for a seeded sample of leaves only (every leaf's
+result depends on the read-only tree alone, so sampled leaves are exact).
+Sampled particles are compared element by element; the momentum residual is
+checked over all particles (it holds at any size).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_helpers import TOL_FP32_RMS, TOL_FP64, TOL_MOM_FP32, TOL_MOM_FP64, acc_rel, momentum_residual, pot_rel, solver
+
+pytestmark = pytest.mark.gpu
+
+_CACHE = {}
+
+
+def _system(name):
+    if name not in _CACHE:
+        _CACHE.clear()
+        pos, m, h = workloads.make(name)
+        w = workloads.WORKLOADS[name]
+        t = oracle.Tree(pos, m, h, w["leaf_size"], p=2)
+        _CACHE[name] = (pos, m, h, w, t)
+    return _CACHE[name]
+
+
+def _sample(t, k, seed):
+    """k seeded leaves plus the first and the last leaf of the tree."""
+    rng = np.random.default_rng(seed)
+    sel = rng.choice(t.nleaves, size=min(k, t.nleaves), replace=False)
+    return np.unique(np.concatenate([sel, [0, t.nleaves - 1]])).astype(np.int32)
+
+
+def _sampled_particles(t, sel):
+    return np.concatenate([t.perm[t.first[L]:t.first[L] + t.count[L]] for L in t.leaves[sel]])
+
+
+def test_full_size_tree_leaves_match_oracle():
+    """The GPU tree of the 10^6 Plummer sphere has the oracle's leaves."""
+    pos, m, h, w, t = _system("plummer_1e6")
+    s = solver("fp32")
+    s.build(pos, m, h, w["leaf_size"])
+    g = s.tree()
+    s.close()
+    np.testing.assert_array_equal(g["perm"], t.perm)
+    np.testing.assert_array_equal(g["first"][g["leaves"]], t.first[t.leaves])
+    np.testing.assert_array_equal(g["count"][g["leaves"]], t.count[t.leaves])
+
+
+@pytest.mark.parametrize("name,prec,theta", [
+    ("plummer_1e6", "fp32", 0.5),
+    ("plummer_1e6", "fp64", 0.5),
+    ("plummer_1e6", "fp32", 0.3),
+    ("plummer_1e6", "fp32", 0.7),
+    ("binary_polytrope_2e6", "fp32", 0.5),
+    ("clustered_1.6e7", "fp32", 0.5),
+])
+def test_full_size_sampled_leaves_match_oracle(name, prec, theta):
+    pos, m, h, w, t = _system(name)
+    s = solver(prec, walk=1)
+    s.build(pos, m, h, w["leaf_size"])
+    acc, pot = s.gravity(theta, 2)
+    acc, pot = acc.cpu().numpy(), pot.cpu().numpy()
+    s.close()
+
+    res = momentum_residual(m, acc)
+    assert res <= (TOL_MOM_FP64 if prec == "fp64" else TOL_MOM_FP32), res
+
+    sel = _sample(t, 96 if theta >= 0.5 else 48, seed=len(name) + int(100 * theta))
+    a_o, p_o, _ = t.sfmm(theta, leaf_sample=sel)
+    idx = _sampled_particles(t, sel)
+    assert len(idx) > 0
+    e = acc_rel(acc[idx], a_o[idx])
+    ep = pot_rel(pot[idx], p_o[idx])
+    if prec == "fp64":
+        assert e.max() <= TOL_FP64, e.max()
+        assert ep.max() <= TOL_FP64, ep.max()
+    else:
+        assert math.sqrt((e**2).mean()) <= TOL_FP32_RMS, math.sqrt((e**2).mean())
+        assert math.sqrt((ep**2).mean()) <= TOL_FP32_RMS, math.sqrt((ep**2).mean())

@@ -155,7 +155,7 @@ def clustered_cloud(n: int, seed: int, nclump: int = 64, clump_scale: float = 0.
     plus ``nclump`` Plummer clumps (scale 0.02, truncated at 20 scales) with
     log-normal masses normalised to the rest; clump centres follow the halo
     profile truncated at 5a; equal particle masses; h from the summed
-    analytic density."""
+    analytic density, each clump's term truncated at its 20 scales."""
     rng = np.random.default_rng(seed)
     cm = rng.lognormal(0.0, sigma, nclump)
     cm *= (1.0 - halo_frac) / cm.sum()
@@ -171,9 +171,19 @@ def clustered_cloud(n: int, seed: int, nclump: int = 64, clump_scale: float = 0.
     pos = np.concatenate(parts)
     m = np.full(n, 1.0 / n)
     rho = plummer_density(np.linalg.norm(pos, axis=1), 1.0, halo_frac)
+    # each clump's density is truncated like its particles (at 20 scales): only
+    # particles inside that ball receive it; they are found from an x-sorted slab
+    rcut = 20.0 * clump_scale
+    xorder = np.argsort(pos[:, 0], kind="stable")
+    xs, ys, zs = pos[xorder, 0], pos[xorder, 1], pos[xorder, 2]
     for c in range(nclump):
-        d = np.linalg.norm(pos - centres[c][None, :], axis=1)
-        rho += plummer_density(d, clump_scale, cm[c])
+        cx, cy, cz = centres[c]
+        lo, hi = np.searchsorted(xs, [cx - rcut, cx + rcut])
+        box = np.flatnonzero((np.abs(ys[lo:hi] - cy) < rcut) & (np.abs(zs[lo:hi] - cz) < rcut)) + lo
+        dx, dy, dz = xs[box] - cx, ys[box] - cy, zs[box] - cz
+        d = np.sqrt(dx * dx + dy * dy + dz * dz)
+        inside = d < rcut
+        rho[xorder[box[inside]]] += plummer_density(d[inside], clump_scale, cm[c])
     return pos, m, _hsml(m, rho)
 
 
