@@ -30,7 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particles/sec & interactions/sec of SFMM gravity, FP32 vs FP64 form on 1 GB300"
-WORKLOAD = dict(name="plummer_1e6", n=1_000_000, seed=1002, theta=0.5, order=2, leaf_size=16)
+WORKLOAD = dict(name="plummer_1e6", gen_name="plummer_1e6", n=1_000_000, seed=1002, theta=0.5, order=2,
+                leaf_size=16)
 FLOPS_PER_PAIR = 20      # far-field pair: dx 3, r^2 5, rsqrt 1, m r^-3 3, acc 6, pot 2 (FMA = 2)
 L2_FLUSH_BYTES = 512 << 20
 
@@ -167,7 +168,7 @@ def run_reference(args):
     import workloads
 
     w = WORKLOAD
-    pos, m, h = workloads.plummer(w["n"], w["seed"])
+    pos, m, h = workloads.make(w["gen_name"], n=w["n"], seed=w["seed"])
     times = []
     base = None
     for it in range(args.warmup + args.steps):
@@ -179,7 +180,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * w["n"] / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded Plummer sphere)",
+            "data": "synthetic (seeded %s)" % w["gen_name"],
             "config": {"workload": w["name"], "n": w["n"], "theta": w["theta"], "order": w["order"],
                        "leaf_size": w["leaf_size"], "form": "oracle FP64 (CPU)"},
             "cpu_baseline": base,
@@ -367,7 +368,7 @@ def run_gpu(args):
 
     w = WORKLOAD
     wr = rank_workload(w, rank)
-    pos, m, h = workloads.plummer(wr["n"], wr["seed"])
+    pos, m, h = workloads.make(w["gen_name"], n=wr["n"], seed=wr["seed"])
     dev = torch.device("cuda", local)
     pos_d = torch.from_numpy(pos).to(dev)
     m_d = torch.from_numpy(m).to(dev)
@@ -414,7 +415,8 @@ def run_gpu(args):
         ms_t, st_t = time_steps(torch, s32, pos_d, m_d, h_d, acc, pot, w, th, max(1, min(args.steps, 3)), 1, flush)
         sweep[str(th)] = {"particles_per_s": w["n"] / (np.mean(ms_t) * 1e-3),
                           "interactions_per_s": (st_t["p2p_pairs"] + st_t["m2l_unique"]) / (np.mean(ms_t) * 1e-3),
-                          "ms_per_step": float(np.mean(ms_t)), "m2l": st_t["m2l"], "p2p_pairs": st_t["p2p_pairs"]}
+                          "ms_per_step": float(np.mean(ms_t)), "m2l": st_t["m2l"], "p2p_pairs": st_t["p2p_pairs"],
+                          "stage_ms": {k[3:]: st_t[k] for k in ("ms_build", "ms_moments", "ms_walk", "ms_p2p")}}
 
     # the other walk on the same workload (same interactions, same results up
     # to summation order): the per-leaf replay of Algorithm 1 as printed, or the
@@ -489,7 +491,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Plummer sphere, one per rank)",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded %s, one per rank)" % w["gen_name"],
         "config": {"workload": w["name"], "n": w["n"], "theta": w["theta"], "order": w["order"],
                    "leaf_size": w["leaf_size"], "form": "FP32 (FP64 centres, decisions, reductions)",
                    "walk": "per-node shared pairs" if args.walk == 1 else "per-leaf replay (Algorithm 1)",
@@ -536,6 +538,9 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the binary-polytrope (2e6) and clustered-cloud (1.6e7) measurements")
+    ap.add_argument("--workload", default="plummer_1e6",
+                    choices=["plummer_1e6", "uniform_1e4", "binary_polytrope_2e6", "clustered_1.6e7"],
+                    help="headline workload (default: the 10^6 Plummer sphere; the others are for profiling)")
     ap.add_argument("--n", type=int, default=None, help="particle count (default: the workload's 10^6)")
     ap.add_argument("--leaf", type=int, default=None, help="leaf size (default: the workload's 16)")
     ap.add_argument("--walk", type=int, default=1, choices=[0, 1],
@@ -543,11 +548,17 @@ def main():
     ap.add_argument("--only", default="all", choices=["all", "fp32"],
                     help="fp32: time the headline FP32 step only (for profiler launch lists)")
     args = ap.parse_args()
+    if args.workload != "plummer_1e6":
+        import workloads
+
+        wk = workloads.WORKLOADS[args.workload]
+        WORKLOAD.update(name=args.workload, gen_name=args.workload, n=wk["n"], seed=wk["seed"],
+                        theta=wk["theta"], leaf_size=wk["leaf_size"])
     if args.leaf:
         WORKLOAD["leaf_size"] = int(args.leaf)
     if args.n:
         WORKLOAD["n"] = int(args.n)
-        WORKLOAD["name"] = "plummer_%d" % args.n
+        WORKLOAD["name"] = "%s_n%d" % (WORKLOAD["gen_name"].split("_")[0], args.n)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -48,6 +48,15 @@ struct P2PArgs {
   double* acc;
   double* pot;
   double* leafsum;  // nleaves x 5: sum m a (3), sum |m a|, sum m Phi
+  // long lists: work items [0, nextra) are the further chunks (leaf, chunk)
+  // of split lists, items [nextra, nextra + nleaves) the first chunk of every
+  // leaf; a split leaf's chunk k writes its sums to partial slot split[leaf] + k
+  int nextra;
+  const int2* extra;
+  const int* split;   // per leaf: first partial slot, -1 (or NULL array) if unsplit
+  const int* slist;   // the split leaves
+  void* part;         // [slot][lmax][4] partial sums in the form's type
+  int lmax;
 };
 
 // M4 softening kernel of one particle (compact support 2h), evaluated with
@@ -131,6 +140,40 @@ __device__ __forceinline__ void pair_cand(R xi, R yi, R zi, R hinvi, R h2i, bool
 
 template <bool F32> __host__ __device__ constexpr int p2p_warps() { return F32 ? P2P_WARPS : P2P_WARPS / 2; }
 
+// Near sums v (a, Phi) of sorted particle i plus its far field: scaled by G,
+// written in caller order, added to the leaf's momentum and energy sums.
+template <bool F32, typename R>
+__device__ __forceinline__ void p2p_finish(const P2PArgs& a, int i, const R (&v)[4], double (&sm)[5]) {
+  double f[4];
+  if constexpr (F32) {
+    const float4 fr = a.far32[i];
+    f[0] = (double)(v[0] + fr.x);
+    f[1] = (double)(v[1] + fr.y);
+    f[2] = (double)(v[2] + fr.z);
+    f[3] = (double)(v[3] + fr.w);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) f[c] = v[c] + a.far64[4 * (size_t)i + c];
+  }
+  const double m = a.pm[i];
+  double pot = a.G * f[3];
+  if (a.self_pot) pot += a.G * m * (-1.4 / a.ph[i]);
+  const int o = a.perm[i];
+  double am[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double acc = a.G * f[c];
+    a.acc[3 * (size_t)o + c] = acc;
+    am[c] = m * acc;
+  }
+  if (a.pot) a.pot[o] = pot;
+  sm[0] += am[0];
+  sm[1] += am[1];
+  sm[2] += am[2];
+  sm[3] += fabs(am[0]) + fabs(am[1]) + fabs(am[2]);
+  sm[4] += m * pot;
+}
+
 // One warp per target leaf.  Sources: the particles of the leaf's neighbour
 // list, streamed 32 at a time over consecutive list entries (every lane
 // busy), moved to the target leaf's frame (FP32 form) and split once per
@@ -138,7 +181,7 @@ template <bool F32> __host__ __device__ constexpr int p2p_warps() { return F32 ?
 // (|x_j - s_L| < l_L + 2 max(h_max,L, h_j), with a small safety factor) and
 // those that cannot; the latter take the unsoftened branch-free loop.
 template <bool F32>
-__global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
+__global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
   using R = typename std::conditional<F32, float, double>::type;
   using V = typename Vec4<R>::T;
   using V2 = typename Vec4<R>::T2;
@@ -152,11 +195,21 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
+  const int nitems = a.nextra + a.nleaves;
   while (true) {
-    int leaf = 0;
-    if (lane == 0) leaf = atomicAdd(a.leaf_counter, 1);
-    leaf = __shfl_sync(SFMM_FULL, leaf, 0);
-    if (leaf >= a.nleaves) break;
+    int item = 0;
+    if (lane == 0) item = atomicAdd(a.leaf_counter, 1);
+    item = __shfl_sync(SFMM_FULL, item, 0);
+    if (item >= nitems) break;
+    int leaf, chunk = 0;
+    if (item < a.nextra) {
+      const int2 x = a.extra[item];
+      leaf = x.x;
+      chunk = x.y;
+    } else {
+      leaf = item - a.nextra;
+    }
+    const int pslot = a.split ? a.split[leaf] : -1;
     const int L = a.leaf_node[leaf];
     const int fL = a.nfirst[L], nL = a.ncount[L];
     const float4 hiL = a.geo_hi[L], loL = a.geo_lo[L];
@@ -188,8 +241,8 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
     R ax0 = R(0), ay0 = R(0), az0 = R(0), pt0 = R(0);
     R ax1 = R(0), ay1 = R(0), az1 = R(0), pt1 = R(0);
 
-    const long long off = a.p2p_off[leaf];
-    const int cnt = a.p2p_cnt[leaf];
+    const long long off = a.p2p_off[leaf] + (long long)chunk * SFMM_P2P_CHUNK;
+    const int cnt = (pslot < 0) ? a.p2p_cnt[leaf] : min(SFMM_P2P_CHUNK, a.p2p_cnt[leaf] - chunk * SFMM_P2P_CHUNK);
     int nfar = 0, nnear = 0;
     int e = 0;                 // next list entry to load
     int tot = 0, pdone = 0;    // particles of the loaded entries / staged so far
@@ -333,37 +386,81 @@ __global__ void __launch_bounds__(P2P_NT) k_p2p(const P2PArgs a) {
           for (int q = 0; q < nph; ++q) sacc += s_red[warp][c][q * ntl + lane];
           v[c] = sacc;
         }
-        const int i = fL + t;
-        double f[4];
-        if constexpr (F32) {
-          const float4 fr = a.far32[i];
-          f[0] = (double)(v[0] + fr.x);
-          f[1] = (double)(v[1] + fr.y);
-          f[2] = (double)(v[2] + fr.z);
-          f[3] = (double)(v[3] + fr.w);
+        if (pslot < 0) {
+          p2p_finish<F32>(a, fL + t, v, sm);
         } else {
+          R* pp = static_cast<R*>(a.part) + ((size_t)(pslot + chunk) * a.lmax + t) * 4;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) f[c] = v[c] + a.far64[4 * (size_t)i + c];
+          for (int c = 0; c < 4; ++c) pp[c] = v[c];
         }
-        const double m = a.pm[i];
-        double pot = a.G * f[3];
-        if (a.self_pot) pot += a.G * m * (-1.4 / a.ph[i]);
-        const int o = a.perm[i];
-        double am[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const double acc = a.G * f[c];
-          a.acc[3 * (size_t)o + c] = acc;
-          am[c] = m * acc;
-        }
-        if (a.pot) a.pot[o] = pot;
-        sm[0] += am[0];
-        sm[1] += am[1];
-        sm[2] += am[2];
-        sm[3] += fabs(am[0]) + fabs(am[1]) + fabs(am[2]);
-        sm[4] += m * pot;
       }
       __syncwarp();
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      double sv = sm[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(SFMM_FULL, sv, o);
+      sm[c] = sv;
+    }
+    if (lane == 0 && pslot < 0) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) a.leafsum[5 * (size_t)leaf + c] = sm[c];
+    }
+  }
+}
+
+// Long lists: thread per leaf; a list of more than SFMM_P2P_CHUNK entries
+// gets ceil(entries / SFMM_P2P_CHUNK) partial slots and one extra work item
+// per chunk after the first.  ctr[0]: extra items, ctr[1]: slots, ctr[2]:
+// split leaves.  Which slots a leaf gets does not change any result.
+__global__ void k_p2p_split(int nleaves, const int* __restrict__ p2p_cnt, int* __restrict__ split,
+                            int2* __restrict__ extra, int* __restrict__ slist, unsigned long long* __restrict__ ctr,
+                            int max_extra, int max_slots, int max_split, int* __restrict__ status) {
+  const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+  if (leaf >= nleaves) return;
+  const int cnt = p2p_cnt[leaf];
+  if (cnt <= SFMM_P2P_CHUNK) {
+    split[leaf] = -1;
+    return;
+  }
+  const int nch = (cnt + SFMM_P2P_CHUNK - 1) / SFMM_P2P_CHUNK;
+  const int x = (int)atomicAdd(ctr, (unsigned long long)(nch - 1));
+  const int base = (int)atomicAdd(ctr + 1, (unsigned long long)nch);
+  const int q = (int)atomicAdd(ctr + 2, 1ull);
+  if (x + nch - 1 > max_extra || base + nch > max_slots || q >= max_split) {
+    // the walk counted these exactly: more means an internal inconsistency
+    split[leaf] = -1;
+    set_status(status, SFMM_ST_INTERNAL);
+    return;
+  }
+  split[leaf] = base;
+  for (int k = 1; k < nch; ++k) extra[x + k - 1] = make_int2(leaf, k);
+  slist[q] = leaf;
+}
+
+// Split leaves: one warp per leaf sums the chunks' partial sums in chunk
+// order (so reruns are bitwise identical) and finishes as an unsplit leaf.
+template <bool F32>
+__global__ void k_p2p_combine(const P2PArgs a, int nsplit) {
+  using R = typename std::conditional<F32, float, double>::type;
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int q = w0; q < nsplit; q += nw) {
+    const int leaf = a.slist[q];
+    const int L = a.leaf_node[leaf];
+    const int fL = a.nfirst[L], nL = a.ncount[L];
+    const int nch = (a.p2p_cnt[leaf] + SFMM_P2P_CHUNK - 1) / SFMM_P2P_CHUNK;
+    const int base = a.split[leaf];
+    double sm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int t = lane; t < nL; t += 32) {
+      R v[4] = {R(0), R(0), R(0), R(0)};
+      for (int k = 0; k < nch; ++k) {
+        const R* pp = static_cast<const R*>(a.part) + ((size_t)(base + k) * a.lmax + t) * 4;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] += pp[c];
+      }
+      p2p_finish<F32>(a, fL + t, v, sm);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -457,7 +554,25 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   int rc;
   if ((rc = c->red_part.ensure(sizeof(double) * 5 * ((size_t)nl + RED_BLOCKS + 1)))) return rc;
   unsigned long long* ctr = c->counters.as<unsigned long long>();
-  SFMM_CUDA_TRY(cudaMemsetAsync(ctr + 10, 0, sizeof(unsigned long long), c->stream));
+  SFMM_CUDA_TRY(cudaMemsetAsync(ctr + 10, 0, 4 * sizeof(unsigned long long), c->stream));
+  const bool f32 = (c->precision == SFMM_FP32);
+  // long lists (counted exactly by the walk): slots, extra items, split leaves
+  const int nsplit = (int)c->split_lists;
+  const int nslots = (int)c->split_chunks;
+  const int nextra = nslots - nsplit;
+  int lmax = c->leaf_size;
+  for (int v : c->h_sys_lsz) lmax = v > lmax ? v : lmax;
+  if (nsplit > 0) {
+    if ((rc = c->p2p_split.ensure(sizeof(int) * (size_t)nl))) return rc;
+    if ((rc = c->p2p_extra.ensure(sizeof(int2) * (size_t)nextra))) return rc;
+    if ((rc = c->p2p_slist.ensure(sizeof(int) * (size_t)nsplit))) return rc;
+    if ((rc = c->p2p_part.ensure((f32 ? sizeof(float) : sizeof(double)) * 4 * (size_t)lmax * nslots))) return rc;
+    k_p2p_split<<<(nl + 255) / 256, 256, 0, c->stream>>>(nl, c->p2p_cnt.as<int>(), c->p2p_split.as<int>(),
+                                                       c->p2p_extra.as<int2>(), c->p2p_slist.as<int>(), ctr + 11,
+                                                       nextra, nslots, nsplit, c->d_status);
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
+  }
   P2PArgs a{};
   a.nleaves = nl;
   a.leaf_node = c->leaf_node.as<int>();
@@ -488,7 +603,12 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   a.acc = acc;
   a.pot = pot;
   a.leafsum = c->red_part.as<double>();
-  const bool f32 = (c->precision == SFMM_FP32);
+  a.nextra = nsplit > 0 ? nextra : 0;
+  a.extra = nsplit > 0 ? c->p2p_extra.as<int2>() : nullptr;
+  a.split = nsplit > 0 ? c->p2p_split.as<int>() : nullptr;
+  a.slist = nsplit > 0 ? c->p2p_slist.as<int>() : nullptr;
+  a.part = nsplit > 0 ? c->p2p_part.p : nullptr;
+  a.lmax = lmax;
   const int nt = 32 * (f32 ? p2p_warps<true>() : p2p_warps<false>());
   int per_sm = 0;
   if (f32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<true>, nt, 0);
@@ -499,6 +619,13 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   else k_p2p<false><<<nblocks, nt, 0, c->stream>>>(a);
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
+  if (nsplit > 0) {
+    const int cblocks = (nsplit + 7) / 8;
+    if (f32) k_p2p_combine<true><<<cblocks, 256, 0, c->stream>>>(a, nsplit);
+    else k_p2p_combine<false><<<cblocks, 256, 0, c->stream>>>(a, nsplit);
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
+  }
   return SFMM_OK;
 }
 

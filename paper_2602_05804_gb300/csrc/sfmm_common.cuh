@@ -20,6 +20,11 @@
 
 #define SFMM_MAXDEPTH 128
 
+// Neighbour lists longer than this many entries are split into chunks of it,
+// each a separate near-field work item (long lists would otherwise leave one
+// warp working alone at the end of the pass).
+#define SFMM_P2P_CHUNK 256
+
 namespace sfmm {
 
 // ---------------------------------------------------------------------------

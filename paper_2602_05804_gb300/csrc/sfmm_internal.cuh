@@ -79,6 +79,11 @@ struct sfmm_ctx {
   // gravity
   DevBuf ring, far, arena, p2p_off, p2p_cnt, counters, red_part, dump;
   DevBuf cf_arena, cf_off, cf_cnt, Tnode;  // shared walk: child frontiers, node coefficients
+  // near field: chunks of long neighbour lists (extra work items, per-leaf
+  // slot base, split leaves, partial sums) and the list entries in use
+  DevBuf p2p_extra, p2p_split, p2p_slist, p2p_part;
+  int64_t arena_used = 0;
+  int64_t split_chunks = 0, split_lists = 0;  // from the walk: chunks of split lists, split lists
 
   // status word (device) + pinned host mirror
   int* d_status = nullptr;

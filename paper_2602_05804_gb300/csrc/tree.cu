@@ -919,6 +919,9 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     SFMM_CUDA_TRY(cudaMemcpyAsync(c->nright.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
     SFMM_CUDA_TRY(cudaMemcpyAsync(c->nparent.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
     SFMM_CUDA_TRY(cudaMemcpyAsync(c->leaf_node.as<int>(), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    // leaf numbers of the nodes (exclusive scan of the leaf flags): node 0 is leaf 0
+    static const uint32_t leaf_scan[2] = {0u, 1u};
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->isleaf.p, leaf_scan, sizeof(leaf_scan), cudaMemcpyHostToDevice, st));
     c->nnodes = 1;
     c->nleaves = 1;
   } else {

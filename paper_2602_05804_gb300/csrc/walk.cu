@@ -337,6 +337,10 @@ __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
         a.p2p_cnt[leaf] = nn;
         st_pl += nn;
         st_pp += pairs;
+        if (nn > SFMM_P2P_CHUNK) {
+          atomicAdd(a.split_counter, (unsigned long long)((nn + SFMM_P2P_CHUNK - 1) / SFMM_P2P_CHUNK));
+          atomicAdd(a.split_counter + 1, 1ull);
+        }
       }
     }
     __syncwarp();
@@ -434,6 +438,7 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
     a.leaf_counter = reinterpret_cast<int*>(ctr + 8);
     a.arena = c->arena.as<int>();
     a.arena_counter = ctr + 9;
+    a.split_counter = ctr + 5;
     a.arena_cap = arena_cap;
     a.p2p_off = c->p2p_off.as<long long>();
     a.p2p_cnt = c->p2p_cnt.as<int>();
@@ -472,8 +477,11 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
       SFMM_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
       continue;
     }
-    SFMM_CUDA_TRY(cudaMemcpy(c->h_scalars, ctr, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost));
+    SFMM_CUDA_TRY(cudaMemcpy(c->h_scalars, ctr, sizeof(unsigned long long) * 10, cudaMemcpyDeviceToHost));
     const unsigned long long* hs = reinterpret_cast<const unsigned long long*>(c->h_scalars);
+    c->arena_used = (int64_t)hs[9];
+    c->split_chunks = (int64_t)hs[5];
+    c->split_lists = (int64_t)hs[6];
     c->stats.m2l = (int64_t)hs[0];
     c->stats.m2l_unique = (int64_t)hs[1];
     c->stats.p2p_leaves = (int64_t)hs[2];
@@ -510,6 +518,7 @@ int run_walk_dump_write(sfmm_ctx* c, double theta, const long long* d_off, int* 
   a.leaf_counter = reinterpret_cast<int*>(ctr + 8);
   a.arena = c->arena.as<int>();
   a.arena_counter = ctr + 9;
+  a.split_counter = ctr + 5;
   a.arena_cap = (long long)(c->arena.bytes / sizeof(int));
   a.p2p_off = c->p2p_off.as<long long>();
   a.p2p_cnt = c->p2p_cnt.as<int>();

@@ -42,6 +42,7 @@ struct WalkArgs {
   int* leaf_counter;
   int* arena;
   unsigned long long* arena_counter;
+  unsigned long long* split_counter;  // [0]: chunks of split lists, [1]: split lists
   long long arena_cap;
   long long* p2p_off;
   int* p2p_cnt;

@@ -349,6 +349,10 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_level(const LevelArgs la) {
         a.p2p_cnt[leaf] = nn;
         st_pl += nn;
         st_pp += pairs;
+        if (nn > SFMM_P2P_CHUNK) {
+          atomicAdd(a.split_counter, (unsigned long long)((nn + SFMM_P2P_CHUNK - 1) / SFMM_P2P_CHUNK));
+          atomicAdd(a.split_counter + 1, 1ull);
+        }
       }
     }
     __syncwarp();
@@ -421,6 +425,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     a.ring_cap = c->ring_capacity;
     a.arena = c->arena.as<int>();
     a.arena_counter = ctr + 9;
+    a.split_counter = ctr + 5;
     a.arena_cap = arena_cap;
     a.p2p_off = c->p2p_off.as<long long>();
     a.p2p_cnt = c->p2p_cnt.as<int>();
@@ -481,8 +486,11 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
       if (bits & SFMM_ST_CHILDLIST) c->cf_capacity = 4 * cf_cap;
       continue;
     }
-    SFMM_CUDA_TRY(cudaMemcpy(c->h_scalars, ctr, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost));
+    SFMM_CUDA_TRY(cudaMemcpy(c->h_scalars, ctr, sizeof(unsigned long long) * 10, cudaMemcpyDeviceToHost));
     const unsigned long long* hs = reinterpret_cast<const unsigned long long*>(c->h_scalars);
+    c->arena_used = (int64_t)hs[9];
+    c->split_chunks = (int64_t)hs[5];
+    c->split_lists = (int64_t)hs[6];
     c->stats.m2l = (int64_t)hs[0];
     c->stats.m2l_unique = (int64_t)hs[1];
     c->stats.p2p_leaves = (int64_t)hs[2];

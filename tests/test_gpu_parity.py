@@ -294,3 +294,32 @@ def test_shared_walk_capacity_regrow():
     s.build(pos, m, h, 16)
     acc, pot = s.gravity(0.3, 2)
     assert acc_rel(acc.cpu().numpy(), acc_o).max() <= TOL_FP64
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("walk", [0, 1])
+def test_long_lists_split_into_chunks(prec, walk):
+    """Neighbour lists longer than one chunk are evaluated as several work
+    items and recombined in chunk order: the result still matches the
+    oracle, and a rerun is bitwise identical."""
+    pos, m, h = workloads.uniform_sphere(6000, 31)
+    acc_o, pot_o, st_o = oracle.sfmm(pos, m, h, theta=0.1, p=2, leaf_size=4)
+    s = solver(prec, walk=walk)
+    s.build(pos, m, h, 4)
+    acc, pot = s.gravity(0.1, 2)
+    acc, pot = acc.cpu().numpy(), pot.cpu().numpy()
+    st = s.stats()
+    assert st["p2p_leaves"] == st_o["p2p_leaves"] and st["p2p_pairs"] == st_o["p2p_pairs"]
+    assert st["p2p_leaves"] > 2 * 256 * st["nleaves"] // 4  # most lists span several chunks
+    e = acc_rel(acc, acc_o)
+    if prec == "fp64":
+        assert e.max() <= TOL_FP64
+        assert pot_rel(pot, pot_o).max() <= TOL_FP64
+        assert momentum_residual(m, acc) <= TOL_MOM_FP64
+    else:
+        assert math.sqrt((e**2).mean()) <= TOL_FP32_RMS
+        assert momentum_residual(m, acc) <= TOL_MOM_FP32
+    s.build(pos, m, h, 4)
+    acc2, pot2 = s.gravity(0.1, 2)
+    np.testing.assert_array_equal(acc, acc2.cpu().numpy())
+    np.testing.assert_array_equal(pot, pot2.cpu().numpy())
