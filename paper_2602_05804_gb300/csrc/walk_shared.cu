@@ -38,7 +38,7 @@ struct LevelArgs {
 };
 
 template <int P, bool F32>
-__global__ void __launch_bounds__(WALK_NT) k_walk_level(const LevelArgs la) {
+__global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 5 : 1) k_walk_level(const LevelArgs la) {
   using E = Exp<P>;
   using R = typename std::conditional<F32, float, double>::type;
   constexpr int NC = E::NC;
@@ -81,38 +81,50 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_level(const LevelArgs la) {
       cAy = a.ncy[A];
       cAz = a.ncz[A];
     }
-    // the opened list inherited from the parent (a system's root starts from itself)
+    // the opened list inherited from the parent (a system's root starts from
+    // itself), read in order; a leaf's lowering pushes the pairs it opens on
+    // the warp's stack and pops them after the inherited list
     const int* fin = nullptr;
     int nF = 1;
     if (par >= 0) {
       fin = la.cf_in + la.cf_off[par];
       nF = la.cf_cnt[par];
     }
-    int head = 0, tail = nF, nn = 0;
+    int head = 0, sp = 0, nn = 0;
     bool bad = false;
-    if (leafA) {
-      // lowering mutates the list: copy it to the warp's stack
-      if (nF > cap) bad = true;
-      else {
-        for (int t = lane; t < nF; t += 32) stk[t] = fin ? fin[t] : A;
+    // an internal node writes the list its children inherit straight into the
+    // arena: every opened pair yields at most two entries
+    int* cfw = nullptr;
+    unsigned long long cfbase = 0;
+    if (!leafA) {
+      if (lane == 0) cfbase = atomicAdd(la.cf_counter, 2ull * (unsigned long long)nF);
+      cfbase = __shfl_sync(SFMM_FULL, cfbase, 0);
+      if ((long long)(cfbase + 2ull * nF) > la.cf_cap) {
+        if (lane == 0) {
+          set_status(a.status, SFMM_ST_CHILDLIST);
+          la.cf_cnt_out[A] = 0;
+        }
+        continue;
       }
-      __syncwarp();
+      cfw = la.cf_out + cfbase;
     }
     R C[NCS * 32];
 #pragma unroll
     for (int t = 0; t < NCS * 32; ++t) C[t] = R(0);
     int nq = 0, nacc_tot = 0;
     while (!bad) {
-      const bool more = head < tail;
+      const bool from_fin = head < nF;
+      const bool more = from_fin || sp > 0;
       if (more) {
-        const int cnt = min(32, tail - head);
         int s;
-        if (!leafA) {
+        if (from_fin) {
+          const int cnt = min(32, nF - head);
           s = (lane < cnt) ? (fin ? fin[head + lane] : A) : -1;
           head += cnt;
         } else {
-          s = (lane < cnt) ? stk[tail - cnt + lane] : -1;
-          tail -= cnt;
+          const int cnt = min(32, sp);
+          s = (lane < cnt) ? stk[sp - cnt + lane] : -1;
+          sp -= cnt;
         }
         bool acc = false, open = false;
         int rB = -1;
@@ -135,32 +147,30 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_level(const LevelArgs la) {
         if (!leafA) {
           const unsigned b1 = __ballot_sync(SFMM_FULL, open), b2 = __ballot_sync(SFMM_FULL, sint);
           const int add = __popc(b1) + __popc(b2);
-          if (nn + add > cap) {
-            bad = true;
-          } else if (open) {
+          if (open) {
             const int pos = nn + __popc(b1 & lt) + __popc(b2 & lt);
-            if (sleaf) out[pos] = s;
+            if (sleaf) cfw[pos] = s;
             else {
-              out[pos] = s + 1;
-              out[pos + 1] = rB;
+              cfw[pos] = s + 1;
+              cfw[pos + 1] = rB;
             }
           }
           nn += add;
         } else {
           const unsigned bl = __ballot_sync(SFMM_FULL, sleaf), bi = __ballot_sync(SFMM_FULL, sint);
           const int addl = __popc(bl), addi = 2 * __popc(bi);
-          if (nn + addl > cap || tail + addi > cap) {
+          if (nn + addl > cap || sp + addi > cap) {
             bad = true;
           } else {
             if (sleaf) out[nn + __popc(bl & lt)] = s;
             if (sint) {
-              const int cp = tail + 2 * __popc(bi & lt);
+              const int cp = sp + 2 * __popc(bi & lt);
               stk[cp] = s + 1;
               stk[cp + 1] = rB;
             }
           }
           nn += addl;
-          tail += addi;
+          sp += addi;
         }
         __syncwarp();
         if (bad) break;
@@ -273,21 +283,10 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_level(const LevelArgs la) {
     }
 
     if (!leafA) {
-      // the opened list both children inherit
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(la.cf_counter, (unsigned long long)nn);
-      base = __shfl_sync(SFMM_FULL, base, 0);
-      if ((long long)(base + nn) > la.cf_cap) {
-        if (lane == 0) {
-          set_status(a.status, SFMM_ST_CHILDLIST);
-          la.cf_cnt_out[A] = 0;
-        }
-      } else {
-        for (int t = lane; t < nn; t += 32) la.cf_out[base + t] = out[t];
-        if (lane == 0) {
-          la.cf_off_out[A] = (long long)base;
-          la.cf_cnt_out[A] = nn;
-        }
+      // the opened list both children inherit, already in the arena
+      if (lane == 0) {
+        la.cf_off_out[A] = (long long)cfbase;
+        la.cf_cnt_out[A] = nn;
       }
       __syncwarp();
       continue;
@@ -483,7 +482,12 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
         int64_t grown = 2 * (int64_t)arena_cap, want = (int64_t)(need + need / 4 + 1024);
         c->list_capacity = want > grown ? want : grown;
       }
-      if (bits & SFMM_ST_CHILDLIST) c->cf_capacity = 4 * cf_cap;
+      if (bits & SFMM_ST_CHILDLIST) {
+        unsigned long long need = 0;
+        SFMM_CUDA_TRY(cudaMemcpy(&need, ctr + 16, sizeof(need), cudaMemcpyDeviceToHost));
+        const int64_t grown = 2 * (int64_t)cf_cap, want = (int64_t)(need + need / 4 + 4096);
+        c->cf_capacity = want > grown ? want : grown;
+      }
       continue;
     }
     SFMM_CUDA_TRY(cudaMemcpy(c->h_scalars, ctr, sizeof(unsigned long long) * 10, cudaMemcpyDeviceToHost));

@@ -269,10 +269,12 @@ def test_errors_are_reported():
         s.set_option("ring_capacity", 1000)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", TOL_FP32_RMS)])
 def test_shared_walk_equals_replay(prec, tol):
     """Per-node shared pairs and the per-leaf replay evaluate the same
-    interactions: equal counts, results equal up to summation order."""
+    interactions: equal counts, results equal up to summation order (in the
+    FP32 form the M2L terms are accumulated in FP32 in a walk-dependent
+    order, so the bound is the FP32 form's own tolerance)."""
     pos, m, h = workloads.plummer(20000, 44)
     out = []
     for walk in (0, 1):
