@@ -102,10 +102,10 @@ __device__ __forceinline__ T reduce_scatter32(T (&v)[32], int lane) {
 // Acceptance test of Sect. 3: accept iff (l_t + l_s) < theta d and not
 // d < l_t + l_s + R_kern max(h_t, h_s).
 __device__ __forceinline__ bool decide(const float4& hiA, const float4& loA, const float4& hiB, const float4& loB,
-                                       int A, int B, const WalkArgs& a, int& nfb) {
-  const float dx = df_diff(hiB.x, loB.x, hiA.x, loA.x);
-  const float dy = df_diff(hiB.y, loB.y, hiA.y, loA.y);
-  const float dz = df_diff(hiB.z, loB.z, hiA.z, loA.z);
+                                       int A, int B, const WalkArgs& a, int& nfb, float& dx, float& dy, float& dz) {
+  dx = df_diff(hiB.x, loB.x, hiA.x, loA.x);
+  dy = df_diff(hiB.y, loB.y, hiA.y, loA.y);
+  dz = df_diff(hiB.z, loB.z, hiA.z, loA.z);
   // squared form (all terms non-negative): l^2 < theta^2 d^2 and d^2 >= (l + 2h)^2;
   // the float32 error is below 1.5e-6 relative, the tie band 1e-5
   const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -133,18 +133,17 @@ __device__ __forceinline__ bool decide(const float4& hiA, const float4& loA, con
 }
 
 // One node-node interaction (target centre A, source node s) accumulated
-// into the lane's coefficients.
+// into the lane's coefficients.  In the FP32 form r = s_B - s_A comes from
+// the acceptance test (the same double-float difference).
 template <int P, bool F32>
 __device__ __forceinline__ void m2l_eval(int s, const float4& hiA, const float4& loA, double cAx, double cAy,
                                          double cAz, const WalkArgs& a,
-                                         typename std::conditional<F32, float, double>::type* C) {
+                                         typename std::conditional<F32, float, double>::type* C,
+                                         const float4& r) {
   using E = Exp<P>;
   if (s < 0) return;
   if constexpr (F32) {
-    const float4 hB = a.geo_hi[s], lB = a.geo_lo[s];
-    const float rx = df_diff(hB.x, lB.x, hiA.x, loA.x);
-    const float ry = df_diff(hB.y, lB.y, hiA.y, loA.y);
-    const float rz = df_diff(hB.z, lB.z, hiA.z, loA.z);
+    const float rx = r.x, ry = r.y, rz = r.z;
     const float ri = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
     float D[E::NMONO1];
     E::derivs(rx * ri, ry * ri, rz * ri, ri, D);
@@ -172,6 +171,28 @@ __device__ __forceinline__ void m2l_eval(int s, const float4& hiA, const float4&
     for (int t = 0; t < E::NQ; ++t) Q[t] = __ldg(q + t);
     E::m2l(D, Q, C);
   }
+}
+
+// The same with r computed here from the node records (FP32 form).
+template <int P, bool F32>
+__device__ __forceinline__ void m2l_eval(int s, const float4& hiA, const float4& loA, double cAx, double cAy,
+                                         double cAz, const WalkArgs& a,
+                                         typename std::conditional<F32, float, double>::type* C) {
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (F32 && s >= 0) {
+    const float4 hB = a.geo_hi[s], lB = a.geo_lo[s];
+    r.x = df_diff(hB.x, lB.x, hiA.x, loA.x);
+    r.y = df_diff(hB.y, lB.y, hiA.y, loA.y);
+    r.z = df_diff(hB.z, lB.z, hiA.z, loA.z);
+  }
+  m2l_eval<P, F32>(s, hiA, loA, cAx, cAy, cAz, a, C, r);
+}
+
+// Acceptance test without the separation output.
+__device__ __forceinline__ bool decide(const float4& hiA, const float4& loA, const float4& hiB, const float4& loB,
+                                       int A, int B, const WalkArgs& a, int& nfb) {
+  float dx, dy, dz;
+  return decide(hiA, loA, hiB, loB, A, B, a, nfb, dx, dy, dz);
 }
 
 }  // namespace sfmm

@@ -38,7 +38,7 @@ struct LevelArgs {
 };
 
 template <int P, bool F32>
-__global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 5 : 1) k_walk_level(const LevelArgs la) {
+__global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level(const LevelArgs la) {
   using E = Exp<P>;
   using R = typename std::conditional<F32, float, double>::type;
   constexpr int NC = E::NC;
@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 5 : 1) k_walk_level
   const WalkArgs& a = la.w;
 
   __shared__ int s_queue[WALK_WARPS][WALK_MQ];
+  __shared__ float4 s_qr[WALK_WARPS][F32 ? WALK_MQ : 1];  // accepted pairs' separation s_B - s_A
   __shared__ R s_T[WALK_WARPS][NCS * 32];
   __shared__ R s_h[WALK_WARPS][E::NMONO1];
   __shared__ signed char s_tab[NC * NC];
@@ -112,35 +113,63 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 5 : 1) k_walk_level
 #pragma unroll
     for (int t = 0; t < NCS * 32; ++t) C[t] = R(0);
     int nq = 0, nacc_tot = 0;
+    // the inherited list is read through a two-stage pipeline: ids one chunk
+    // ahead of the node records, records one chunk ahead of their use, so the
+    // loads of a chunk overlap the work on the previous one
+    auto fin_id = [&](int at) -> int { return (at + lane < nF) ? (fin ? fin[at + lane] : A) : -1; };
+    int pf_s = fin_id(0), pf_s2 = fin_id(32), pf_r = -1;
+    float4 pf_hi = make_float4(0.f, 0.f, 0.f, 0.f), pf_lo = pf_hi;
+    if (pf_s >= 0) {
+      pf_hi = a.geo_hi[pf_s];
+      pf_lo = a.geo_lo[pf_s];
+      pf_r = a.nright[pf_s];
+    }
     while (!bad) {
       const bool from_fin = head < nF;
       const bool more = from_fin || sp > 0;
       if (more) {
-        int s;
+        int s, rB = -1;
+        float4 hiB = make_float4(0.f, 0.f, 0.f, 0.f), loB = hiB;
         if (from_fin) {
-          const int cnt = min(32, nF - head);
-          s = (lane < cnt) ? (fin ? fin[head + lane] : A) : -1;
-          head += cnt;
+          s = pf_s;
+          hiB = pf_hi;
+          loB = pf_lo;
+          rB = pf_r;
+          head += min(32, nF - head);
+          pf_s = pf_s2;
+          if (pf_s >= 0) {
+            pf_hi = a.geo_hi[pf_s];
+            pf_lo = a.geo_lo[pf_s];
+            pf_r = a.nright[pf_s];
+          }
+          pf_s2 = fin_id(head + 32);
         } else {
           const int cnt = min(32, sp);
           s = (lane < cnt) ? stk[sp - cnt + lane] : -1;
           sp -= cnt;
+          if (s >= 0) {
+            hiB = a.geo_hi[s];
+            loB = a.geo_lo[s];
+            rB = a.nright[s];
+          }
         }
         bool acc = false, open = false;
-        int rB = -1;
+        float rx = 0.f, ry = 0.f, rz = 0.f;
         if (s >= 0) {
-          const float4 hiB = a.geo_hi[s], loB = a.geo_lo[s];
-          rB = a.nright[s];
           if (s == A) open = true;
           else {
-            acc = decide(hiA, loA, hiB, loB, A, s, a, st_fb);
+            acc = decide(hiA, loA, hiB, loB, A, s, a, st_fb, rx, ry, rz);
             open = !acc;
           }
         }
         const unsigned bacc = __ballot_sync(SFMM_FULL, acc);
         const int nacc = __popc(bacc);
         nacc_tot += nacc;
-        if (acc) s_queue[warp][nq + __popc(bacc & lt)] = s;
+        if (acc) {
+          const int q = nq + __popc(bacc & lt);
+          s_queue[warp][q] = s;
+          if constexpr (F32) s_qr[warp][q] = make_float4(rx, ry, rz, 0.f);
+        }
         nq += nacc;
         const bool sleaf = open && rB < 0;
         const bool sint = open && rB >= 0;
@@ -178,8 +207,12 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 5 : 1) k_walk_level
       while (nq >= 32 || (!more && nq > 0)) {
         const int take = min(nq, 32);
         const int src = (lane < take) ? s_queue[warp][nq - take + lane] : -1;
+        float4 rq = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (F32) {
+          if (lane < take) rq = s_qr[warp][nq - take + lane];
+        }
         __syncwarp();
-        m2l_eval<P, F32>(src, hiA, loA, cAx, cAy, cAz, a, C);
+        m2l_eval<P, F32>(src, hiA, loA, cAx, cAy, cAz, a, C, rq);
         nq -= take;
       }
       if (!more) break;
