@@ -353,6 +353,37 @@ def config_block(torch, local, flush, name, steps, fp32_peak, hbm_peak):
             "stage_rooflines": stage_rooflines(st, n, fp32_peak, hbm_peak), "generate_s": t_gen}
 
 
+def leapfrog_block(torch, local, orbits=20, steps_per_orbit=400, n=13000):
+    """Gravity-only leapfrog of the orbiting binary polytrope (the gravity
+    part of the binary test of Sect. 4): ~1.3e4 particles, 20 orbits at
+    400 steps per orbit, records every 1% of the period; linear momentum
+    drift and angular momentum fluctuation in both forms."""
+    import workloads
+    from paper_2602_05804_gb300 import sfmm
+
+    pos, vel, m, h = workloads.binary_orbit(n, 1006)
+    period = workloads.orbital_period()
+    dt = period / steps_per_orbit
+    nsteps = orbits * steps_per_orbit
+    out = {"n": n, "orbits": orbits, "steps": nsteps, "dt": dt, "theta": 0.5, "order": 2, "leaf_size": 16}
+    for prec in ("fp64", "fp32"):
+        s = sfmm.Solver(local, prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, rec = s.leapfrog(pos, vel, m, h, 16, 0.5, 2, dt, nsteps, record_every=steps_per_orbit // 100)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        s.close()
+        scale = rec[:, 7].max()
+        lz = rec[:, 6]
+        out[prec] = {"ms_per_step": 1e3 * wall / nsteps,
+                     "max_abs_linear_momentum": float(np.abs(rec[:, 1:4]).max()),
+                     "max_linear_momentum_drift_rel": float(np.abs(rec[:, 1:4] - rec[0, 1:4]).max() / scale),
+                     "angular_momentum_rel_std": float(np.std(lz) / abs(lz[0])),
+                     "angular_momentum_rel_drift": float((lz[-1] - lz[0]) / abs(lz[0]))}
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -439,6 +470,7 @@ def run_gpu(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, unit counts x max clock
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    leapfrog = None if args.no_leapfrog else leapfrog_block(torch, local)
     configs = None
     if not args.no_configs:
         configs = {name: config_block(torch, local, flush, name, max(1, min(args.steps, 5)), fp32_peak, hbm_peak)
@@ -510,6 +542,7 @@ def run_gpu(args):
         "ensemble_256": ensemble,
         "stage_rooflines": stage_rooflines(st32, w["n"], fp32_peak, hbm_peak),
         "configs": configs,
+        "leapfrog_binary": leapfrog,
         "e2e": {"value": ws * w["n"] / (e2e_ms * 1e-3), "unit": "particles/s",
                 "h2d_bytes_per_step": int(w["n"] * 40), "d2h_bytes_per_step": int(w["n"] * 32)},
         "gpu_launches": int(st32["kernel_launches_per_step"] * args.steps),
@@ -536,6 +569,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--no-leapfrog", action="store_true", help="skip the 20-orbit binary leapfrog")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the binary-polytrope (2e6) and clustered-cloud (1.6e7) measurements")
     ap.add_argument("--workload", default="plummer_1e6",

@@ -212,6 +212,31 @@ int sfmm_moments_export(sfmm_ctx* ctx, int order, double* Q, int32_t* mi);
 int sfmm_lists(sfmm_ctx* ctx, double theta, int64_t* m2l_off, int32_t* m2l_level, int32_t* m2l_src,
                int64_t cap_m2l, int64_t* p2p_off, int32_t* p2p_src, int64_t cap_p2p);
 
+/* Gravity-only leapfrog of one particle set with the SFMM forces (the
+ * gravity part of the binary-polytrope test of Sect. 4: every pair force is
+ * antisymmetric, so the total linear momentum is conserved to rounding).
+ * Kick-drift-kick steps: v += a dt/2, x += v dt, rebuild the tree at the new
+ * positions, a = SFMM acceleration, v += a dt/2.
+ *   n            number of particles, as in sfmm_build
+ *   pos, vel     device, n x 3 row-major FP64, caller order; advanced in
+ *                place by nsteps steps
+ *   mass, h      device, n; h stays fixed
+ *   leaf_size, theta, order   as in sfmm_build / sfmm_gravity
+ *   dt           step length (finite, may be negative: steps run backwards)
+ *   nsteps       >= 0
+ *   record_every >= 1; a record is taken before the first step and after
+ *                every record_every-th step
+ *   record       host, (nsteps / record_every + 1) x 8 doubles, or NULL:
+ *                t, P = sum m v (3), L = sum m x cross v (3), sum |m v_d|
+ *                (over particles and components); FP64 sums in a fixed order
+ *   acc          device n x 3 or NULL: the accelerations of the final state
+ * The context holds the tree of the final positions afterwards.  Errors: as
+ * sfmm_build and sfmm_gravity, EINVAL for bad arguments; after an error pos
+ * and vel are left part-way through the failed step. */
+int sfmm_leapfrog(sfmm_ctx* ctx, int64_t n, double* pos, double* vel, const double* mass, const double* h,
+                  int leaf_size, double theta, int order, double dt, int64_t nsteps, int64_t record_every,
+                  double* record, double* acc);
+
 /* Largest n accepted by sfmm_reduce_noalloc. */
 #define SFMM_NOALLOC_MAX_N 67108864
 

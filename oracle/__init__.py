@@ -19,6 +19,9 @@ Parity status per function (how each is pinned; see tests/test_oracle_*.py):
   sfmm (Algorithms 1-2)      pinned: theta = 0 equals the direct sum, list
                              symmetry, momentum to round-off, an independent
                              recursive dual-tree walk gives the same pairs
+  leapfrog (kick-drift-kick) pinned: exact time reversal, Kepler two-body
+                             orbit closes with O(dt^2) energy error, linear
+                             momentum constant to round-off
   softening pair rule        parity unpinned: the paper does not print how the
                              two smoothing lengths of a pair combine (mean of
                              the two kernels is the reading taken)
@@ -292,6 +295,33 @@ class Tree:
         if rc != 0:
             raise RuntimeError("oracle walk stack overflow")
         return mo, lv, src, po, ps
+
+
+def _momentum_record(t, x, v, m):
+    p = m[:, None] * v
+    return np.concatenate([[t], p.sum(0), np.cross(x, p).sum(0), [np.abs(p).sum()]])
+
+
+def leapfrog(pos, vel, m, h, theta, p=2, leaf_size=16, dt=0.01, nsteps=1, record_every=1, G=1.0, nthreads=0):
+    """Gravity-only kick-drift-kick leapfrog with these SFMM accelerations
+    (the integration of the binary-polytrope test, Sect. 4): v += a dt/2,
+    x += v dt, new tree and accelerations, v += a dt/2.  Returns (pos, vel,
+    records); a record (t, P = sum m v, L = sum m x cross v, sum |m v_d|) is
+    taken before the first step and after every record_every-th step."""
+    x = np.array(pos, dtype=np.float64, copy=True)
+    v = np.array(vel, dtype=np.float64, copy=True)
+    m = np.asarray(m, dtype=np.float64)
+    hdt = 0.5 * dt
+    a, _, _ = sfmm(x, m, h, theta, p, leaf_size, G=G, nthreads=nthreads)
+    recs = [_momentum_record(0.0, x, v, m)]
+    for s in range(1, int(nsteps) + 1):
+        v = v + a * hdt
+        x = x + v * dt
+        a, _, _ = sfmm(x, m, h, theta, p, leaf_size, G=G, nthreads=nthreads)
+        v = v + a * hdt
+        if s % record_every == 0:
+            recs.append(_momentum_record(s * dt, x, v, m))
+    return x, v, np.array(recs)
 
 
 def sfmm(pos, m, h, theta, p=2, leaf_size=10, G=1.0, self_potential=False, nthreads=0):

@@ -167,7 +167,8 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->Qf, &c->ring, &c->far, &c->arena, &c->p2p_off, &c->p2p_cnt, &c->counters,
                     &c->red_part, &c->dump, &c->nlu, &c->level_nodes, &c->level_off, &c->level_cur,
                     &c->cf_arena, &c->cf_off, &c->cf_cnt, &c->Tnode, &c->leaf_order, &c->sys_off,
-                    &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_leaf_off, &c->sys_sums};
+                    &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_leaf_off, &c->sys_sums,
+                    &c->p2p_extra, &c->p2p_split, &c->p2p_slist, &c->p2p_part, &c->lf_acc, &c->lf_part};
   for (DevBuf* b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);

@@ -82,6 +82,8 @@ struct sfmm_ctx {
   // near field: chunks of long neighbour lists (extra work items, per-leaf
   // slot base, split leaves, partial sums) and the list entries in use
   DevBuf p2p_extra, p2p_split, p2p_slist, p2p_part;
+  // leapfrog: accelerations, per-tile momentum partials and their sum
+  DevBuf lf_acc, lf_part;
   int64_t arena_used = 0;
   int64_t split_chunks = 0, split_lists = 0;  // from the walk: chunks of split lists, split lists
 

@@ -23,7 +23,7 @@ SFMM_FP64, SFMM_FP32 = 0, 1
 EXPORTS = ("sfmm_create", "sfmm_destroy", "sfmm_set_stream", "sfmm_set_option", "sfmm_build", "sfmm_gravity",
            "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
            "sfmm_lists", "sfmm_strerror", "sfmm_last_error", "sfmm_version", "sfmm_reduce_noalloc",
-           "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums")
+           "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums", "sfmm_leapfrog")
 SFMM_NOALLOC_MAX_N = 67108864
 
 
@@ -83,9 +83,10 @@ def load(path: str = LIB_PATH):
     lib.sfmm_batch_sums.argtypes = [P, i32, P]
     lib.sfmm_reduce_noalloc.argtypes = [i64, P, P, P, P, P]
     lib.sfmm_reduce_noalloc.restype = i32
+    lib.sfmm_leapfrog.argtypes = [P, i64, P, P, P, P, i32, dbl, i32, dbl, i64, i64, P, P]
     for name in ("sfmm_create", "sfmm_set_stream", "sfmm_set_option", "sfmm_build", "sfmm_gravity",
                  "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
-                 "sfmm_lists", "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums"):
+                 "sfmm_lists", "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums", "sfmm_leapfrog"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -202,6 +203,17 @@ def sfmm_batch_sums(ctx, nsys):
     return out
 
 
+def sfmm_leapfrog(ctx, n, pos, vel, mass, h, leaf_size, theta, order, dt, nsteps, record_every=1, acc=None):
+    """Leapfrog in place on device arrays; returns the momentum records
+    (rows: t, P (3), L (3), sum |m v_d|)."""
+    nrec = int(nsteps) // int(record_every) + 1 if int(record_every) >= 1 and int(nsteps) >= 0 else 1
+    rec = np.empty((nrec, 8))
+    _check(load().sfmm_leapfrog(ctx, int(n), _ptr(pos), _ptr(vel), _ptr(mass), _ptr(h), int(leaf_size),
+                                float(theta), int(order), float(dt), int(nsteps), int(record_every), _ptr(rec),
+                                _ptr(acc)), ctx)
+    return rec
+
+
 def sfmm_reduce_noalloc(n, mass, acc, pot, out, stream=None):
     """Momentum/energy sums over device arrays without any device allocation
     (see include/sfmm.h); ``out`` is a device buffer of 5 float64."""
@@ -288,6 +300,17 @@ class Solver:
 
     def batch_sums(self):
         return sfmm_batch_sums(self.ctx, self.nsys)
+
+    def leapfrog(self, pos, vel, mass, h, leaf_size, theta, order, dt, nsteps, record_every=1):
+        """Kick-drift-kick steps on host or device arrays.  Returns (pos, vel,
+        records) as device tensors and a numpy array of records."""
+        n = int(mass.shape[0])
+        pos, vel = self._dev(pos, (n, 3)).clone(), self._dev(vel, (n, 3)).clone()
+        mass, h = self._dev(mass, (n,)), self._dev(h, (n,))
+        rec = sfmm_leapfrog(self.ctx, int(mass.shape[0]), pos, vel, mass, h, leaf_size, theta, order, dt, nsteps,
+                            record_every)
+        self.n = int(mass.shape[0])
+        return pos, vel, rec
 
     def solve_host(self, pos, mass, h, leaf_size, theta, order, acc, pot):
         """Host (numpy or pinned torch CPU) buffers in and out."""

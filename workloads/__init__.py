@@ -149,6 +149,28 @@ def binary_polytrope(n: int, seed: int, q: float = 0.3, r1: float = 1.0, r2: flo
     return pos, m, _hsml(m, rho)
 
 
+def binary_orbit(n: int, seed: int, q: float = 0.3, r1: float = 1.0, r2: float = 0.6, sep: float = 3.0,
+                 G: float = 1.0):
+    """The binary polytrope set moving on a circular orbit: every particle of
+    a star gets that star's orbital velocity (along y, perpendicular to the
+    separation on x), v_rel = sqrt(G M / sep) with M the total mass and the
+    centre of mass at rest.  Returns (pos, vel, m, h); the orbital period is
+    2 pi sqrt(sep^3 / (G M))."""
+    pos, m, h = binary_polytrope(n, seed, q, r1, r2, sep)
+    n1 = int(round(n * (1.0 / (1.0 + q))))
+    m1, m2 = m[:n1].sum(), m[n1:].sum()
+    mt = m1 + m2
+    v_rel = math.sqrt(G * mt / sep)
+    vel = np.zeros((n, 3))
+    vel[:n1, 1] = -v_rel * m2 / mt
+    vel[n1:, 1] = v_rel * m1 / mt
+    return pos, vel, m, h
+
+
+def orbital_period(sep: float = 3.0, mass: float = 1.0, G: float = 1.0) -> float:
+    return 2.0 * math.pi * math.sqrt(sep ** 3 / (G * mass))
+
+
 def clustered_cloud(n: int, seed: int, nclump: int = 64, clump_scale: float = 0.02,
                     halo_frac: float = 0.7, sigma: float = 1.0):
     """Plummer halo (a=1, truncated at 20a) holding ``halo_frac`` of the mass
