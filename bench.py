@@ -384,6 +384,43 @@ def leapfrog_block(torch, local, orbits=20, steps_per_orbit=400, n=13000):
     return out
 
 
+def accuracy_sweep_block(torch, local, n=100_000, thetas=None, trees=("morton",)):
+    """Force accuracy against the direct sum (the opening-angle study of
+    Sect. 4.1): Plummer and uniform spheres of 10^5 particles, theta from 0.1
+    to 0.6 in steps of 0.05, p = 2, leaf 16; mean, maximum and 10th
+    percentile of |a - a_direct| / |a_direct| over all particles, for both
+    forms (the direct sum is the oracle's, on the host cores)."""
+    import oracle
+    import workloads
+    from paper_2602_05804_gb300 import sfmm
+
+    thetas = thetas or [round(0.1 + 0.05 * k, 2) for k in range(11)]
+    out = {"n": n, "order": 2, "leaf_size": 16, "thetas": thetas}
+    for prof, gen in (("plummer", workloads.plummer), ("uniform", workloads.uniform_sphere)):
+        pos, m, h = gen(n, 1100 + len(prof))
+        t0 = time.perf_counter()
+        a_d, _ = oracle.direct(pos, m, h)
+        t_direct = time.perf_counter() - t0
+        an = np.linalg.norm(a_d, axis=1)
+        res = {"direct_s": t_direct}
+        for tree in trees:
+            for prec in ("fp64", "fp32"):
+                s = sfmm.Solver(local, prec)
+                if tree != "morton":
+                    s.set_option("tree", 1.0)
+                s.build(pos, m, h, 16)
+                rows = []
+                for th in thetas:
+                    acc, _ = s.gravity(th, 2, want_pot=False)
+                    e = np.linalg.norm(acc.cpu().numpy() - a_d, axis=1) / an
+                    rows.append([float(e.mean()), float(e.max()), float(np.percentile(e, 10))])
+                s.close()
+                res["%s_%s" % (tree, prec)] = {"mean": [r[0] for r in rows], "max": [r[1] for r in rows],
+                                               "p10": [r[2] for r in rows]}
+        out[prof] = res
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -471,6 +508,7 @@ def run_gpu(args):
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, unit counts x max clock
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     leapfrog = None if args.no_leapfrog else leapfrog_block(torch, local)
+    accuracy = None if args.no_accuracy else accuracy_sweep_block(torch, local)
     configs = None
     if not args.no_configs:
         configs = {name: config_block(torch, local, flush, name, max(1, min(args.steps, 5)), fp32_peak, hbm_peak)
@@ -543,6 +581,7 @@ def run_gpu(args):
         "stage_rooflines": stage_rooflines(st32, w["n"], fp32_peak, hbm_peak),
         "configs": configs,
         "leapfrog_binary": leapfrog,
+        "accuracy_sweep": accuracy,
         "e2e": {"value": ws * w["n"] / (e2e_ms * 1e-3), "unit": "particles/s",
                 "h2d_bytes_per_step": int(w["n"] * 40), "d2h_bytes_per_step": int(w["n"] * 32)},
         "gpu_launches": int(st32["kernel_launches_per_step"] * args.steps),
@@ -570,6 +609,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--no-leapfrog", action="store_true", help="skip the 20-orbit binary leapfrog")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the theta sweep against the direct sum")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the binary-polytrope (2e6) and clustered-cloud (1.6e7) measurements")
     ap.add_argument("--workload", default="plummer_1e6",

@@ -65,6 +65,8 @@ def _load():
             i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
             lib.orc_build.restype = P
             lib.orc_build.argtypes = [i64, P, P, P, i32, i32, i32]
+            lib.orc_build_kd.restype = P
+            lib.orc_build_kd.argtypes = [i64, P, P, P, i32, i32, i32]
             lib.orc_free.argtypes = [P]
             lib.orc_tree_nnodes.restype = i64
             lib.orc_tree_nnodes.argtypes = [P]
@@ -223,15 +225,18 @@ def full_index(gamma):
 class Tree:
     """Oracle tree: sorted particles, nodes in pre-order, direct moments."""
 
-    def __init__(self, pos, m, h, leaf_size, p=2, nthreads=0):
+    def __init__(self, pos, m, h, leaf_size, p=2, nthreads=0, tree="morton"):
         self._lib = _load()
+        if tree not in ("morton", "kd"):
+            raise ValueError("tree must be 'morton' or 'kd'")
+        self.tree = tree
         self.pos = _f64(pos, (-1, 3))
         self.m, self.h = _f64(m), _f64(h)
         self.n = len(self.m)
         self.p = int(p)
         self.leaf_size = int(leaf_size)
-        ptr = self._lib.orc_build(self.n, _p(self.pos), _p(self.m), _p(self.h), self.leaf_size, self.p,
-                                  int(nthreads))
+        build = self._lib.orc_build_kd if tree == "kd" else self._lib.orc_build
+        ptr = build(self.n, _p(self.pos), _p(self.m), _p(self.h), self.leaf_size, self.p, int(nthreads))
         if not ptr:
             raise ValueError("oracle tree build rejected its arguments")
         self._ptr = ctypes.c_void_p(ptr)
@@ -324,8 +329,8 @@ def leapfrog(pos, vel, m, h, theta, p=2, leaf_size=16, dt=0.01, nsteps=1, record
     return x, v, np.array(recs)
 
 
-def sfmm(pos, m, h, theta, p=2, leaf_size=10, G=1.0, self_potential=False, nthreads=0):
+def sfmm(pos, m, h, theta, p=2, leaf_size=10, G=1.0, self_potential=False, nthreads=0, tree="morton"):
     """Convenience: build the oracle tree and run the SFMM; returns
     (acc, pot, stats)."""
-    t = Tree(pos, m, h, leaf_size, p, nthreads=nthreads)
+    t = Tree(pos, m, h, leaf_size, p, nthreads=nthreads, tree=tree)
     return t.sfmm(theta, G=G, self_potential=self_potential, nthreads=nthreads)

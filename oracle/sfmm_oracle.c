@@ -28,6 +28,7 @@
  *   orc_m2l_eval      dM_k / M_k expansion about two centres (Eq. dmkdeffmm, Sect. 2.2)
  *   orc_l2l           translation of gravitational moments (Eq. gravmtranslat, App. A.2)
  *   orc_build         tree, node centres/sizes/h_max/moments (Sect. 3)
+ *   orc_build_kd      the same over a centre-of-mass-pivot kd tree (Sect. 3)
  *   orc_sfmm          Algorithms 1 and 2, propagation, evaluation, P2P (Sect. 3)
  *
  * Readings where the paper is silent or garbled (each is stated in the
@@ -601,6 +602,111 @@ orc_tree* orc_build(int64_t n, const double* pos, const double* m, const double*
     t->depth = (int32_t*)malloc(sizeof(int32_t) * cap);
     t->nnodes = 0;
     build_rec(t, 0, n, 0, -1);
+    int64_t nn = t->nnodes;
+    t->centre = (double*)malloc(sizeof(double) * 3 * nn);
+    t->size = (double*)malloc(sizeof(double) * nn);
+    t->hmax = (double*)malloc(sizeof(double) * nn);
+    t->mass = (double*)malloc(sizeof(double) * nn);
+    t->Q = (double*)malloc(sizeof(double) * nn * packed_size(p));
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t id = 0; id < nn; ++id) node_props(t, id);
+    t->nleaves = 0;
+    for (int64_t id = 0; id < nn; ++id) if (t->left[id] < 0) t->nleaves++;
+    t->leaves = (int32_t*)malloc(sizeof(int32_t) * t->nleaves);
+    int64_t k = 0;
+    for (int64_t id = 0; id < nn; ++id) if (t->left[id] < 0) t->leaves[k++] = (int32_t)id;
+    return t;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Centre-of-mass-pivot kd tree (Sect. 3: "the centre of mass ... as the     */
+/* pivot position to build the kd-tree"; the axis rule is not printed).      */
+/* Reading: split along the axis of largest extent of the node's particles   */
+/* (ties: lowest axis) at the node's centre of mass on that axis; particles  */
+/* below the pivot go left, the others right, both keeping their order.  If  */
+/* one side would be empty the node is split at the middle of its order.     */
+/* ------------------------------------------------------------------------ */
+
+static int64_t build_kd_rec(orc_tree* t, int64_t first, int64_t count, int depth, int32_t parent,
+                            double* tx, double* tm, double* th, int64_t* tp)
+{
+    int64_t id = t->nnodes++;
+    t->first[id] = (int32_t)first;
+    t->count[id] = (int32_t)count;
+    t->parent[id] = parent;
+    t->depth[id] = depth;
+    t->left[id] = -1;
+    t->right[id] = -1;
+    if (count <= t->leaf_size) return id;
+    double mn[3], mx[3], M = 0.0, sm[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < 3; ++c) { mn[c] = t->x[3 * first + c]; mx[c] = mn[c]; }
+    for (int64_t j = first; j < first + count; ++j) {
+        M += t->m[j];
+        for (int c = 0; c < 3; ++c) {
+            double v = t->x[3 * j + c];
+            sm[c] += t->m[j] * v;
+            if (v < mn[c]) mn[c] = v;
+            if (v > mx[c]) mx[c] = v;
+        }
+    }
+    int axis = 0;
+    for (int c = 1; c < 3; ++c) if (mx[c] - mn[c] > mx[axis] - mn[axis]) axis = c;
+    double pivot = sm[axis] / M;
+    int64_t nl = 0;
+    for (int64_t j = first; j < first + count; ++j) if (t->x[3 * j + axis] < pivot) ++nl;
+    if (nl == 0 || nl == count) {
+        nl = count / 2;  /* degenerate pivot: keep the order, split in the middle */
+    } else {
+        int64_t a = 0, b = nl;
+        for (int64_t j = first; j < first + count; ++j) {
+            int64_t d = (t->x[3 * j + axis] < pivot) ? a++ : b++;
+            tx[3 * d] = t->x[3 * j]; tx[3 * d + 1] = t->x[3 * j + 1]; tx[3 * d + 2] = t->x[3 * j + 2];
+            tm[d] = t->m[j]; th[d] = t->h[j]; tp[d] = t->perm[j];
+        }
+        memcpy(t->x + 3 * first, tx, sizeof(double) * 3 * count);
+        memcpy(t->m + first, tm, sizeof(double) * count);
+        memcpy(t->h + first, th, sizeof(double) * count);
+        memcpy(t->perm + first, tp, sizeof(int64_t) * count);
+    }
+    int64_t l = build_kd_rec(t, first, nl, depth + 1, (int32_t)id, tx, tm, th, tp);
+    int64_t r = build_kd_rec(t, first + nl, count - nl, depth + 1, (int32_t)id, tx, tm, th, tp);
+    t->left[id] = (int32_t)l;
+    t->right[id] = (int32_t)r;
+    return id;
+}
+
+orc_tree* orc_build_kd(int64_t n, const double* pos, const double* m, const double* h,
+                       int leaf_size, int p, int nthreads)
+{
+    if (n < 1 || leaf_size < 1 || p < 0 || p > ORC_PMAX) return NULL;
+    orc_tree* t = (orc_tree*)calloc(1, sizeof(orc_tree));
+    t->n = n; t->leaf_size = leaf_size; t->p = p;
+    t->x = (double*)malloc(sizeof(double) * 3 * n);
+    t->m = (double*)malloc(sizeof(double) * n);
+    t->h = (double*)malloc(sizeof(double) * n);
+    t->perm = (int64_t*)malloc(sizeof(int64_t) * n);
+    t->key = (uint64_t*)calloc((size_t)n, sizeof(uint64_t));  /* no keys in a kd tree */
+    memcpy(t->x, pos, sizeof(double) * 3 * n);
+    memcpy(t->m, m, sizeof(double) * n);
+    memcpy(t->h, h, sizeof(double) * n);
+    for (int64_t i = 0; i < n; ++i) t->perm[i] = i;
+    int64_t cap = 2 * n + 1;
+    t->first = (int32_t*)malloc(sizeof(int32_t) * cap);
+    t->count = (int32_t*)malloc(sizeof(int32_t) * cap);
+    t->left = (int32_t*)malloc(sizeof(int32_t) * cap);
+    t->right = (int32_t*)malloc(sizeof(int32_t) * cap);
+    t->parent = (int32_t*)malloc(sizeof(int32_t) * cap);
+    t->depth = (int32_t*)malloc(sizeof(int32_t) * cap);
+    double* tx = (double*)malloc(sizeof(double) * 3 * n);
+    double* tm = (double*)malloc(sizeof(double) * n);
+    double* th = (double*)malloc(sizeof(double) * n);
+    int64_t* tp = (int64_t*)malloc(sizeof(int64_t) * n);
+    t->nnodes = 0;
+    build_kd_rec(t, 0, n, 0, -1, tx, tm, th, tp);
+    free(tx); free(tm); free(th); free(tp);
     int64_t nn = t->nnodes;
     t->centre = (double*)malloc(sizeof(double) * 3 * nn);
     t->size = (double*)malloc(sizeof(double) * nn);
