@@ -508,7 +508,7 @@ def run_gpu(args):
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, unit counts x max clock
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     leapfrog = None if args.no_leapfrog else leapfrog_block(torch, local)
-    accuracy = None if args.no_accuracy else accuracy_sweep_block(torch, local)
+    accuracy = None if args.no_accuracy else accuracy_sweep_block(torch, local, trees=("morton", "kd"))
     configs = None
     if not args.no_configs:
         configs = {name: config_block(torch, local, flush, name, max(1, min(args.steps, 5)), fp32_peak, hbm_peak)

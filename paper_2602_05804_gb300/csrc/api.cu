@@ -168,7 +168,8 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->red_part, &c->dump, &c->nlu, &c->level_nodes, &c->level_off, &c->level_cur,
                     &c->cf_arena, &c->cf_off, &c->cf_cnt, &c->Tnode, &c->leaf_order, &c->sys_off,
                     &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_leaf_off, &c->sys_sums,
-                    &c->p2p_extra, &c->p2p_split, &c->p2p_slist, &c->p2p_part, &c->lf_acc, &c->lf_part};
+                    &c->p2p_extra, &c->p2p_split, &c->p2p_slist, &c->p2p_part, &c->lf_acc, &c->lf_part,
+                    &c->kd_ord, &c->kd_node, &c->kd_act, &c->kd_work, &c->kd_chunk, &c->kd_part, &c->kd_split};
   for (DevBuf* b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -214,6 +215,9 @@ int sfmm_set_option(sfmm_ctx* c, const char* key, double v) {
   } else if (!strcmp(key, "walk")) {
     if (v != 0.0 && v != 1.0) return set_error(c, SFMM_EINVAL, "walk: 0 (per-leaf replay) or 1 (per-node shared pairs)");
     c->walk_mode = (int)v;
+  } else if (!strcmp(key, "tree")) {
+    if (v != 0.0 && v != 1.0) return set_error(c, SFMM_EINVAL, "tree: 0 (Morton radix tree) or 1 (centre-of-mass kd tree)");
+    c->tree_kind = (int)v;
   } else if (!strcmp(key, "profile")) {
     c->profile = (v != 0.0);
   } else {
@@ -305,6 +309,7 @@ int sfmm_build_batch(sfmm_ctx* c, int nsys, const int64_t* offsets, const double
   if (nsys < 1 || nsys > 65536 || !offsets) return set_error(c, SFMM_EINVAL, "nsys must be in [1, 65536]");
   if (!pos || !mass || !h) return set_error(c, SFMM_EINVAL, "NULL input pointer");
   if (offsets[0] != 0) return set_error(c, SFMM_EINVAL, "offsets[0] must be 0");
+  if (c->tree_kind != 0) return set_error(c, SFMM_ENOTIMPL, "batched builds use the Morton tree (option tree = 0)");
   for (int s = 0; s < nsys; ++s)
     if (offsets[s + 1] <= offsets[s]) return set_error(c, SFMM_EINVAL, "every system needs at least one particle");
   const int64_t n = offsets[nsys];

@@ -29,6 +29,7 @@ struct sfmm_ctx {
   int64_t list_capacity = 0;
   int64_t cf_capacity = 0;  // child-frontier arena entries per level parity (0 = automatic)
   int profile = 0;
+  int tree_kind = 0;        // 0: Morton radix tree, 1: centre-of-mass-pivot kd tree
 
   // built state
   bool built = false;
@@ -84,6 +85,8 @@ struct sfmm_ctx {
   DevBuf p2p_extra, p2p_split, p2p_slist, p2p_part;
   // leapfrog: accelerations, per-tile momentum partials and their sum
   DevBuf lf_acc, lf_part;
+  // kd-tree build: particle orders, breadth-first node records, level scratch
+  DevBuf kd_ord, kd_node, kd_act, kd_work, kd_chunk, kd_part, kd_split;
   int64_t arena_used = 0;
   int64_t split_chunks = 0, split_lists = 0;  // from the walk: chunks of split lists, split lists
 
@@ -103,6 +106,8 @@ int set_error(sfmm_ctx* c, int code, const char* msg);
 
 // tree.cu
 int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double* h);
+// kdtree.cu: kd-tree topology, sorted particles and pre-order node layout
+int build_kd_topology(sfmm_ctx* c, const double* pos, const double* mass, const double* h);
 int compute_depth(sfmm_ctx* c);
 int build_levels(sfmm_ctx* c);  // depth, level lists, leaves under each node
 

@@ -875,91 +875,99 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     k_bbox_seg<<<nsys, BB_NT, 0, st>>>(pos, mass, h, c->sys_off.as<int>(), bbox, c->d_status);
     ++c->nlaunch;
   }
-  k_morton<<<nblk(n, 256), 256, 0, st>>>(pos, n, bbox, psys, c->keys_a.as<uint64_t>(), c->idx_a.as<uint32_t>());
-  ++c->nlaunch;
-  SFMM_CUDA_TRY(cudaGetLastError());
-
-  // S2: radix sort, 8 passes of 8 bits (the top pass holds 7 key bits)
-  const int ntiles = (n + RS_TILE - 1) / RS_TILE;
-  if ((rc = c->sort_counts.ensure(sizeof(uint32_t) * 256 * (size_t)ntiles)) != SFMM_OK) return rc;
-  uint64_t *ka = c->keys_a.as<uint64_t>(), *kb = c->keys_b.as<uint64_t>();
-  uint32_t *va = c->idx_a.as<uint32_t>(), *vb = c->idx_b.as<uint32_t>();
-  // Morton passes, then (batches) the system id as the most significant digits:
-  // the result is ordered by (system, key, input index)
-  int sys_bits = 0;
-  while ((1 << sys_bits) < nsys) ++sys_bits;
-  const int npass = 8 + (sys_bits + 7) / 8;
-  for (int pass = 0; pass < npass; ++pass) {
-    const bool by_sys = pass >= 8;
-    const int shift = by_sys ? 8 * (pass - 8) : 8 * pass;
-    const int* dsys = by_sys ? psys : nullptr;
-    k_rs_hist<<<ntiles, RS_NT, 0, st>>>(ka, va, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
-    ++c->nlaunch;
-    SFMM_CUDA_TRY(cudaGetLastError());
-    if ((rc = exclusive_scan_u32(c, c->sort_counts.as<uint32_t>(), (int64_t)256 * ntiles, nullptr))) return rc;
-    k_rs_scatter<<<ntiles, RS_NT, 0, st>>>(ka, va, kb, vb, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
-    ++c->nlaunch;
-    SFMM_CUDA_TRY(cudaGetLastError());
-    std::swap(ka, kb);
-    std::swap(va, vb);
-  }
-  // the sorted data is in ka / va
-  k_gather<<<nblk(n, 256), 256, 0, st>>>(pos, mass, h, va, n, c->px.as<double>(), c->py.as<double>(),
-                                         c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(),
-                                         c->perm.as<int>());
-  ++c->nlaunch;
-  SFMM_CUDA_TRY(cudaGetLastError());
-
-  // S3: radix tree, collapse, pre-order
   int nnodes = 1;
-  if (n == 1) {
-    int one = 1, zero = 0, minus = -1;
-    SFMM_CUDA_TRY(cudaMemcpyAsync(c->nfirst.as<int>(), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-    SFMM_CUDA_TRY(cudaMemcpyAsync(c->ncount.as<int>(), &one, sizeof(int), cudaMemcpyHostToDevice, st));
-    SFMM_CUDA_TRY(cudaMemcpyAsync(c->nright.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
-    SFMM_CUDA_TRY(cudaMemcpyAsync(c->nparent.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
-    SFMM_CUDA_TRY(cudaMemcpyAsync(c->leaf_node.as<int>(), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-    // leaf numbers of the nodes (exclusive scan of the leaf flags): node 0 is leaf 0
-    static const uint32_t leaf_scan[2] = {0u, 1u};
-    SFMM_CUDA_TRY(cudaMemcpyAsync(c->isleaf.p, leaf_scan, sizeof(leaf_scan), cudaMemcpyHostToDevice, st));
-    c->nnodes = 1;
-    c->nleaves = 1;
+  uint64_t* ka_final = c->keys_a.as<uint64_t>();  // where the sorted keys end up
+  if (c->tree_kind == 1) {
+    // centre-of-mass-pivot kd tree: topology, sorted particles, pre-order nodes
+    if ((rc = build_kd_topology(c, pos, mass, h))) return rc;
+    nnodes = c->nnodes;
   } else {
-    const SysView sv{psys, c->sys_off.as<int>()};
-    const LeafRule lr{psys, c->sys_lsz.as<int>(), c->leaf_size};
-    k_radix_tree<<<nblk(n - 1, 256), 256, 0, st>>>(ka, n, sv, c->k_left.as<int>(), c->k_right.as<int>(),
-                                                     c->k_first.as<int>(), c->k_last.as<int>(),
-                                                     c->par_int.as<int>(), c->par_leaf.as<int>());
-    ++c->nlaunch;
-    SFMM_CUDA_TRY(cudaMemsetAsync(c->chain.p, 0, sizeof(uint32_t) * (n + 1), st));
-    k_mark<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_first.as<int>(), c->k_last.as<int>(),
-                                         c->par_int.as<int>(), c->par_leaf.as<int>(), c->chain.as<uint32_t>());
+    k_morton<<<nblk(n, 256), 256, 0, st>>>(pos, n, bbox, psys, c->keys_a.as<uint64_t>(), c->idx_a.as<uint32_t>());
     ++c->nlaunch;
     SFMM_CUDA_TRY(cudaGetLastError());
-    if ((rc = exclusive_scan_u32(c, c->chain.as<uint32_t>(), n, totals))) return rc;
-    k_preorder<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_first.as<int>(), c->k_last.as<int>(),
-                                             c->par_int.as<int>(), c->par_leaf.as<int>(),
-                                             c->chain.as<uint32_t>(), c->pre_int.as<int>(), c->pre_leaf.as<int>());
+
+    // S2: radix sort, 8 passes of 8 bits (the top pass holds 7 key bits)
+    const int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    if ((rc = c->sort_counts.ensure(sizeof(uint32_t) * 256 * (size_t)ntiles)) != SFMM_OK) return rc;
+    uint64_t *ka = c->keys_a.as<uint64_t>(), *kb = c->keys_b.as<uint64_t>();
+    uint32_t *va = c->idx_a.as<uint32_t>(), *vb = c->idx_b.as<uint32_t>();
+    // Morton passes, then (batches) the system id as the most significant digits:
+    // the result is ordered by (system, key, input index)
+    int sys_bits = 0;
+    while ((1 << sys_bits) < nsys) ++sys_bits;
+    const int npass = 8 + (sys_bits + 7) / 8;
+    for (int pass = 0; pass < npass; ++pass) {
+      const bool by_sys = pass >= 8;
+      const int shift = by_sys ? 8 * (pass - 8) : 8 * pass;
+      const int* dsys = by_sys ? psys : nullptr;
+      k_rs_hist<<<ntiles, RS_NT, 0, st>>>(ka, va, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
+      ++c->nlaunch;
+      SFMM_CUDA_TRY(cudaGetLastError());
+      if ((rc = exclusive_scan_u32(c, c->sort_counts.as<uint32_t>(), (int64_t)256 * ntiles, nullptr))) return rc;
+      k_rs_scatter<<<ntiles, RS_NT, 0, st>>>(ka, va, kb, vb, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
+      ++c->nlaunch;
+      SFMM_CUDA_TRY(cudaGetLastError());
+      std::swap(ka, kb);
+      std::swap(va, vb);
+    }
+    // the sorted data is in ka / va
+    ka_final = ka;
+    k_gather<<<nblk(n, 256), 256, 0, st>>>(pos, mass, h, va, n, c->px.as<double>(), c->py.as<double>(),
+                                           c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(),
+                                           c->perm.as<int>());
     ++c->nlaunch;
     SFMM_CUDA_TRY(cudaGetLastError());
-    uint32_t h_tot = 0;
-    SFMM_CUDA_TRY(cudaMemcpyAsync(&h_tot, totals, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    SFMM_CUDA_TRY(cudaStreamSynchronize(st));
-    nnodes = (int)h_tot;
-    c->nnodes = nnodes;
-    k_fill_nodes<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_left.as<int>(), c->k_right.as<int>(),
-                                               c->k_first.as<int>(), c->k_last.as<int>(), c->par_int.as<int>(),
-                                               c->par_leaf.as<int>(), c->pre_int.as<int>(), c->pre_leaf.as<int>(),
-                                               c->nfirst.as<int>(), c->ncount.as<int>(), c->nright.as<int>(),
-                                               c->nparent.as<int>(), c->isleaf.as<uint32_t>(), c->d_status);
-    ++c->nlaunch;
-    SFMM_CUDA_TRY(cudaGetLastError());
-    if ((rc = exclusive_scan_u32(c, c->isleaf.as<uint32_t>(), nnodes, totals + 1))) return rc;
-    k_leaf_list<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->nright.as<int>(), c->isleaf.as<uint32_t>(),
-                                                   c->leaf_node.as<int>());
-    ++c->nlaunch;
-    SFMM_CUDA_TRY(cudaGetLastError());
-    c->nleaves = (nnodes + 1) / 2;  // full binary tree
+
+    // S3: radix tree, collapse, pre-order
+    if (n == 1) {
+      int one = 1, zero = 0, minus = -1;
+      SFMM_CUDA_TRY(cudaMemcpyAsync(c->nfirst.as<int>(), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+      SFMM_CUDA_TRY(cudaMemcpyAsync(c->ncount.as<int>(), &one, sizeof(int), cudaMemcpyHostToDevice, st));
+      SFMM_CUDA_TRY(cudaMemcpyAsync(c->nright.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
+      SFMM_CUDA_TRY(cudaMemcpyAsync(c->nparent.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
+      SFMM_CUDA_TRY(cudaMemcpyAsync(c->leaf_node.as<int>(), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+      // leaf numbers of the nodes (exclusive scan of the leaf flags): node 0 is leaf 0
+      static const uint32_t leaf_scan[2] = {0u, 1u};
+      SFMM_CUDA_TRY(cudaMemcpyAsync(c->isleaf.p, leaf_scan, sizeof(leaf_scan), cudaMemcpyHostToDevice, st));
+      c->nnodes = 1;
+      c->nleaves = 1;
+    } else {
+      const SysView sv{psys, c->sys_off.as<int>()};
+      const LeafRule lr{psys, c->sys_lsz.as<int>(), c->leaf_size};
+      k_radix_tree<<<nblk(n - 1, 256), 256, 0, st>>>(ka, n, sv, c->k_left.as<int>(), c->k_right.as<int>(),
+                                                       c->k_first.as<int>(), c->k_last.as<int>(),
+                                                       c->par_int.as<int>(), c->par_leaf.as<int>());
+      ++c->nlaunch;
+      SFMM_CUDA_TRY(cudaMemsetAsync(c->chain.p, 0, sizeof(uint32_t) * (n + 1), st));
+      k_mark<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_first.as<int>(), c->k_last.as<int>(),
+                                           c->par_int.as<int>(), c->par_leaf.as<int>(), c->chain.as<uint32_t>());
+      ++c->nlaunch;
+      SFMM_CUDA_TRY(cudaGetLastError());
+      if ((rc = exclusive_scan_u32(c, c->chain.as<uint32_t>(), n, totals))) return rc;
+      k_preorder<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_first.as<int>(), c->k_last.as<int>(),
+                                               c->par_int.as<int>(), c->par_leaf.as<int>(),
+                                               c->chain.as<uint32_t>(), c->pre_int.as<int>(), c->pre_leaf.as<int>());
+      ++c->nlaunch;
+      SFMM_CUDA_TRY(cudaGetLastError());
+      uint32_t h_tot = 0;
+      SFMM_CUDA_TRY(cudaMemcpyAsync(&h_tot, totals, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      SFMM_CUDA_TRY(cudaStreamSynchronize(st));
+      nnodes = (int)h_tot;
+      c->nnodes = nnodes;
+      k_fill_nodes<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_left.as<int>(), c->k_right.as<int>(),
+                                                 c->k_first.as<int>(), c->k_last.as<int>(), c->par_int.as<int>(),
+                                                 c->par_leaf.as<int>(), c->pre_int.as<int>(), c->pre_leaf.as<int>(),
+                                                 c->nfirst.as<int>(), c->ncount.as<int>(), c->nright.as<int>(),
+                                                 c->nparent.as<int>(), c->isleaf.as<uint32_t>(), c->d_status);
+      ++c->nlaunch;
+      SFMM_CUDA_TRY(cudaGetLastError());
+      if ((rc = exclusive_scan_u32(c, c->isleaf.as<uint32_t>(), nnodes, totals + 1))) return rc;
+      k_leaf_list<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->nright.as<int>(), c->isleaf.as<uint32_t>(),
+                                                     c->leaf_node.as<int>());
+      ++c->nlaunch;
+      SFMM_CUDA_TRY(cudaGetLastError());
+      c->nleaves = (nnodes + 1) / 2;  // full binary tree
+    }
   }
   const int nl = c->nleaves;
   // walk parents, system roots and leaf ranges of the systems
@@ -1001,9 +1009,9 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
                                                 c->prel.as<float4>(), c->ph32.as<float>(), c->phh.as<float2>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
-  if (c->keys_a.p != (void*)ka) {
+  if (c->keys_a.p != (void*)ka_final) {
     // keep the sorted keys in keys_a for export (even number of passes: no-op)
-    SFMM_CUDA_TRY(cudaMemcpyAsync(c->keys_a.p, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->keys_a.p, ka_final, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
   }
   return SFMM_OK;
 }
