@@ -489,15 +489,26 @@ def run_gpu(args):
     # the other walk on the same workload (same interactions, same results up
     # to summation order): the per-leaf replay of Algorithm 1 as printed, or the
     # per-node shared pairs
-    other = sfmm.Solver(local, "fp32", profile=1, walk=1 - args.walk)
+    other_mode = 0 if args.walk != 0 else 1
+    other = sfmm.Solver(local, "fp32", profile=1, walk=other_mode)
     ms_o, st_o = time_steps(torch, other, pos_d, m_d, h_d, acc, pot, w, w["theta"], max(1, min(args.steps, 3)), 1,
                             flush)
     other.close()
-    other_walk = {"walk": "per-leaf replay (Algorithm 1)" if args.walk == 1 else "per-node shared pairs",
+    other_walk = {"walk": "per-leaf replay (Algorithm 1)" if other_mode == 0 else "per-node shared pairs",
                   "particles_per_s": ws * w["n"] / (np.mean(ms_o) * 1e-3), "ms_per_step": float(np.mean(ms_o)),
                   "stage_ms": {"build": st_o["ms_build"], "moments": st_o["ms_moments"], "walk": st_o["ms_walk"],
                                "p2p": st_o["ms_p2p"]},
                   "m2l": st_o["m2l"], "m2l_unique": st_o["m2l_unique"], "p2p_pairs": st_o["p2p_pairs"]}
+
+    # one-sided symmetric pairs (walk mode 2): one D per pair for both sides
+    sym = sfmm.Solver(local, "fp32", profile=1, walk=2)
+    ms_s, st_s = time_steps(torch, sym, pos_d, m_d, h_d, acc, pot, w, w["theta"], max(1, min(args.steps, 3)), 1,
+                            flush)
+    sym.close()
+    sym_walk = {"walk": "one-sided symmetric pairs (D once per pair, FP64 atomics to the partner)",
+                "particles_per_s": ws * w["n"] / (np.mean(ms_s) * 1e-3), "ms_per_step": float(np.mean(ms_s)),
+                "stage_ms": {"build": st_s["ms_build"], "moments": st_s["ms_moments"], "walk": st_s["ms_walk"],
+                             "p2p": st_s["ms_p2p"]}}
 
     ensemble = None
     if not args.no_ensemble:
@@ -547,11 +558,11 @@ def run_gpu(args):
         src = _kernel_hash("p2p.cu")
     else:
         # the walk evaluates every unique pair once (shared) or once per leaf (replay)
-        nm2l = st32["m2l_unique"] if args.walk == 1 else st32["m2l"]
-        kname = "k_walk_level<2,FP32>" if args.walk == 1 else "k_walk<2,FP32>"
+        nm2l = st32["m2l_unique"] if args.walk >= 1 else st32["m2l"]
+        kname = "k_walk_level<2,FP32>" if args.walk >= 1 else "k_walk<2,FP32>"
         kms = st32["ms_walk"]
         achieved = nm2l * 136 / (kms * 1e-3) / 1e12
-        src = _kernel_hash("walk_shared.cu" if args.walk == 1 else "walk.cu", "walk_common.cuh", "expansion_gen.cuh")
+        src = _kernel_hash("walk_shared.cu" if args.walk >= 1 else "walk.cu", "walk_common.cuh", "expansion_gen.cuh")
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": _traffic(kname, src),
             "peak_source": "FP32 FMA units: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock, %s peaks file)"
@@ -564,7 +575,8 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded %s, one per rank)" % w["gen_name"],
         "config": {"workload": w["name"], "n": w["n"], "theta": w["theta"], "order": w["order"],
                    "leaf_size": w["leaf_size"], "form": "FP32 (FP64 centres, decisions, reductions)",
-                   "walk": "per-node shared pairs" if args.walk == 1 else "per-leaf replay (Algorithm 1)",
+                   "walk": {0: "per-leaf replay (Algorithm 1)", 1: "per-node shared pairs",
+                            2: "one-sided symmetric pairs"}[args.walk],
                    "l2": "flushed between timed steps (512 MB write outside the events)"},
         "interactions_per_s": ws * inter / (step_ms * 1e-3),
         "counts": {"m2l_replicated": st32["m2l"], "m2l_unique": st32["m2l_unique"],
@@ -577,6 +589,7 @@ def run_gpu(args):
                               "fp64": float(np.linalg.norm(st64["momentum"]) / st64["abs_momentum"])},
         "theta_sweep_fp32": sweep,
         "other_walk_fp32": other_walk,
+        "symmetric_walk_fp32": sym_walk,
         "ensemble_256": ensemble,
         "stage_rooflines": stage_rooflines(st32, w["n"], fp32_peak, hbm_peak),
         "configs": configs,
@@ -617,7 +630,7 @@ def main():
                     help="headline workload (default: the 10^6 Plummer sphere; the others are for profiling)")
     ap.add_argument("--n", type=int, default=None, help="particle count (default: the workload's 10^6)")
     ap.add_argument("--leaf", type=int, default=None, help="leaf size (default: the workload's 16)")
-    ap.add_argument("--walk", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--walk", type=int, default=1, choices=[0, 1, 2],
                     help="headline walk: 1 per-node shared pairs (default), 0 per-leaf replay (Algorithm 1)")
     ap.add_argument("--only", default="all", choices=["all", "fp32"],
                     help="fp32: time the headline FP32 step only (for profiler launch lists)")

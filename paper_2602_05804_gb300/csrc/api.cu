@@ -169,7 +169,8 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->cf_arena, &c->cf_off, &c->cf_cnt, &c->Tnode, &c->leaf_order, &c->sys_off,
                     &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_leaf_off, &c->sys_sums,
                     &c->p2p_extra, &c->p2p_split, &c->p2p_slist, &c->p2p_part, &c->lf_acc, &c->lf_part,
-                    &c->kd_ord, &c->kd_node, &c->kd_act, &c->kd_work, &c->kd_chunk, &c->kd_part, &c->kd_split};
+                    &c->kd_ord, &c->kd_node, &c->kd_act, &c->kd_work, &c->kd_chunk, &c->kd_part, &c->kd_split,
+                    &c->sym_own, &c->sym_recv};
   for (DevBuf* b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -213,7 +214,8 @@ int sfmm_set_option(sfmm_ctx* c, const char* key, double v) {
     if (v < 0) return set_error(c, SFMM_EINVAL, "list_capacity must be >= 0");
     c->list_capacity = (int64_t)v;
   } else if (!strcmp(key, "walk")) {
-    if (v != 0.0 && v != 1.0) return set_error(c, SFMM_EINVAL, "walk: 0 (per-leaf replay) or 1 (per-node shared pairs)");
+    if (v != 0.0 && v != 1.0 && v != 2.0)
+      return set_error(c, SFMM_EINVAL, "walk: 0 (per-leaf replay), 1 (per-node shared pairs), 2 (one-sided symmetric pairs)");
     c->walk_mode = (int)v;
   } else if (!strcmp(key, "tree")) {
     if (v != 0.0 && v != 1.0) return set_error(c, SFMM_EINVAL, "tree: 0 (Morton radix tree) or 1 (centre-of-mass kd tree)");
@@ -343,7 +345,7 @@ int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot)
     if ((rc = compute_moments(c, order))) return set_error(c, rc, "moment pass failed");
   }
   if (c->profile) cudaEventRecord(c->ev[3], st);
-  if ((rc = (c->walk_mode == 1) ? run_walk_shared(c, theta, order) : run_walk(c, theta, order, false, 0, 0))) return rc;
+  if ((rc = (c->walk_mode >= 1) ? run_walk_shared(c, theta, order) : run_walk(c, theta, order, false, 0, 0))) return rc;
   if (c->profile) cudaEventRecord(c->ev[4], st);
   if ((rc = run_p2p(c, acc, pot))) return set_error(c, rc, "near-field pass failed");
   if (c->profile) cudaEventRecord(c->ev[5], st);

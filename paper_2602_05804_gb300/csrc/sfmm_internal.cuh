@@ -45,7 +45,8 @@ struct sfmm_ctx {
   DevBuf sys_off, sys_lsz, psys, sys_root, wparent, sys_leaf_off, sys_sums;
   int32_t nnodes = 0, nleaves = 0;
   int moments_order = -1;  // order of the cached moments (-1: none)
-  int walk_mode = 1;        // 1: per-node shared pairs (default), 0: per-leaf replay (Algorithm 1)
+  int walk_mode = 1;        // 1: per-node shared pairs (default), 0: per-leaf replay (Algorithm 1),
+                            // 2: per-node pairs, each evaluated once for both sides
   int max_depth = 0;
   std::vector<int> h_level_off;  // host copy: internal nodes per depth, max_depth + 2 entries
 
@@ -80,6 +81,7 @@ struct sfmm_ctx {
   // gravity
   DevBuf ring, far, arena, p2p_off, p2p_cnt, counters, red_part, dump;
   DevBuf cf_arena, cf_off, cf_cnt, Tnode;  // shared walk: child frontiers, node coefficients
+  DevBuf sym_own, sym_recv;               // walk mode 2: own and received sums per node (FP64)
   // near field: chunks of long neighbour lists (extra work items, per-leaf
   // slot base, split leaves, partial sums) and the list entries in use
   DevBuf p2p_extra, p2p_split, p2p_slist, p2p_part;

@@ -173,6 +173,64 @@ __device__ __forceinline__ void m2l_eval(int s, const float4& hiA, const float4&
   }
 }
 
+// Sign (-1)^|gamma| of entry t of a derivative vector (entries are ordered by
+// degree: ncoef(k) of them have degree <= k).
+__host__ __device__ constexpr int deriv_degree(int t) {
+  int k = 0;
+  while (ncoef(k) <= t) ++k;
+  return k;
+}
+
+// One-sided symmetric interaction (Sect. 5, after Dehnen 2002): D_gamma(r) is
+// evaluated once for the pair; the target's coefficients from the source's
+// moments are added to C as in m2l_eval, and the source's coefficients from
+// the target's moments QA, with D_gamma(-r) = (-1)^|gamma| D_gamma(r), are
+// added to the source's received sums EB (FP64 atomics).
+template <int P, bool F32>
+__device__ __forceinline__ void m2l_eval_sym(int s, double cAx, double cAy, double cAz, const WalkArgs& a,
+                                             typename std::conditional<F32, float, double>::type* C,
+                                             const float4& r,
+                                             const typename std::conditional<F32, float, double>::type* QA,
+                                             double* EB) {
+  using E = Exp<P>;
+  using R = typename std::conditional<F32, float, double>::type;
+  if (s < 0) return;
+  R D[E::NMONO1];
+  R Q[F32 ? ((E::NQ + 3) / 4) * 4 : E::NQ];
+  if constexpr (F32) {
+    const float ri = rsqrtf(fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z)));
+    E::derivs(r.x * ri, r.y * ri, r.z * ri, ri, D);
+    const float4* q4 = reinterpret_cast<const float4*>(a.Qf + (size_t)s * a.nqs);
+#pragma unroll
+    for (int t = 0; t < (E::NQ + 3) / 4; ++t) {
+      const float4 v = __ldg(q4 + t);
+      Q[4 * t] = v.x;
+      Q[4 * t + 1] = v.y;
+      Q[4 * t + 2] = v.z;
+      Q[4 * t + 3] = v.w;
+    }
+    E::m2l_nodip(D, Q, C);
+  } else {
+    const double rx = a.ncx[s] - cAx, ry = a.ncy[s] - cAy, rz = a.ncz[s] - cAz;
+    const double ri = rsqrt(fma(rx, rx, fma(ry, ry, rz * rz)));
+    E::derivs(rx * ri, ry * ri, rz * ri, ri, D);
+    const double* q = a.Qd + (size_t)s * E::NQ;
+#pragma unroll
+    for (int t = 0; t < E::NQ; ++t) Q[t] = __ldg(q + t);
+    E::m2l(D, Q, C);
+  }
+#pragma unroll
+  for (int t = 0; t < E::NMONO1; ++t)
+    if (deriv_degree(t) & 1) D[t] = -D[t];
+  R Cp[E::NC];
+#pragma unroll
+  for (int t = 0; t < E::NC; ++t) Cp[t] = R(0);
+  if constexpr (F32) E::m2l_nodip(D, QA, Cp);
+  else E::m2l(D, QA, Cp);
+#pragma unroll
+  for (int t = 0; t < E::NC; ++t) atomicAdd(EB + t, (double)Cp[t]);
+}
+
 // The same with r computed here from the node records (FP32 form).
 template <int P, bool F32>
 __device__ __forceinline__ void m2l_eval(int s, const float4& hiA, const float4& loA, double cAx, double cAy,

@@ -35,9 +35,151 @@ struct LevelArgs {
   float* T32;                  // node coefficients: hi/lo pairs (FP32 form)
   double* T64;                 // node coefficients (FP64 form)
   int tstride;                 // coefficients per node (padded)
+  // mode 2 (one-sided symmetric pairs): node depths, each node's own sums and
+  // the sums its partners sent it (FP64, tstride per node)
+  const int* ndepth;
+  double* Cown;
+  double* Erecv;
 };
 
+
+// T(A) = shift(T(parent)) + own: the parent's coefficients translated to A's
+// centre (Eq. gravmtranslat, lane-parallel through the shift table) plus A's
+// own sums (own_lo: low parts of a double-float own sum, or zeros).  Stored
+// for an internal node; returned in Tn (+ Tl) for a leaf.
+template <int P, bool F32, bool LO>
+__device__ __forceinline__ void node_coefficients(const LevelArgs& la, int A, int par, bool leafA, const float4& hiA,
+                                                  const float4& loA, double cAx, double cAy, double cAz,
+                                                  const typename std::conditional<F32, float, double>::type* lev,
+                                                  const float* lev_lo,
+                                                  typename std::conditional<F32, float, double>::type* Tn,
+                                                  float* Tl, typename std::conditional<F32, float, double>::type* sT,
+                                                  typename std::conditional<F32, float, double>::type* sH,
+                                                  const signed char* s_tab, int lane) {
+  using E = Exp<P>;
+  using R = typename std::conditional<F32, float, double>::type;
+  constexpr int NC = E::NC;
+  constexpr int NCS = (NC + 31) / 32;
+  const WalkArgs& a = la.w;
+#pragma unroll
+  for (int b = 0; b < NCS; ++b) {
+    Tn[b] = R(0);
+    Tl[b] = 0.0f;
+  }
+  if (par >= 0) {
+    const float4 hiP = a.geo_hi[par], loP = a.geo_lo[par];
+#pragma unroll
+    for (int b = 0; b < NCS; ++b) {
+      const int j = lane + 32 * b;
+      if constexpr (F32) {
+        Tn[b] = la.T32[2 * ((size_t)par * la.tstride + j)];
+        Tl[b] = la.T32[2 * ((size_t)par * la.tstride + j) + 1];
+      } else {
+        Tn[b] = la.T64[(size_t)par * la.tstride + j];
+      }
+      sT[j] = Tn[b];
+    }
+    if (lane == 0) {
+      R hx, hy, hz;
+      if constexpr (F32) {
+        hx = df_diff(hiA.x, loA.x, hiP.x, loP.x);
+        hy = df_diff(hiA.y, loA.y, hiP.y, loP.y);
+        hz = df_diff(hiA.z, loA.z, hiP.z, loP.z);
+      } else {
+        hx = cAx - a.ncx[par];
+        hy = cAy - a.ncy[par];
+        hz = cAz - a.ncz[par];
+      }
+      R hm[E::NMONO1];
+      E::mono1(hx, hy, hz, hm);
+#pragma unroll
+      for (int t = 0; t < E::NMONO1; ++t) sH[t] = hm[t];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < NCS; ++b) {
+      const int j = lane + 32 * b;
+      if (j < NC) {
+        R corr = R(0);
+        const signed char* row = s_tab + j * NC;
+        for (int i = 0; i < NC; ++i) {
+          const int t = row[i];
+          if (t > 0) corr = fma(sH[t], sT[i], corr);
+        }
+        if constexpr (F32) {
+          dfloat r = df_add_f(dfloat{Tn[b], Tl[b]}, corr);
+          Tn[b] = r.hi;
+          Tl[b] = r.lo;
+        } else {
+          Tn[b] += corr;
+        }
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int b = 0; b < NCS; ++b) {
+    const int j = lane + 32 * b;
+    if constexpr (F32) {
+      dfloat r = df_add_f(dfloat{Tn[b], Tl[b]}, lev[b]);
+      if constexpr (LO) r = df_add_f(r, lev_lo[b]);
+      Tn[b] = r.hi;
+      Tl[b] = r.lo;
+      if (!leafA) {
+        la.T32[2 * ((size_t)A * la.tstride + j)] = Tn[b];
+        la.T32[2 * ((size_t)A * la.tstride + j) + 1] = Tl[b];
+      }
+    } else {
+      Tn[b] += lev[b];
+      if (!leafA) la.T64[(size_t)A * la.tstride + j] = Tn[b];
+    }
+  }
+}
+
+// Evaluation of a leaf's coefficients at its particles (L2P, Eq. 16 / 28).
 template <int P, bool F32>
+__device__ __forceinline__ void leaf_l2p(const LevelArgs& la, int A, double cAx, double cAy, double cAz,
+                                         const typename std::conditional<F32, float, double>::type* Tn,
+                                         const float* Tl, typename std::conditional<F32, float, double>::type* sT,
+                                         int lane) {
+  using E = Exp<P>;
+  using R = typename std::conditional<F32, float, double>::type;
+  constexpr int NCS = (E::NC + 31) / 32;
+  const WalkArgs& a = la.w;
+  const int fL = a.nfirst[A], nL = a.ncount[A];
+#pragma unroll
+  for (int b = 0; b < NCS; ++b) {
+    if constexpr (F32) sT[lane + 32 * b] = Tn[b] + Tl[b];
+    else sT[lane + 32 * b] = Tn[b];
+  }
+  __syncwarp();
+  for (int t = lane; t < nL; t += 32) {
+    const int i = fL + t;
+    R ax, ay, az;
+    if constexpr (F32) {
+      const float4 p = a.prel[i];
+      ax = p.x;
+      ay = p.y;
+      az = p.z;
+    } else {
+      ax = a.px[i] - cAx;
+      ay = a.py[i] - cAy;
+      az = a.pz[i] - cAz;
+    }
+    R am[E::NQ], o4[4];
+    E::mono(ax, ay, az, am);
+    E::l2p(am, &sT[0], o4);
+    if constexpr (F32) a.far32[i] = make_float4(o4[1], o4[2], o4[3], -o4[0]);
+    else {
+      a.far64[4 * (size_t)i] = o4[1];
+      a.far64[4 * (size_t)i + 1] = o4[2];
+      a.far64[4 * (size_t)i + 2] = o4[3];
+      a.far64[4 * (size_t)i + 3] = -o4[0];
+    }
+  }
+}
+
+template <int P, bool F32, bool SYM>
 __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level(const LevelArgs la) {
   using E = Exp<P>;
   using R = typename std::conditional<F32, float, double>::type;
@@ -64,6 +206,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
   int* const out = stk + cap;                      // child frontier / neighbour list
 
   unsigned long long st_m2l = 0, st_uniq = 0, st_pl = 0, st_pp = 0;
+  unsigned long long st_m2l_p = 0;  // mode 2: replicated count of the partner sides, per lane
   int st_fb = 0;
 
   while (true) {
@@ -113,6 +256,25 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
 #pragma unroll
     for (int t = 0; t < NCS * 32; ++t) C[t] = R(0);
     int nq = 0, nacc_tot = 0;
+    int rankA = 0;
+    R QA[SYM ? (F32 ? ((E::NQ + 3) / 4) * 4 : E::NQ) : 1];
+    if constexpr (SYM) {
+      rankA = leafA ? INT_MAX : la.ndepth[A];
+      if constexpr (F32) {
+        const float4* q4 = reinterpret_cast<const float4*>(a.Qf + (size_t)A * a.nqs);
+#pragma unroll
+        for (int t = 0; t < (E::NQ + 3) / 4; ++t) {
+          const float4 v = __ldg(q4 + t);
+          QA[4 * t] = v.x;
+          QA[4 * t + 1] = v.y;
+          QA[4 * t + 2] = v.z;
+          QA[4 * t + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < E::NQ; ++t) QA[t] = __ldg(a.Qd + (size_t)A * E::NQ + t);
+      }
+    }
     // the inherited list is read through a two-stage pipeline: ids one chunk
     // ahead of the node records, records one chunk ahead of their use, so the
     // loads of a chunk overlap the work on the previous one
@@ -160,6 +322,14 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
           else {
             acc = decide(hiA, loA, hiB, loB, A, s, a, st_fb, rx, ry, rz);
             open = !acc;
+          }
+        }
+        if constexpr (SYM) {
+          // the node processed first evaluates the pair for both sides
+          // (leaves run last; ties within a launch go to the smaller id)
+          if (acc) {
+            const int rankB = rB < 0 ? INT_MAX : la.ndepth[s];
+            acc = rankA < rankB || (rankA == rankB && A < s);
           }
         }
         const unsigned bacc = __ballot_sync(SFMM_FULL, acc);
@@ -212,7 +382,14 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
           if (lane < take) rq = s_qr[warp][nq - take + lane];
         }
         __syncwarp();
-        m2l_eval<P, F32>(src, hiA, loA, cAx, cAy, cAz, a, C, rq);
+        if constexpr (SYM) {
+          if (src >= 0) {
+            m2l_eval_sym<P, F32>(src, cAx, cAy, cAz, a, C, rq, QA, la.Erecv + (size_t)src * la.tstride);
+            st_m2l_p += (unsigned long long)la.nlu[src];
+          }
+        } else {
+          m2l_eval<P, F32>(src, hiA, loA, cAx, cAy, cAz, a, C, rq);
+        }
         nq -= take;
       }
       if (!more) break;
@@ -227,7 +404,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
       continue;
     }
     if (lane == 0) {
-      st_uniq += nacc_tot;
+      st_uniq += (SYM ? 2ull : 1ull) * nacc_tot;
       st_m2l += (unsigned long long)nacc_tot * la.nlu[A];
     }
 
@@ -242,77 +419,14 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
     }
     R Tn[NCS];
     float Tl[NCS];
+    if constexpr (SYM) {
+      // own sums to the node's slot; the finalize pass adds the parent's
+      // translated coefficients and the sums received from partners
 #pragma unroll
-    for (int b = 0; b < NCS; ++b) {
-      Tn[b] = R(0);
-      Tl[b] = 0.0f;
-    }
-    if (par >= 0) {
-      const float4 hiP = a.geo_hi[par], loP = a.geo_lo[par];
-#pragma unroll
-      for (int b = 0; b < NCS; ++b) {
-        const int j = lane + 32 * b;
-        if constexpr (F32) {
-          Tn[b] = la.T32[2 * ((size_t)par * la.tstride + j)];
-          Tl[b] = la.T32[2 * ((size_t)par * la.tstride + j) + 1];
-        } else {
-          Tn[b] = la.T64[(size_t)par * la.tstride + j];
-        }
-        s_T[warp][j] = Tn[b];
-      }
-      if (lane == 0) {
-        R hx, hy, hz;
-        if constexpr (F32) {
-          hx = df_diff(hiA.x, loA.x, hiP.x, loP.x);
-          hy = df_diff(hiA.y, loA.y, hiP.y, loP.y);
-          hz = df_diff(hiA.z, loA.z, hiP.z, loP.z);
-        } else {
-          hx = cAx - a.ncx[par];
-          hy = cAy - a.ncy[par];
-          hz = cAz - a.ncz[par];
-        }
-        R hm[E::NMONO1];
-        E::mono1(hx, hy, hz, hm);
-#pragma unroll
-        for (int t = 0; t < E::NMONO1; ++t) s_h[warp][t] = hm[t];
-      }
-      __syncwarp();
-#pragma unroll
-      for (int b = 0; b < NCS; ++b) {
-        const int j = lane + 32 * b;
-        if (j < NC) {
-          R corr = R(0);
-          const signed char* row = s_tab + j * NC;
-          for (int i = 0; i < NC; ++i) {
-            const int t = row[i];
-            if (t > 0) corr = fma(s_h[warp][t], s_T[warp][i], corr);
-          }
-          if constexpr (F32) {
-            dfloat r = df_add_f(dfloat{Tn[b], Tl[b]}, corr);
-            Tn[b] = r.hi;
-            Tl[b] = r.lo;
-          } else {
-            Tn[b] += corr;
-          }
-        }
-      }
-      __syncwarp();
-    }
-#pragma unroll
-    for (int b = 0; b < NCS; ++b) {
-      const int j = lane + 32 * b;
-      if constexpr (F32) {
-        dfloat r = df_add_f(dfloat{Tn[b], Tl[b]}, lev[b]);
-        Tn[b] = r.hi;
-        Tl[b] = r.lo;
-        if (!leafA) {
-          la.T32[2 * ((size_t)A * la.tstride + j)] = Tn[b];
-          la.T32[2 * ((size_t)A * la.tstride + j) + 1] = Tl[b];
-        }
-      } else {
-        Tn[b] += lev[b];
-        if (!leafA) la.T64[(size_t)A * la.tstride + j] = Tn[b];
-      }
+      for (int b = 0; b < NCS; ++b) la.Cown[(size_t)A * la.tstride + lane + 32 * b] = (double)lev[b];
+    } else {
+      node_coefficients<P, F32, false>(la, A, par, leafA, hiA, loA, cAx, cAy, cAz, lev, nullptr, Tn, Tl, s_T[warp],
+                                       s_h[warp], s_tab, lane);
     }
 
     if (!leafA) {
@@ -325,39 +439,10 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
       continue;
     }
 
-    // leaf: L2P, then its neighbour list
+    // leaf: L2P (mode 2: in the finalize pass), then its neighbour list
     const int fL = a.nfirst[A], nL = a.ncount[A];
     const int leaf = (int)la.leaf_index[A];
-#pragma unroll
-    for (int b = 0; b < NCS; ++b) {
-      if constexpr (F32) s_T[warp][lane + 32 * b] = Tn[b] + Tl[b];
-      else s_T[warp][lane + 32 * b] = Tn[b];
-    }
-    __syncwarp();
-    for (int t = lane; t < nL; t += 32) {
-      const int i = fL + t;
-      R ax, ay, az;
-      if constexpr (F32) {
-        const float4 p = a.prel[i];
-        ax = p.x;
-        ay = p.y;
-        az = p.z;
-      } else {
-        ax = a.px[i] - cAx;
-        ay = a.py[i] - cAy;
-        az = a.pz[i] - cAz;
-      }
-      R am[E::NQ], o4[4];
-      E::mono(ax, ay, az, am);
-      E::l2p(am, &s_T[warp][0], o4);
-      if constexpr (F32) a.far32[i] = make_float4(o4[1], o4[2], o4[3], -o4[0]);
-      else {
-        a.far64[4 * (size_t)i] = o4[1];
-        a.far64[4 * (size_t)i + 1] = o4[2];
-        a.far64[4 * (size_t)i + 2] = o4[3];
-        a.far64[4 * (size_t)i + 3] = -o4[0];
-      }
-    }
+    if constexpr (!SYM) leaf_l2p<P, F32>(la, A, cAx, cAy, cAz, Tn, Tl, s_T[warp], lane);
     __syncwarp();
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(a.arena_counter, (unsigned long long)nn);
@@ -391,6 +476,11 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) st_fb += __shfl_xor_sync(SFMM_FULL, st_fb, o);
+  if constexpr (SYM) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) st_m2l_p += __shfl_xor_sync(SFMM_FULL, st_m2l_p, o);
+    st_m2l += st_m2l_p;
+  }
   if (lane == 0) {
     atomicAdd(&a.stat[0], st_m2l);
     atomicAdd(&a.stat[1], st_uniq);
@@ -400,13 +490,73 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
   }
 }
 
+// Mode 2, per level after its walk launch: every node's coefficients are
+// the parent's translated ones plus its own sums plus the sums its partners
+// sent it (all partners of a node are processed no later than its own
+// launch); internal nodes store them, leaves evaluate them (L2P).
 template <int P, bool F32>
+__global__ void __launch_bounds__(WALK_NT) k_walk_finalize(const LevelArgs la, int* __restrict__ counter) {
+  using E = Exp<P>;
+  using R = typename std::conditional<F32, float, double>::type;
+  constexpr int NC = E::NC;
+  constexpr int NCS = (NC + 31) / 32;
+  const WalkArgs& a = la.w;
+  __shared__ R s_T[WALK_WARPS][NCS * 32];
+  __shared__ R s_h[WALK_WARPS][E::NMONO1];
+  __shared__ signed char s_tab[NC * NC];
+  {
+    const signed char* tab = E::table();
+    for (int t = threadIdx.x; t < NC * NC; t += WALK_NT) s_tab[t] = tab[t];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  while (true) {
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(counter, 1);
+    idx = __shfl_sync(SFMM_FULL, idx, 0);
+    if (idx >= la.level_count) break;
+    const int A = la.level_nodes[la.level_begin + idx];
+    const bool leafA = a.nright[A] < 0;
+    const int par = la.nparent[A];
+    const float4 hiA = a.geo_hi[A], loA = a.geo_lo[A];
+    double cAx = 0.0, cAy = 0.0, cAz = 0.0;
+    if (!F32) {
+      cAx = a.ncx[A];
+      cAy = a.ncy[A];
+      cAz = a.ncz[A];
+    }
+    R lev[NCS];
+    float lev_lo[NCS];
+#pragma unroll
+    for (int b = 0; b < NCS; ++b) {
+      const size_t j = (size_t)A * la.tstride + lane + 32 * b;
+      const double v = la.Cown[j] + la.Erecv[j];
+      if constexpr (F32) {
+        float hi, lo;
+        split_double(v, hi, lo);
+        lev[b] = hi;
+        lev_lo[b] = lo;
+      } else {
+        lev[b] = v;
+        lev_lo[b] = 0.0f;
+      }
+    }
+    R Tn[NCS];
+    float Tl[NCS];
+    node_coefficients<P, F32, F32>(la, A, par, leafA, hiA, loA, cAx, cAy, cAz, lev, lev_lo, Tn, Tl, s_T[warp],
+                                   s_h[warp], s_tab, lane);
+    if (leafA) leaf_l2p<P, F32>(la, A, cAx, cAy, cAz, Tn, Tl, s_T[warp], lane);
+    __syncwarp();
+  }
+}
+
+template <int P, bool F32, bool SYM>
 static int run_levels(sfmm_ctx* c, double theta, int order) {
   using E = Exp<P>;
   constexpr int NCS = (E::NC + 31) / 32;
   const int nn = c->nnodes, nl = c->nleaves;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_level<P, F32>, WALK_NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_level<P, F32, SYM>, WALK_NT, 0);
   if (per_sm < 1) per_sm = 1;
   const int max_blocks = per_sm * num_sms(c->device);
   const int tstride = NCS * 32;
@@ -424,6 +574,12 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     if ((rc = c->cf_off.ensure(sizeof(long long) * (size_t)nn))) return rc;
     if ((rc = c->cf_cnt.ensure(sizeof(int) * (size_t)nn))) return rc;
     if ((rc = c->Tnode.ensure((F32 ? 2 * sizeof(float) : sizeof(double)) * (size_t)nn * tstride))) return rc;
+    if (SYM) {
+      if ((rc = c->sym_own.ensure(sizeof(double) * (size_t)nn * tstride)) ||
+          (rc = c->sym_recv.ensure(sizeof(double) * (size_t)nn * tstride)))
+        return rc;
+      SFMM_CUDA_TRY(cudaMemsetAsync(c->sym_recv.p, 0, sizeof(double) * (size_t)nn * tstride, c->stream));
+    }
     if ((rc = c->p2p_off.ensure(sizeof(long long) * (size_t)nl))) return rc;
     if ((rc = c->p2p_cnt.ensure(sizeof(int) * (size_t)nl))) return rc;
     const int nlev = c->max_depth + 1;  // levels holding internal nodes
@@ -482,6 +638,9 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     la.cf_off_out = c->cf_off.as<long long>();
     la.cf_cnt_out = c->cf_cnt.as<int>();
     la.cf_counter = ctr + 16;
+    la.ndepth = c->ndepth.as<int>();
+    la.Cown = SYM ? c->sym_own.as<double>() : nullptr;
+    la.Erecv = SYM ? c->sym_recv.as<double>() : nullptr;
     // internal nodes level by level (each needs its parent's opened list and
     // coefficients), then every leaf in one launch, shallowest first
     for (int k = 0; k <= nlev; ++k) {
@@ -499,8 +658,12 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
       if (la.level_count <= 0) continue;
       a.leaf_counter = reinterpret_cast<int*>(ctr + 18 + 2 * k);
       const int blocks = min(max_blocks, (la.level_count + WALK_WARPS - 1) / WALK_WARPS);
-      k_walk_level<P, F32><<<blocks, WALK_NT, 0, c->stream>>>(la);
+      k_walk_level<P, F32, SYM><<<blocks, WALK_NT, 0, c->stream>>>(la);
       ++c->nlaunch;
+      if (SYM) {
+        k_walk_finalize<P, F32><<<blocks, WALK_NT, 0, c->stream>>>(la, reinterpret_cast<int*>(ctr + 19 + 2 * k));
+        ++c->nlaunch;
+      }
       SFMM_CUDA_TRY(cudaGetLastError());
     }
     int bits = 0;
@@ -540,12 +703,18 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
 
 int run_walk_shared(sfmm_ctx* c, double theta, int order) {
   const bool f32 = c->precision == SFMM_FP32;
+  const bool sym = c->walk_mode == 2;  // one-sided symmetric pairs
   switch (order) {
-    case 0: return f32 ? run_levels<0, true>(c, theta, order) : run_levels<0, false>(c, theta, order);
-    case 1: return f32 ? run_levels<1, true>(c, theta, order) : run_levels<1, false>(c, theta, order);
-    case 2: return f32 ? run_levels<2, true>(c, theta, order) : run_levels<2, false>(c, theta, order);
-    case 3: return f32 ? run_levels<3, true>(c, theta, order) : run_levels<3, false>(c, theta, order);
-    case 4: return f32 ? run_levels<4, true>(c, theta, order) : run_levels<4, false>(c, theta, order);
+    case 0: return f32 ? (sym ? run_levels<0, true, true>(c, theta, order) : run_levels<0, true, false>(c, theta, order))
+                : (sym ? run_levels<0, false, true>(c, theta, order) : run_levels<0, false, false>(c, theta, order));
+    case 1: return f32 ? (sym ? run_levels<1, true, true>(c, theta, order) : run_levels<1, true, false>(c, theta, order))
+                : (sym ? run_levels<1, false, true>(c, theta, order) : run_levels<1, false, false>(c, theta, order));
+    case 2: return f32 ? (sym ? run_levels<2, true, true>(c, theta, order) : run_levels<2, true, false>(c, theta, order))
+                : (sym ? run_levels<2, false, true>(c, theta, order) : run_levels<2, false, false>(c, theta, order));
+    case 3: return f32 ? (sym ? run_levels<3, true, true>(c, theta, order) : run_levels<3, true, false>(c, theta, order))
+                : (sym ? run_levels<3, false, true>(c, theta, order) : run_levels<3, false, false>(c, theta, order));
+    case 4: return f32 ? (sym ? run_levels<4, true, true>(c, theta, order) : run_levels<4, true, false>(c, theta, order))
+                : (sym ? run_levels<4, false, true>(c, theta, order) : run_levels<4, false, false>(c, theta, order));
     default: return SFMM_EINVAL;
   }
 }

@@ -121,7 +121,7 @@ PARITY = [("uniform", 6000, 10, 0.5, 2), ("plummer", 8001, 16, 0.5, 2), ("plumme
           ("plummer", 2500, 1, 0.5, 2), ("uniform", 1000, 64, 0.9, 2)]
 
 
-@pytest.mark.parametrize("walk", [0, 1])
+@pytest.mark.parametrize("walk", [0, 1, 2])
 @pytest.mark.parametrize("kind,n,ls,theta,p", PARITY)
 def test_fp64_form_matches_oracle(kind, n, ls, theta, p, walk):
     pos, m, h = _set(kind, n, 17)
@@ -141,7 +141,7 @@ def test_fp64_form_matches_oracle(kind, n, ls, theta, p, walk):
     assert abs(st["W"] - 0.5 * (m * pot_o).sum()) <= 1e-10 * abs(st["W"])
 
 
-@pytest.mark.parametrize("walk", [0, 1])
+@pytest.mark.parametrize("walk", [0, 1, 2])
 @pytest.mark.parametrize("kind,n,ls,theta,p", PARITY)
 def test_fp32_form_matches_oracle(kind, n, ls, theta, p, walk):
     pos, m, h = _set(kind, n, 17)
@@ -325,3 +325,24 @@ def test_long_lists_split_into_chunks(prec, walk):
     acc2, pot2 = s.gravity(0.1, 2)
     np.testing.assert_array_equal(acc, acc2.cpu().numpy())
     np.testing.assert_array_equal(pot, pot2.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", TOL_FP32_RMS)])
+def test_one_sided_symmetric_pairs_equal_shared_walk(prec, tol):
+    """Walk mode 2 evaluates D once per pair for both sides (Sect. 5): same
+    interaction counts as the shared walk, same results up to summation
+    order, momentum to round-off in the FP64 form."""
+    pos, m, h = workloads.plummer(30000, 45)
+    out = []
+    for walk in (1, 2):
+        s = solver(prec, walk=walk)
+        s.build(pos, m, h, 16)
+        acc, pot = s.gravity(0.5, 2)
+        out.append((acc.cpu().numpy(), pot.cpu().numpy(), s.stats()))
+    (a1, p1, s1), (a2, p2, s2) = out
+    for k in ("m2l", "m2l_unique", "p2p_pairs", "p2p_leaves"):
+        assert s1[k] == s2[k], k
+    assert acc_rel(a2, a1).max() <= tol
+    assert pot_rel(p2, p1).max() <= tol
+    if prec == "fp64":
+        assert momentum_residual(m, a2) <= TOL_MOM_FP64
