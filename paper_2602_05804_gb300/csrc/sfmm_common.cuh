@@ -19,6 +19,7 @@
 #define SFMM_ST_CHILDLIST   0x40  // child-frontier arena overflow (capacity)
 
 #define SFMM_MAXDEPTH 128
+#define SFMM_WALK_ATTEMPTS 6  // walk runs: the first plus regrow-and-retry of short buffers
 
 // Neighbour lists longer than this many entries are split into chunks of it,
 // each a separate near-field work item (long lists would otherwise leave one

@@ -401,7 +401,7 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
   const int nblocks = B(c);
   const int nwarps = nblocks * WALK_WARPS;
 
-  for (int attempt = 0; attempt < 4; ++attempt) {
+  for (int attempt = 0; attempt < SFMM_WALK_ATTEMPTS; ++attempt) {
     if ((rc = c->ring.ensure(sizeof(int) * (size_t)nwarps * 2 * c->ring_capacity))) return rc;
     long long arena_cap = c->list_capacity > 0 ? c->list_capacity : (long long)nl * 96 + 1024;
     if ((rc = c->arena.ensure(sizeof(int) * (size_t)arena_cap))) return rc;
@@ -463,7 +463,8 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
     if ((rc = sync_status(c, &bits))) return rc;
     if (bits & SFMM_ST_DEPTH) return set_error(c, SFMM_ESTACK, "a leaf's branch is deeper than the walk supports");
     if (bits & (SFMM_ST_RING | SFMM_ST_ARENA)) {
-      if (attempt == 3) return set_error(c, SFMM_ECAPACITY, "walk buffers too small after three regrows");
+      if (attempt == SFMM_WALK_ATTEMPTS - 1)
+        return set_error(c, SFMM_ECAPACITY, "walk buffers too small after the last regrow");
       // the arena counter counts every list that reached it, so it is a lower
       // bound when frontier rings also overflowed
       unsigned long long need = 0;

@@ -561,7 +561,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
   const int max_blocks = per_sm * num_sms(c->device);
   const int tstride = NCS * 32;
   int rc;
-  for (int attempt = 0; attempt < 4; ++attempt) {
+  for (int attempt = 0; attempt < SFMM_WALK_ATTEMPTS; ++attempt) {
     const int nwarps = max_blocks * WALK_WARPS;
     if ((rc = c->ring.ensure(sizeof(int) * (size_t)nwarps * 2 * c->ring_capacity))) return rc;
     long long arena_cap = c->list_capacity > 0 ? c->list_capacity : (long long)nl * 96 + 1024;
@@ -670,7 +670,8 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     if ((rc = sync_status(c, &bits))) return rc;
     if (bits & SFMM_ST_DEPTH) return set_error(c, SFMM_ESTACK, "tree deeper than supported");
     if (bits & (SFMM_ST_RING | SFMM_ST_ARENA | SFMM_ST_CHILDLIST)) {
-      if (attempt == 3) return set_error(c, SFMM_ECAPACITY, "walk buffers too small after three regrows");
+      if (attempt == SFMM_WALK_ATTEMPTS - 1)
+        return set_error(c, SFMM_ECAPACITY, "walk buffers too small after the last regrow");
       if (bits & SFMM_ST_RING) c->ring_capacity = c->ring_capacity < (1 << 20) ? c->ring_capacity * 16 : (1 << 24);
       if (bits & SFMM_ST_ARENA) {
         unsigned long long need = 0;
@@ -679,9 +680,11 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
         c->list_capacity = want > grown ? want : grown;
       }
       if (bits & SFMM_ST_CHILDLIST) {
+        // the count undercounts: a node that could not reserve skipped its
+        // children's lists, so their descendants reserved less
         unsigned long long need = 0;
         SFMM_CUDA_TRY(cudaMemcpy(&need, ctr + 16, sizeof(need), cudaMemcpyDeviceToHost));
-        const int64_t grown = 2 * (int64_t)cf_cap, want = (int64_t)(need + need / 4 + 4096);
+        const int64_t grown = 4 * (int64_t)cf_cap, want = 2 * (int64_t)need + 4096;
         c->cf_capacity = want > grown ? want : grown;
       }
       continue;

@@ -346,3 +346,18 @@ def test_one_sided_symmetric_pairs_equal_shared_walk(prec, tol):
     assert pot_rel(p2, p1).max() <= tol
     if prec == "fp64":
         assert momentum_residual(m, a2) <= TOL_MOM_FP64
+
+
+@pytest.mark.parametrize("walk", [0, 1, 2])
+def test_small_theta_grows_buffers_and_matches_oracle(walk):
+    """theta = 0.1: almost every pair is done pairwise, lists are long and
+    several work buffers must grow (regrow and retry inside the call)."""
+    pos, m, h = workloads.plummer(20000, 46)
+    acc_o, pot_o, st_o = oracle.sfmm(pos, m, h, theta=0.1, p=2, leaf_size=16)
+    s = solver("fp32", walk=walk)
+    s.build(pos, m, h, 16)
+    acc, pot = s.gravity(0.1, 2)
+    st = s.stats()
+    assert st["p2p_pairs"] == st_o["p2p_pairs"] and st["m2l"] == st_o["m2l"]
+    e = acc_rel(acc.cpu().numpy(), acc_o)
+    assert math.sqrt((e**2).mean()) <= TOL_FP32_RMS
