@@ -274,7 +274,7 @@ __global__ void k_morton(const double* __restrict__ pos, int n, const double* __
 // S2: stable LSD radix sort of (key, index), 8-bit digits
 // ---------------------------------------------------------------------------
 #define RS_NT 256
-#define RS_ITEMS 16
+#define RS_ITEMS 4
 #define RS_TILE (RS_NT * RS_ITEMS)
 #define RS_WARPS (RS_NT / 32)
 
@@ -601,12 +601,15 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
                             const double* __restrict__ pm, const double* __restrict__ ph,
                             double* __restrict__ ncx, double* __restrict__ ncy, double* __restrict__ ncz,
                             double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ pnode,
-                            int* __restrict__ nlu) {
+                            int* __restrict__ nlu, double* __restrict__ extv, int* __restrict__ exti) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nleaves) return;
   const int v = leaf_node[q];
   const int f = nfirst[v], cnt = ncount[v];
   double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, hm = 0.0;
+  // extreme particles per axis (min x, y, z, max x, y, z; first one on ties)
+  double ev[6] = {px[f], py[f], pz[f], px[f], py[f], pz[f]};
+  int ei[6] = {f, f, f, f, f, f};
   for (int i = f; i < f + cnt; ++i) {
     const double m = pm[i];
     M = dadd(M, m);
@@ -615,6 +618,17 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
     sz = dadd(sz, dmul(m, pz[i]));
     hm = fmax(hm, ph[i]);
     pnode[i] = v;
+    const double xc[3] = {px[i], py[i], pz[i]};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (xc[c] < ev[c]) { ev[c] = xc[c]; ei[c] = i; }
+      if (xc[c] > ev[3 + c]) { ev[3 + c] = xc[c]; ei[3 + c] = i; }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    extv[6 * (size_t)v + c] = ev[c];
+    exti[6 * (size_t)v + c] = ei[c];
   }
   nmass[v] = M;
   ncx[v] = __ddiv_rn(sx, M);
@@ -627,7 +641,7 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
 // Bottom-up: the second child to finish computes its parent.
 __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nparent,
                          const int* __restrict__ nright, double* ncx, double* ncy, double* ncz, double* nmass,
-                         double* nhmax, int* nlu, int* flags) {
+                         double* nhmax, int* nlu, int* flags, double* extv, int* exti) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nleaves) return;
   int v = nparent[leaf_node[q]];
@@ -644,40 +658,125 @@ __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const i
     nmass[v] = M;
     nhmax[v] = fmax(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
     nlu[v] = __ldcg(&nlu[L]) + __ldcg(&nlu[R]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const double a = __ldcg(&extv[6 * (size_t)L + c]), b = __ldcg(&extv[6 * (size_t)R + c]);
+      const bool right = (c < 3) ? (b < a) : (b > a);
+      extv[6 * (size_t)v + c] = right ? b : a;
+      exti[6 * (size_t)v + c] = __ldcg(&exti[6 * (size_t)(right ? R : L) + c]);
+    }
     v = nparent[v];
   }
 }
 
-// Exact node sizes: every particle visits its ancestors; lanes at the same
-// node combine their squared distances, one atomic max per group.
+// Exact node sizes l_v = max over the node's particles of |x_i - s_v| (the
+// squared distance rounded as written, then one square root).  Most
+// (particle, ancestor) pairs cannot hold the maximum, so only candidates are
+// evaluated:
+//  * LB(v): the largest distance from s_v among the node's six axis-extreme
+//    particles -- real particles, so LB(v) <= l_v;
+//  * a leaf L (exact size l_L) can hold the maximum of an ancestor v only if
+//    l_L + |s_L - s_v| >= LB(v); the test uses margins of 1e-12, far above
+//    the rounding of these few operations, so a skipped particle's distance
+//    is strictly below LB(v);
+//  * every particle then visits its ancestors and evaluates only those its
+//    leaf is a candidate for.
+__device__ __forceinline__ double exact_d2(double x, double y, double z, double cx, double cy, double cz) {
+  const double dx = dsub(x, cx), dy = dsub(y, cy), dz = dsub(z, cz);
+  return dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+}
+
+__global__ void k_node_lb(int nn, const int* __restrict__ wparent, const int* __restrict__ exti,
+                          const double* __restrict__ px, const double* __restrict__ py,
+                          const double* __restrict__ pz, const double* __restrict__ ncx,
+                          const double* __restrict__ ncy, const double* __restrict__ ncz, double* __restrict__ lb) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nn) return;
+  double m = 0.0;
+  if (wparent[v] != -2) {
+    const double cx = ncx[v], cy = ncy[v], cz = ncz[v];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const int e = exti[6 * (size_t)v + c];
+      m = fmax(m, exact_d2(px[e], py[e], pz[e], cx, cy, cz));
+    }
+  }
+  lb[v] = __dsqrt_rn(m);
+}
+
+// Thread per leaf: the leaf's exact size, and which ancestors it is a
+// candidate for (bit k: the ancestor k levels up; beyond 127 levels every
+// ancestor counts as a candidate).
+__global__ void k_size_leaf(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
+                            const int* __restrict__ ncount, const int* __restrict__ wparent,
+                            const double* __restrict__ px, const double* __restrict__ py,
+                            const double* __restrict__ pz, const double* __restrict__ ncx,
+                            const double* __restrict__ ncy, const double* __restrict__ ncz,
+                            const double* __restrict__ lb, unsigned long long* __restrict__ l2bits,
+                            unsigned long long* __restrict__ cand) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nleaves) return;
+  const int L = leaf_node[q];
+  const int f = nfirst[L], cnt = ncount[L];
+  const double cx = ncx[L], cy = ncy[L], cz = ncz[L];
+  double l2 = 0.0;
+  for (int i = f; i < f + cnt; ++i) l2 = fmax(l2, exact_d2(px[i], py[i], pz[i], cx, cy, cz));
+  l2bits[L] = (unsigned long long)__double_as_longlong(l2);
+  const double lL = __dsqrt_rn(l2) * (1.0 + 1e-12);
+  unsigned long long m0 = 0ull, m1 = 0ull;
+  int k = 1;
+  for (int v = (wparent[L] >= 0) ? wparent[L] : -1; v >= 0; v = wparent[v], ++k) {
+    const double bound = lb[v] * (1.0 - 1e-12) - lL;
+    const bool skip = bound > 0.0 && exact_d2(cx, cy, cz, ncx[v], ncy[v], ncz[v]) * (1.0 + 1e-12) < bound * bound;
+    if (!skip) {
+      if (k < 64) m0 |= 1ull << k;
+      else if (k < 128) m1 |= 1ull << (k - 64);
+    }
+  }
+  cand[2 * (size_t)q] = m0;
+  cand[2 * (size_t)q + 1] = m1;
+}
+
+// Thread per particle: candidate ancestors only; lanes at the same node
+// combine their squared distances, one atomic max per group.
 __global__ void k_size(int n, const double* __restrict__ px, const double* __restrict__ py,
                        const double* __restrict__ pz, const int* __restrict__ pnode,
+                       const uint32_t* __restrict__ leaf_index, const unsigned long long* __restrict__ cand,
                        const int* __restrict__ wparent, const double* __restrict__ ncx,
                        const double* __restrict__ ncy, const double* __restrict__ ncz,
                        unsigned long long* __restrict__ l2bits) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  int v = (i < n) ? pnode[i] : -1;
+  int v = -1;
+  unsigned long long m0 = 0ull, m1 = 0ull;
   double x = 0.0, y = 0.0, z = 0.0;
   if (i < n) {
+    const int L = pnode[i];
+    v = wparent[L];  // the leaf itself was done by k_size_leaf
+    const uint32_t q = leaf_index[L];
+    m0 = cand[2 * (size_t)q];
+    m1 = cand[2 * (size_t)q + 1];
     x = px[i];
     y = py[i];
     z = pz[i];
   }
+  int k = 1;
   while (true) {
-    unsigned act = __ballot_sync(SFMM_FULL, v >= 0);
+    const unsigned act = __ballot_sync(SFMM_FULL, v >= 0);
     if (act == 0u) break;
-    if (v >= 0) {
-      double dx = dsub(x, ncx[v]), dy = dsub(y, ncy[v]), dz = dsub(z, ncz[v]);
-      double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+    const bool want = v >= 0 && (k >= 128 || ((k < 64 ? (m0 >> k) : (m1 >> (k - 64))) & 1ull));
+    const unsigned actw = __ballot_sync(SFMM_FULL, want);
+    if (want) {
+      const double d2 = exact_d2(x, y, z, ncx[v], ncy[v], ncz[v]);
       unsigned long long bits = (unsigned long long)__double_as_longlong(d2);
-      unsigned grp = __match_any_sync(act, v);
+      unsigned grp = __match_any_sync(actw, v);
       unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
       unsigned mhi = __reduce_max_sync(grp, hi);
       unsigned mlo = __reduce_max_sync(grp, hi == mhi ? lo : 0u);
       if ((__ffs(grp) - 1) == lane) atomicMax(&l2bits[v], ((unsigned long long)mhi << 32) | mlo);
-      v = wparent[v];  // stops after the system root (-1)
     }
+    if (v >= 0) v = wparent[v];  // stops after the system root (-1)
+    ++k;
   }
 }
 
@@ -848,6 +947,10 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ENS(geo_lo, sizeof(float4) * nn_max);
   ENS(leaf_node, sizeof(int) * nn_max);
   ENS(nlu, sizeof(int) * nn_max);
+  ENS(n_extv, sizeof(double) * 6 * nn_max);
+  ENS(n_exti, sizeof(int) * 6 * nn_max);
+  ENS(n_lb, sizeof(double) * nn_max);
+  ENS(size_cand, sizeof(unsigned long long) * 2 * nn_max);
   const int nbb = 2 * num_sms(c->device);
   ENS(bbox_part, sizeof(double) * 6 * nbb);
 #undef ENS
@@ -984,19 +1087,31 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
       nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
       c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
       c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),
-      c->nlu.as<int>());
+      c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaMemsetAsync(c->flags.p, 0, sizeof(int) * nnodes, st));
   k_upward<<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
                                           c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
                                           c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
-                                          c->flags.as<int>());
+                                          c->flags.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaMemsetAsync(c->l2bits.p, 0, sizeof(unsigned long long) * nnodes, st));
+  k_node_lb<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->wparent.as<int>(), c->n_exti.as<int>(),
+                                               c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
+                                               c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
+                                               c->n_lb.as<double>());
+  k_size_leaf<<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(),
+                                             c->wparent.as<int>(), c->px.as<double>(), c->py.as<double>(),
+                                             c->pz.as<double>(), c->ncx.as<double>(), c->ncy.as<double>(),
+                                             c->ncz.as<double>(), c->n_lb.as<double>(),
+                                             c->l2bits.as<unsigned long long>(),
+                                             c->size_cand.as<unsigned long long>());
   k_size<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
-                                       c->pnode.as<int>(), c->wparent.as<int>(), c->ncx.as<double>(),
-                                       c->ncy.as<double>(), c->ncz.as<double>(),
+                                       c->pnode.as<int>(), c->isleaf.as<uint32_t>(),
+                                       c->size_cand.as<unsigned long long>(), c->wparent.as<int>(),
+                                       c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
                                        c->l2bits.as<unsigned long long>());
+  c->nlaunch += 2;
   ++c->nlaunch;
   k_finalize_nodes<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->l2bits.as<unsigned long long>(), c->ncx.as<double>(),
                                                       c->ncy.as<double>(), c->ncz.as<double>(), c->nhmax.as<double>(),
