@@ -341,6 +341,7 @@ int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot)
   int rc;
   cudaStream_t st = c->stream;
   if (c->profile) cudaEventRecord(c->ev[2], st);
+  c->pref_order = order;  // later builds compute these moments on the way up
   if (c->moments_order != order) {
     if ((rc = compute_moments(c, order))) return set_error(c, rc, "moment pass failed");
   }

@@ -3,24 +3,11 @@
 // particles at the leaves (P2M) and translated bottom-up to the parents
 // (Eq. massmomtrans, App. A.1: Q'_alpha/alpha! = sum_{beta<=alpha}
 // g^(alpha-beta)/(alpha-beta)! Q_beta/beta!, g = child - parent centre).
-#include "expansion_gen.cuh"
+#include "mom_ops.cuh"
 #include "sfmm_internal.cuh"
 
 namespace sfmm {
 
-template <int P> struct MomOps;
-#define SFMM_MOMOPS(PP)                                                                               \
-  template <> struct MomOps<PP> {                                                                     \
-    static constexpr int NQ = ncoef(PP);                                                              \
-    template <typename T> __device__ static void mono(T x, T y, T z, T* o) { sfmm_mono_##PP(x, y, z, o); } \
-    template <typename T> __device__ static void m2m(const T* g, const T* qc, T* qp) { sfmm_m2m_##PP(g, qc, qp); } \
-  };
-SFMM_MOMOPS(0)
-SFMM_MOMOPS(1)
-SFMM_MOMOPS(2)
-SFMM_MOMOPS(3)
-SFMM_MOMOPS(4)
-#undef SFMM_MOMOPS
 
 // P2M: one thread per leaf (short FP64 sums; no cross-lane reduction).
 template <int P>

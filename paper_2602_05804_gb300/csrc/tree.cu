@@ -4,6 +4,7 @@
 // exact sizes l = max_j |x_j - s| over each node's particles.
 #include <cfloat>
 
+#include "mom_ops.cuh"
 #include "sfmm_internal.cuh"
 
 namespace sfmm {
@@ -595,13 +596,17 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // One thread per leaf (the FP64 sums of a leaf are short; warp reductions in
 // FP64 would cost more than the sums themselves).
+// P >= 0: also the leaf's scaled moments of order P about its centre of mass
+// (P2M, Eq. massmom) in FP64 and their FP32 copy; P < 0: geometry only.
+template <int P>
 __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
                             const int* __restrict__ ncount, const double* __restrict__ px,
                             const double* __restrict__ py, const double* __restrict__ pz,
                             const double* __restrict__ pm, const double* __restrict__ ph,
                             double* __restrict__ ncx, double* __restrict__ ncy, double* __restrict__ ncz,
                             double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ pnode,
-                            int* __restrict__ nlu, double* __restrict__ extv, int* __restrict__ exti) {
+                            int* __restrict__ nlu, double* __restrict__ extv, int* __restrict__ exti,
+                            double* __restrict__ Qd, float* __restrict__ Qf, int nqs) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nleaves) return;
   const int v = leaf_node[q];
@@ -631,17 +636,40 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
     exti[6 * (size_t)v + c] = ei[c];
   }
   nmass[v] = M;
-  ncx[v] = __ddiv_rn(sx, M);
-  ncy[v] = __ddiv_rn(sy, M);
-  ncz[v] = __ddiv_rn(sz, M);
+  const double cx = __ddiv_rn(sx, M), cy = __ddiv_rn(sy, M), cz = __ddiv_rn(sz, M);
+  ncx[v] = cx;
+  ncy[v] = cy;
+  ncz[v] = cz;
   nhmax[v] = hm;
   nlu[v] = 1;
+  if constexpr (P >= 0) {
+    constexpr int NQ = MomOps<P>::NQ;
+    double acc[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) acc[k] = 0.0;
+    for (int i = f; i < f + cnt; ++i) {
+      double mono[NQ];
+      MomOps<P>::mono(px[i] - cx, py[i] - cy, pz[i] - cz, mono);
+      const double m = pm[i];
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) acc[k] = fma(m, mono[k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) Qd[(int64_t)v * NQ + k] = acc[k];
+    constexpr int NQS = (NQ + 3) & ~3;  // == nqs
+#pragma unroll
+    for (int k = 0; k < NQS; ++k) Qf[(int64_t)v * NQS + k] = (k < NQ) ? __double2float_rn(acc[k]) : 0.0f;
+  }
 }
 
-// Bottom-up: the second child to finish computes its parent.
+// Bottom-up: the second child to finish computes its parent (P >= 0: also
+// the parent's moments, both children's translated to its centre, Eq.
+// massmomtrans).
+template <int P>
 __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nparent,
                          const int* __restrict__ nright, double* ncx, double* ncy, double* ncz, double* nmass,
-                         double* nhmax, int* nlu, int* flags, double* extv, int* exti) {
+                         double* nhmax, int* nlu, int* flags, double* extv, int* exti, double* Qd, float* Qf,
+                         int nqs) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nleaves) return;
   int v = nparent[leaf_node[q]];
@@ -652,9 +680,35 @@ __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const i
     int L = v + 1, R = nright[v];
     double mL = __ldcg(&nmass[L]), mR = __ldcg(&nmass[R]);
     double M = dadd(mL, mR);
-    ncx[v] = __ddiv_rn(dadd(dmul(mL, __ldcg(&ncx[L])), dmul(mR, __ldcg(&ncx[R]))), M);
-    ncy[v] = __ddiv_rn(dadd(dmul(mL, __ldcg(&ncy[L])), dmul(mR, __ldcg(&ncy[R]))), M);
-    ncz[v] = __ddiv_rn(dadd(dmul(mL, __ldcg(&ncz[L])), dmul(mR, __ldcg(&ncz[R]))), M);
+    const double cLx = __ldcg(&ncx[L]), cLy = __ldcg(&ncy[L]), cLz = __ldcg(&ncz[L]);
+    const double cRx = __ldcg(&ncx[R]), cRy = __ldcg(&ncy[R]), cRz = __ldcg(&ncz[R]);
+    const double cx = __ddiv_rn(dadd(dmul(mL, cLx), dmul(mR, cRx)), M);
+    const double cy = __ddiv_rn(dadd(dmul(mL, cLy), dmul(mR, cRy)), M);
+    const double cz = __ddiv_rn(dadd(dmul(mL, cLz), dmul(mR, cRz)), M);
+    ncx[v] = cx;
+    ncy[v] = cy;
+    ncz[v] = cz;
+    if constexpr (P >= 0) {
+      constexpr int NQ = MomOps<P>::NQ;
+      double qp[NQ];
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) qp[k] = 0.0;
+      const int kids[2] = {L, R};
+      const double kx[2] = {cLx, cRx}, ky[2] = {cLy, cRy}, kz[2] = {cLz, cRz};
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        double g[NQ], qc[NQ];
+        MomOps<P>::mono(kx[c] - cx, ky[c] - cy, kz[c] - cz, g);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) qc[k] = __ldcg(&Qd[(int64_t)kids[c] * NQ + k]);
+        MomOps<P>::m2m(g, qc, qp);
+      }
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) Qd[(int64_t)v * NQ + k] = qp[k];
+      constexpr int NQS = (NQ + 3) & ~3;  // == nqs
+#pragma unroll
+      for (int k = 0; k < NQS; ++k) Qf[(int64_t)v * NQS + k] = (k < NQ) ? __double2float_rn(qp[k]) : 0.0f;
+    }
     nmass[v] = M;
     nhmax[v] = fmax(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
     nlu[v] = __ldcg(&nlu[L]) + __ldcg(&nlu[R]);
@@ -899,6 +953,28 @@ int compute_depth(sfmm_ctx* c) {
 // ---------------------------------------------------------------------------
 // Host orchestration of the build
 // ---------------------------------------------------------------------------
+template <int P>
+static int geom_upward(sfmm_ctx* c, int nnodes, int nqs) {
+  cudaStream_t st = c->stream;
+  const int nl = c->nleaves;
+  (void)nnodes;
+  k_leaf_geom<P><<<nblk(nl, 128), 128, 0, st>>>(
+      nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
+      c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
+      c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),
+      c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->Qd.as<double>(),
+      c->Qf.as<float>(), nqs);
+  ++c->nlaunch;
+  k_upward<P><<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
+                                          c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
+                                          c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
+                                          c->flags.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->Qd.as<double>(),
+      c->Qf.as<float>(), nqs);
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
+  return SFMM_OK;
+}
+
 int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double* h) {
   const int n = (int)c->n;
   cudaStream_t st = c->stream;
@@ -1082,19 +1158,22 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
 
-  // S4 geometry
-  k_leaf_geom<<<nblk(nl, 128), 128, 0, st>>>(
-      nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
-      c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
-      c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),
-      c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>());
-  ++c->nlaunch;
+  // S4 geometry, and the moments of the order the last gravity call used
+  // (P2M at the leaves, M2M on the way up: the same passes)
+  const int P = c->pref_order;
+  const int NQ = (int)ncoef(P), nqs = (NQ + 3) & ~3;
+  if ((rc = c->Qd.ensure(sizeof(double) * (size_t)nnodes * NQ)) ||
+      (rc = c->Qf.ensure(sizeof(float) * (size_t)nnodes * nqs)))
+    return rc;
   SFMM_CUDA_TRY(cudaMemsetAsync(c->flags.p, 0, sizeof(int) * nnodes, st));
-  k_upward<<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
-                                          c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                          c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
-                                          c->flags.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>());
-  ++c->nlaunch;
+  switch (P) {
+    case 0: rc = geom_upward<0>(c, nnodes, nqs); break;
+    case 1: rc = geom_upward<1>(c, nnodes, nqs); break;
+    case 2: rc = geom_upward<2>(c, nnodes, nqs); break;
+    case 3: rc = geom_upward<3>(c, nnodes, nqs); break;
+    default: rc = geom_upward<4>(c, nnodes, nqs); break;
+  }
+  if (rc) return rc;
   SFMM_CUDA_TRY(cudaMemsetAsync(c->l2bits.p, 0, sizeof(unsigned long long) * nnodes, st));
   k_node_lb<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->wparent.as<int>(), c->n_exti.as<int>(),
                                                c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
@@ -1124,6 +1203,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
                                                 c->prel.as<float4>(), c->ph32.as<float>(), c->phh.as<float2>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
+  c->moments_order = P;
   if (c->keys_a.p != (void*)ka_final) {
     // keep the sorted keys in keys_a for export (even number of passes: no-op)
     SFMM_CUDA_TRY(cudaMemcpyAsync(c->keys_a.p, ka_final, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
