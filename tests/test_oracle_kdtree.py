@@ -19,7 +19,7 @@ import workloads
 from test_oracle_tree_sfmm import _recursive_pairs
 
 
-@pytest.fixture(scope="module", params=[("uniform", 3000, 10), ("plummer", 4000, 16), ("plummer", 1500, 1),
+@pytest.fixture(scope="module", params=[("uniform", 3000, 10), ("plummer", 4000, 16), ("plummer", 700, 1),
                                         ("uniform", 1200, 64)])
 def kd(request):
     kind, n, ls = request.param
