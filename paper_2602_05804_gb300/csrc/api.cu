@@ -355,6 +355,9 @@ int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot)
   if (c->nsys > 1 && (rc = run_reduce_systems(c))) return set_error(c, rc, "reduction failed");
   if (c->profile) cudaEventRecord(c->ev[6], st);
   cudaError_t e = cudaMemcpyAsync(c->h_scalars + 16, red, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)  // pair evaluations, counted by the near-field pass
+    e = cudaMemcpyAsync(c->h_scalars + 24, c->counters.as<unsigned long long>() + 3, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return set_error(c, SFMM_ECUDA, cudaGetErrorString(e));
   int bits = 0;
   if ((rc = sync_status(c, &bits))) return rc;
@@ -365,6 +368,7 @@ int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot)
   c->stats.momentum[2] = r[2];
   c->stats.abs_momentum = r[3];
   c->stats.W = 0.5 * r[4];
+  c->stats.p2p_pairs = (int64_t) * reinterpret_cast<const unsigned long long*>(c->h_scalars + 24);
   if (c->profile) {
     c->stats.ms_moments = elapsed(c->ev[2], c->ev[3]);
     c->stats.ms_walk = elapsed(c->ev[3], c->ev[4]);

@@ -57,6 +57,7 @@ struct P2PArgs {
   const int* slist;   // the split leaves
   void* part;         // [slot][lmax][4] partial sums in the form's type
   int lmax;
+  unsigned long long* pair_counter;  // pair evaluations (statistics)
 };
 
 // M4 softening kernel of one particle (compact support 2h), evaluated with
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
   const int nitems = a.nextra + a.nleaves;
+  unsigned long long pairs = 0;  // this lane's share of the pair evaluations
   while (true) {
     int item = 0;
     if (lane == 0) item = atomicAdd(a.leaf_counter, 1);
@@ -258,6 +260,7 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
           const int S = a.arena[off + k];
           fS = a.nfirst[S];
           nS = a.ncount[S];
+          pairs += (unsigned long long)nL * nS - (S == L ? nL : 0);
           if constexpr (F32) {
             const float4 hS = a.geo_hi[S], lS = a.geo_lo[S];
             ox = df_diff(hS.x, lS.x, hiL.x, loL.x);
@@ -408,6 +411,9 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
       for (int c = 0; c < 5; ++c) a.leafsum[5 * (size_t)leaf + c] = sm[c];
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(SFMM_FULL, pairs, o);
+  if (lane == 0 && pairs) atomicAdd(a.pair_counter, pairs);
 }
 
 // Long lists: thread per leaf; a list of more than SFMM_P2P_CHUNK entries
@@ -609,6 +615,7 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   a.slist = nsplit > 0 ? c->p2p_slist.as<int>() : nullptr;
   a.part = nsplit > 0 ? c->p2p_part.p : nullptr;
   a.lmax = lmax;
+  a.pair_counter = ctr + 3;
   const int nt = 32 * (f32 ? p2p_warps<true>() : p2p_warps<false>());
   int per_sm = 0;
   if (f32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<true>, nt, 0);

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
   int* const bufA = a.ring + (size_t)gw * 2 * cap;
   int* const bufB = bufA + cap;
 
-  unsigned long long st_m2l = 0, st_uniq = 0, st_pl = 0, st_pp = 0;
+  unsigned long long st_m2l = 0, st_uniq = 0, st_pl = 0;
   int st_fb = 0;
 
   while (true) {
@@ -324,19 +324,12 @@ __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
         a.p2p_cnt[leaf] = 0;
       }
     } else {
-      unsigned long long pairs = 0;
-      for (int t = lane; t < nn; t += 32) {
-        const int sN = nxt[t];
-        a.arena[base + t] = sN;
-        pairs += (unsigned long long)nL * a.ncount[sN] - (sN == L ? nL : 0);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(SFMM_FULL, pairs, o);
+      // (the pair count is taken by the near-field pass, which loads the counts anyway)
+      for (int t = lane; t < nn; t += 32) a.arena[base + t] = nxt[t];
       if (lane == 0) {
         a.p2p_off[leaf] = (long long)base;
         a.p2p_cnt[leaf] = nn;
         st_pl += nn;
-        st_pp += pairs;
         if (nn > SFMM_P2P_CHUNK) {
           atomicAdd(a.split_counter, (unsigned long long)((nn + SFMM_P2P_CHUNK - 1) / SFMM_P2P_CHUNK));
           atomicAdd(a.split_counter + 1, 1ull);
@@ -352,7 +345,6 @@ __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
     atomicAdd(&a.stat[0], st_m2l);
     atomicAdd(&a.stat[1], st_uniq);
     atomicAdd(&a.stat[2], st_pl);
-    atomicAdd(&a.stat[3], st_pp);
     atomicAdd(&a.stat[4], (unsigned long long)st_fb);
   }
 }
