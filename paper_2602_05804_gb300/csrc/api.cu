@@ -252,32 +252,12 @@ int build_common(sfmm_ctx* c, const double* pos, const double* mass, const doubl
   if (c->profile) cudaEventRecord(c->ev[0], c->stream);
   rc = build_tree(c, pos, mass, h);
   if (rc) return set_error(c, rc, "tree build failed");
-  if ((rc = build_levels(c))) return set_error(c, rc, "level lists failed");
-  // walkable internal-node level offsets to the host (the tree is at most 128
-  // levels deep: system, key and position bits distinguish every particle)
-  const int ncopy = (int)std::min<int64_t>((int64_t)c->nnodes + 1, 130);
-  c->h_level_off.assign(ncopy, 0);
-  uint32_t h_tot = 0;
-  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_off.data(), c->level_off.p, sizeof(int) * ncopy, cudaMemcpyDeviceToHost,
-                                c->stream));
-  SFMM_CUDA_TRY(cudaMemcpyAsync(&h_tot, c->level_off.as<uint32_t>() + 2 * ((size_t)c->nnodes + 1), sizeof(uint32_t),
-                                cudaMemcpyDeviceToHost, c->stream));
   if (c->profile) cudaEventRecord(c->ev[1], c->stream);
   int bits = 0;
   if ((rc = sync_status(c, &bits))) return rc;
   if (bits & (SFMM_ST_NONFINITE | SFMM_ST_NONPOSITIVE))
     return set_error(c, SFMM_ENONFINITE, "non-finite position/mass/h or non-positive mass/h");
   if (bits) return set_error(c, SFMM_ECUDA, "internal consistency check of the tree failed");
-  // deepest level holding a walkable internal node (-1: none)
-  const int nint = (int)h_tot;
-  c->max_depth = -2;
-  for (int d = 0; d < (int)c->h_level_off.size(); ++d)
-    if (c->h_level_off[d] >= nint) {
-      c->max_depth = d - 1;
-      break;
-    }
-  if (c->max_depth < -1) return set_error(c, SFMM_ESTACK, "tree deeper than 128 levels");
-  c->h_level_off.resize(c->max_depth + 2);
   c->built = true;
   c->stats = sfmm_stats{};
   c->stats.n = c->n;

@@ -723,6 +723,71 @@ __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const i
   }
 }
 
+// Bottom-up, one launch per depth (deepest first): every internal node of
+// the level combines its two finished children -- mass, centre of mass,
+// h_max, leaves below, axis-extreme particles and (P >= 0) the moments
+// translated to the new centre (Eq. massmomtrans).
+template <int P>
+__device__ __forceinline__ void upward_node(int v, const int* __restrict__ nright, double* __restrict__ ncx,
+                                            double* __restrict__ ncy, double* __restrict__ ncz,
+                                            double* __restrict__ nmass, double* __restrict__ nhmax,
+                                            int* __restrict__ nlu, double* __restrict__ extv,
+                                            int* __restrict__ exti, double* __restrict__ Qd, float* __restrict__ Qf) {
+  const int L = v + 1, R = nright[v];
+  const double mL = nmass[L], mR = nmass[R];
+  const double M = dadd(mL, mR);
+  const double cLx = ncx[L], cLy = ncy[L], cLz = ncz[L];
+  const double cRx = ncx[R], cRy = ncy[R], cRz = ncz[R];
+  const double cx = __ddiv_rn(dadd(dmul(mL, cLx), dmul(mR, cRx)), M);
+  const double cy = __ddiv_rn(dadd(dmul(mL, cLy), dmul(mR, cRy)), M);
+  const double cz = __ddiv_rn(dadd(dmul(mL, cLz), dmul(mR, cRz)), M);
+  ncx[v] = cx;
+  ncy[v] = cy;
+  ncz[v] = cz;
+  nmass[v] = M;
+  nhmax[v] = fmax(nhmax[L], nhmax[R]);
+  nlu[v] = nlu[L] + nlu[R];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const double a = extv[6 * (size_t)L + c], b = extv[6 * (size_t)R + c];
+    const bool right = (c < 3) ? (b < a) : (b > a);
+    extv[6 * (size_t)v + c] = right ? b : a;
+    exti[6 * (size_t)v + c] = exti[6 * (size_t)(right ? R : L) + c];
+  }
+  if constexpr (P >= 0) {
+    constexpr int NQ = MomOps<P>::NQ;
+    double qp[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) qp[k] = 0.0;
+    const int kids[2] = {L, R};
+    const double kx[2] = {cLx, cRx}, ky[2] = {cLy, cRy}, kz[2] = {cLz, cRz};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      double g[NQ], qc[NQ];
+      MomOps<P>::mono(kx[c] - cx, ky[c] - cy, kz[c] - cz, g);
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) qc[k] = Qd[(int64_t)kids[c] * NQ + k];
+      MomOps<P>::m2m(g, qc, qp);
+    }
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) Qd[(int64_t)v * NQ + k] = qp[k];
+    constexpr int NQS = (NQ + 3) & ~3;
+#pragma unroll
+    for (int k = 0; k < NQS; ++k) Qf[(int64_t)v * NQS + k] = (k < NQ) ? __double2float_rn(qp[k]) : 0.0f;
+  }
+}
+
+template <int P>
+__global__ void k_upward_level(int count, const int* __restrict__ nodes, const int* __restrict__ nright,
+                               double* __restrict__ ncx, double* __restrict__ ncy, double* __restrict__ ncz,
+                               double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ nlu,
+                               double* __restrict__ extv, int* __restrict__ exti, double* __restrict__ Qd,
+                               float* __restrict__ Qf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) upward_node<P>(nodes[t], nright, ncx, ncy, ncz, nmass, nhmax, nlu, extv, exti, Qd, Qf);
+}
+
+
 // Exact node sizes l_v = max over the node's particles of |x_i - s_v| (the
 // squared distance rounded as written, then one square root).  Most
 // (particle, ancestor) pairs cannot hold the maximum, so only candidates are
@@ -953,25 +1018,71 @@ int compute_depth(sfmm_ctx* c) {
 // ---------------------------------------------------------------------------
 // Host orchestration of the build
 // ---------------------------------------------------------------------------
+// The upward pass climbs from every leaf with atomic arrival flags (one
+// launch; each climb pays fences) or runs one launch per depth; measured on
+// GB300 the climb wins below about half a million leaves.
+#define UP_LEVEL_MIN_LEAVES (1 << 19)
+
 template <int P>
-static int geom_upward(sfmm_ctx* c, int nnodes, int nqs) {
+static int geom_upward(sfmm_ctx* c, int nqs) {
   cudaStream_t st = c->stream;
   const int nl = c->nleaves;
-  (void)nnodes;
   k_leaf_geom<P><<<nblk(nl, 128), 128, 0, st>>>(
       nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
       c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
       c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),
-      c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->Qd.as<double>(),
-      c->Qf.as<float>(), nqs);
+      c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->Qd.as<double>(), c->Qf.as<float>(), nqs);
   ++c->nlaunch;
-  k_upward<P><<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
-                                          c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                          c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
-                                          c->flags.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->Qd.as<double>(),
-      c->Qf.as<float>(), nqs);
-  ++c->nlaunch;
+  if (nl >= UP_LEVEL_MIN_LEAVES) {
+    // many leaves: one launch per depth (no atomics or fences)
+    for (int d = c->max_depth; d >= 0; --d) {
+      const int lo = c->h_level_off[d], cnt = c->h_level_off[d + 1] - lo;
+      if (cnt <= 0) continue;
+      k_upward_level<P><<<nblk(cnt, 128), 128, 0, st>>>(
+          cnt, c->level_nodes.as<int>() + lo, c->nright.as<int>(), c->ncx.as<double>(), c->ncy.as<double>(),
+          c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
+          c->n_extv.as<double>(), c->n_exti.as<int>(), c->Qd.as<double>(), c->Qf.as<float>());
+      ++c->nlaunch;
+    }
+  } else {
+    // fewer leaves: one launch, the second child to finish climbs on
+    SFMM_CUDA_TRY(cudaMemsetAsync(c->flags.p, 0, sizeof(int) * (size_t)c->nnodes, st));
+    k_upward<P><<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
+                                               c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
+                                               c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
+                                               c->flags.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(),
+                                               c->Qd.as<double>(), c->Qf.as<float>(), nqs);
+    ++c->nlaunch;
+  }
   SFMM_CUDA_TRY(cudaGetLastError());
+  return SFMM_OK;
+}
+
+// Depth, the per-depth lists of walkable internal nodes (the upward pass and
+// the walk run over them) and their offsets on the host (one synchronisation).
+static int levels_to_host(sfmm_ctx* c) {
+  int rc;
+  if ((rc = build_levels(c))) return rc;
+  // the tree is at most 128 levels deep: system, key and position bits
+  // distinguish every particle
+  const int ncopy = (int)std::min<int64_t>((int64_t)c->nnodes + 1, 130);
+  c->h_level_off.assign(ncopy, 0);
+  uint32_t h_tot = 0;
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_off.data(), c->level_off.p, sizeof(int) * ncopy, cudaMemcpyDeviceToHost,
+                                c->stream));
+  SFMM_CUDA_TRY(cudaMemcpyAsync(&h_tot, c->level_off.as<uint32_t>() + 2 * ((size_t)c->nnodes + 1), sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, c->stream));
+  SFMM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  // deepest level holding a walkable internal node (-1: none)
+  const int nint = (int)h_tot;
+  c->max_depth = -2;
+  for (int d = 0; d < (int)c->h_level_off.size(); ++d)
+    if (c->h_level_off[d] >= nint) {
+      c->max_depth = d - 1;
+      break;
+    }
+  if (c->max_depth < -1) return SFMM_ESTACK;
+  c->h_level_off.resize(c->max_depth + 2);
   return SFMM_OK;
 }
 
@@ -1165,13 +1276,13 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   if ((rc = c->Qd.ensure(sizeof(double) * (size_t)nnodes * NQ)) ||
       (rc = c->Qf.ensure(sizeof(float) * (size_t)nnodes * nqs)))
     return rc;
-  SFMM_CUDA_TRY(cudaMemsetAsync(c->flags.p, 0, sizeof(int) * nnodes, st));
+  if ((rc = levels_to_host(c))) return rc;
   switch (P) {
-    case 0: rc = geom_upward<0>(c, nnodes, nqs); break;
-    case 1: rc = geom_upward<1>(c, nnodes, nqs); break;
-    case 2: rc = geom_upward<2>(c, nnodes, nqs); break;
-    case 3: rc = geom_upward<3>(c, nnodes, nqs); break;
-    default: rc = geom_upward<4>(c, nnodes, nqs); break;
+    case 0: rc = geom_upward<0>(c, nqs); break;
+    case 1: rc = geom_upward<1>(c, nqs); break;
+    case 2: rc = geom_upward<2>(c, nqs); break;
+    case 3: rc = geom_upward<3>(c, nqs); break;
+    default: rc = geom_upward<4>(c, nqs); break;
   }
   if (rc) return rc;
   SFMM_CUDA_TRY(cudaMemsetAsync(c->l2bits.p, 0, sizeof(unsigned long long) * nnodes, st));
