@@ -304,15 +304,14 @@ NCOEF_P2 = 10
 
 def stage_rooflines(st, n, fp32_peak, hbm_peak):
     """Achieved fraction of each stage's roofline from live CUDA-event stage
-    times: build and moments against HBM (algorithmic bytes), the walk (M2L)
-    and P2P against the FP32 FMA units (algorithmic flops)."""
+    times: the build (which also forms the moments of the order in use)
+    against HBM (algorithmic bytes), the walk (M2L) and P2P against the FP32
+    FMA units (algorithmic flops)."""
     nn = st["nnodes"]
-    b_build = n * (40 + 40 + 16) + nn * (16 + NCOEF_P2) * 8
-    b_mom = n * 32 + nn * (NCOEF_P2 + 4) * 8
+    b_build = n * (40 + 40 + 16) + nn * (16 + NCOEF_P2) * 8 + n * 32 + nn * (NCOEF_P2 + 4) * 8
     out = {}
     for key, ms, work, unit, peak in (
-            ("build", st["ms_build"], b_build / 1e9, "GB/s", hbm_peak),
-            ("moments", st["ms_moments"], b_mom / 1e9, "GB/s", hbm_peak),
+            ("build_and_moments", st["ms_build"] + st["ms_moments"], b_build / 1e9, "GB/s", hbm_peak),
             ("walk_m2l", st["ms_walk"], st["m2l_unique"] * M2L_FLOPS_P2 / 1e12, "TFLOP/s", fp32_peak),
             ("p2p", st["ms_p2p"], st["p2p_pairs"] * FLOPS_PER_PAIR / 1e12, "TFLOP/s", fp32_peak)):
         ach = work / (ms * 1e-3) if ms > 0 else 0.0
