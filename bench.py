@@ -444,8 +444,8 @@ def run_gpu(args):
     pot = torch.empty(w["n"], dtype=torch.float64, device=dev)
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    s32 = sfmm.Solver(local, "fp32", profile=1, walk=args.walk)
-    s64 = sfmm.Solver(local, "fp64", profile=1, walk=args.walk)
+    s32 = sfmm.Solver(local, "fp32", profile=1, walk=args.walk, schedule=args.schedule)
+    s64 = sfmm.Solver(local, "fp64", profile=1, walk=args.walk, schedule=args.schedule)
 
     def barrier():
         if dist is not None:
@@ -508,6 +508,18 @@ def run_gpu(args):
                 "particles_per_s": ws * w["n"] / (np.mean(ms_s) * 1e-3), "ms_per_step": float(np.mean(ms_s)),
                 "stage_ms": {"build": st_s["ms_build"], "moments": st_s["ms_moments"], "walk": st_s["ms_walk"],
                              "p2p": st_s["ms_p2p"]}}
+
+    # the shared walk under both node orders (bitwise the same results): one
+    # launch per depth, and one launch over a queue of nodes whose parent is
+    # done; the automatic choice takes the queue while the walk's per-node
+    # records fit in L2
+    schedules = {}
+    for sched, label in ((1, "one launch per depth"), (2, "readiness queue")):
+        sq = sfmm.Solver(local, "fp32", profile=1, walk=1, schedule=sched)
+        ms_q, st_q = time_steps(torch, sq, pos_d, m_d, h_d, acc, pot, w, w["theta"], max(1, min(args.steps, 3)), 1,
+                                flush)
+        sq.close()
+        schedules[label] = {"ms_per_step": float(np.mean(ms_q)), "walk_ms": st_q["ms_walk"]}
 
     ensemble = None
     if not args.no_ensemble:
@@ -576,6 +588,7 @@ def run_gpu(args):
                    "leaf_size": w["leaf_size"], "form": "FP32 (FP64 centres, decisions, reductions)",
                    "walk": {0: "per-leaf replay (Algorithm 1)", 1: "per-node shared pairs",
                             2: "one-sided symmetric pairs"}[args.walk],
+                   "schedule": {0: "automatic", 1: "one launch per depth", 2: "readiness queue"}[args.schedule],
                    "l2": "flushed between timed steps (512 MB write outside the events)"},
         "interactions_per_s": ws * inter / (step_ms * 1e-3),
         "counts": {"m2l_replicated": st32["m2l"], "m2l_unique": st32["m2l_unique"],
@@ -589,6 +602,7 @@ def run_gpu(args):
         "theta_sweep_fp32": sweep,
         "other_walk_fp32": other_walk,
         "symmetric_walk_fp32": sym_walk,
+        "walk_schedules_fp32": schedules,
         "ensemble_256": ensemble,
         "stage_rooflines": stage_rooflines(st32, w["n"], fp32_peak, hbm_peak),
         "configs": configs,
@@ -630,7 +644,10 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="particle count (default: the workload's 10^6)")
     ap.add_argument("--leaf", type=int, default=None, help="leaf size (default: the workload's 16)")
     ap.add_argument("--walk", type=int, default=1, choices=[0, 1, 2],
-                    help="headline walk: 1 per-node shared pairs (default), 0 per-leaf replay (Algorithm 1)")
+                    help="headline walk: 1 per-node shared pairs (default), 0 per-leaf replay (Algorithm 1), "
+                         "2 one-sided symmetric pairs")
+    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2],
+                    help="walk 1 node order: 0 automatic (default), 1 one launch per depth, 2 readiness queue")
     ap.add_argument("--only", default="all", choices=["all", "fp32"],
                     help="fp32: time the headline FP32 step only (for profiler launch lists)")
     args = ap.parse_args()

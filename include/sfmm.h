@@ -107,8 +107,20 @@ int sfmm_set_stream(sfmm_ctx* ctx, void* stream);
  *   "walk"           1 (default): each node's pairs are evaluated once and
  *                    shared by the leaves below it (the caching of shared
  *                    interactions proposed in Sect. 5); 0: each leaf replays
- *                    the walk of its branch (Algorithm 1 as printed); same
+ *                    the walk of its branch (Algorithm 1 as printed); 2: as
+ *                    1, with each accepted pair's derivative tensor evaluated
+ *                    once for both nodes (the one-sided symmetric form of
+ *                    Sect. 5, FP64 accumulation of the partner's side); same
  *                    interactions, same results up to summation order
+ *   "schedule"       order of the nodes in walk 1 (a node needs its parent's
+ *                    opened list and coefficients): 1 one launch per depth;
+ *                    2 one launch in which a warp takes the next node whose
+ *                    parent is done from a queue; 0 (default) chooses 2 when
+ *                    the walk's per-node records fit in three quarters of the
+ *                    L2 cache, else 1; bitwise the same results
+ *   "tree"           0 (default): binary radix tree over Morton keys (Sect. 3);
+ *                    1: centre-of-mass-pivot kd tree (Sect. 3; single
+ *                    systems only, sfmm_build_batch returns ENOTIMPL)
  *   "profile"        1 records per-stage device times into the stats
  * Errors: EINVAL (unknown key or out-of-range value). */
 int sfmm_set_option(sfmm_ctx* ctx, const char* key, double value);

@@ -170,7 +170,7 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_leaf_off, &c->sys_sums,
                     &c->p2p_extra, &c->p2p_split, &c->p2p_slist, &c->p2p_part, &c->lf_acc, &c->lf_part,
                     &c->kd_ord, &c->kd_node, &c->kd_act, &c->kd_work, &c->kd_chunk, &c->kd_part, &c->kd_split,
-                    &c->sym_own, &c->sym_recv, &c->n_extv, &c->n_exti, &c->n_lb, &c->size_cand};
+                    &c->sym_own, &c->sym_recv, &c->wqueue, &c->n_extv, &c->n_exti, &c->n_lb, &c->size_cand};
   for (DevBuf* b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -217,6 +217,10 @@ int sfmm_set_option(sfmm_ctx* c, const char* key, double v) {
     if (v != 0.0 && v != 1.0 && v != 2.0)
       return set_error(c, SFMM_EINVAL, "walk: 0 (per-leaf replay), 1 (per-node shared pairs), 2 (one-sided symmetric pairs)");
     c->walk_mode = (int)v;
+  } else if (!strcmp(key, "schedule")) {
+    if (v != 0.0 && v != 1.0 && v != 2.0)
+      return set_error(c, SFMM_EINVAL, "schedule: 0 (automatic), 1 (one launch per depth), 2 (readiness queue)");
+    c->schedule = (int)v;
   } else if (!strcmp(key, "tree")) {
     if (v != 0.0 && v != 1.0) return set_error(c, SFMM_EINVAL, "tree: 0 (Morton radix tree) or 1 (centre-of-mass kd tree)");
     c->tree_kind = (int)v;

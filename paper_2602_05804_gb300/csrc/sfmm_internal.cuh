@@ -48,6 +48,7 @@ struct sfmm_ctx {
   int pref_order = 2;      // order the build computes moments for (the last gravity call's)
   int walk_mode = 1;        // 1: per-node shared pairs (default), 0: per-leaf replay (Algorithm 1),
                             // 2: per-node pairs, each evaluated once for both sides
+  int schedule = 0;         // walk mode 1: 0 automatic, 1 one launch per depth, 2 readiness queue
   int max_depth = 0;
   std::vector<int> h_level_off;  // host copy: internal nodes per depth, max_depth + 2 entries
 
@@ -85,6 +86,7 @@ struct sfmm_ctx {
   DevBuf ring, far, arena, p2p_off, p2p_cnt, counters, red_part, dump;
   DevBuf cf_arena, cf_off, cf_cnt, Tnode;  // shared walk: child frontiers, node coefficients
   DevBuf sym_own, sym_recv;               // walk mode 2: own and received sums per node (FP64)
+  DevBuf wqueue;                          // walk mode 3: nodes in order of readiness
   // near field: chunks of long neighbour lists (extra work items, per-leaf
   // slot base, split leaves, partial sums) and the list entries in use
   DevBuf p2p_extra, p2p_split, p2p_slist, p2p_part;

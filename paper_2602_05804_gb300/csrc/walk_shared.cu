@@ -40,14 +40,33 @@ struct LevelArgs {
   const int* ndepth;
   double* Cown;
   double* Erecv;
+  // queue walk (mode 3): ready nodes in order of readiness (-1: not yet
+  // filled), slots handed out by q_head, filled through q_tail; q_total
+  // walkable nodes in all
+  int* queue;
+  int* q_head;
+  int* q_tail;
+  int q_total;
+  int q_leaves;  // leaves go through the queue too (else one launch afterwards)
 };
+
+// Data a parent's warp wrote earlier in the same launch (the queue walk) is
+// read through L2; written by an earlier launch, a plain load may use L1.
+template <typename T>
+__device__ __forceinline__ T ld_parent(const T* p, bool l2) {
+  return l2 ? __ldcg(p) : *p;
+}
+
+// Bounded wait of the queue walk for a slot to be filled: about a second,
+// then the walk reports an internal error instead of waiting on.
+#define SFMM_QUEUE_SPIN (1 << 24)
 
 
 // T(A) = shift(T(parent)) + own: the parent's coefficients translated to A's
 // centre (Eq. gravmtranslat, lane-parallel through the shift table) plus A's
 // own sums (own_lo: low parts of a double-float own sum, or zeros).  Stored
 // for an internal node; returned in Tn (+ Tl) for a leaf.
-template <int P, bool F32, bool LO>
+template <int P, bool F32, bool LO, bool L2 = false>
 __device__ __forceinline__ void node_coefficients(const LevelArgs& la, int A, int par, bool leafA, const float4& hiA,
                                                   const float4& loA, double cAx, double cAy, double cAz,
                                                   const typename std::conditional<F32, float, double>::type* lev,
@@ -72,10 +91,10 @@ __device__ __forceinline__ void node_coefficients(const LevelArgs& la, int A, in
     for (int b = 0; b < NCS; ++b) {
       const int j = lane + 32 * b;
       if constexpr (F32) {
-        Tn[b] = la.T32[2 * ((size_t)par * la.tstride + j)];
-        Tl[b] = la.T32[2 * ((size_t)par * la.tstride + j) + 1];
+        Tn[b] = ld_parent(&la.T32[2 * ((size_t)par * la.tstride + j)], L2);
+        Tl[b] = ld_parent(&la.T32[2 * ((size_t)par * la.tstride + j) + 1], L2);
       } else {
-        Tn[b] = la.T64[(size_t)par * la.tstride + j];
+        Tn[b] = ld_parent(&la.T64[(size_t)par * la.tstride + j], L2);
       }
       sT[j] = Tn[b];
     }
@@ -179,8 +198,9 @@ __device__ __forceinline__ void leaf_l2p(const LevelArgs& la, int A, double cAx,
   }
 }
 
-template <int P, bool F32, bool SYM>
+template <int P, bool F32, bool SYM, bool QUEUE>
 __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level(const LevelArgs la) {
+  static_assert(!(SYM && QUEUE), "the queue walk runs walk mode 1 only");
   using E = Exp<P>;
   using R = typename std::conditional<F32, float, double>::type;
   constexpr int NC = E::NC;
@@ -209,12 +229,52 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
   unsigned long long st_m2l_p = 0;  // mode 2: replicated count of the partner sides, per lane
   int st_fb = 0;
 
+  // queue walk: an internal node hands its children on once everything they
+  // read (coefficients, opened list) is written
+  constexpr bool queue = QUEUE;
+  auto push_children = [&](int node, int right) {
+    if constexpr (queue) {
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) {
+        const bool pl = la.q_leaves || a.nright[node + 1] >= 0, pr = la.q_leaves || a.nright[right] >= 0;
+        if (pl || pr) {
+          int t = atomicAdd(la.q_tail, (int)pl + (int)pr);
+          if (pl) la.queue[t++] = node + 1;
+          if (pr) la.queue[t] = right;
+        }
+      }
+    }
+  };
   while (true) {
-    int idx = 0;
-    if (lane == 0) idx = atomicAdd(a.leaf_counter, 1);
-    idx = __shfl_sync(SFMM_FULL, idx, 0);
-    if (idx >= la.level_count) break;
-    const int A = la.level_nodes[la.level_begin + idx];
+    int A;
+    if constexpr (queue) {
+      int slot = 0;
+      if (lane == 0) slot = atomicAdd(la.q_head, 1);
+      slot = __shfl_sync(SFMM_FULL, slot, 0);
+      if (slot >= la.q_total) break;
+      int got = -1;
+      if (lane == 0) {
+        for (int it = 0; it < SFMM_QUEUE_SPIN; ++it) {
+          got = *reinterpret_cast<volatile int*>(la.queue + slot);
+          if (got >= 0) break;
+          __nanosleep(64);
+        }
+      }
+      got = __shfl_sync(SFMM_FULL, got, 0);
+      if (got < 0) {
+        if (lane == 0) set_status(a.status, SFMM_ST_INTERNAL);
+        break;
+      }
+      __threadfence();
+      A = got;
+    } else {
+      int idx = 0;
+      if (lane == 0) idx = atomicAdd(a.leaf_counter, 1);
+      idx = __shfl_sync(SFMM_FULL, idx, 0);
+      if (idx >= la.level_count) break;
+      A = la.level_nodes[la.level_begin + idx];
+    }
     const int rA = a.nright[A];
     const bool leafA = rA < 0;
     const int par = la.nparent[A];
@@ -231,8 +291,10 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
     const int* fin = nullptr;
     int nF = 1;
     if (par >= 0) {
-      fin = la.cf_in + la.cf_off[par];
-      nF = la.cf_cnt[par];
+      // written by the parent's warp: read through L2 (the queue walk runs
+      // parent and child in the same launch)
+      fin = la.cf_in + ld_parent(&la.cf_off[par], queue);
+      nF = ld_parent(&la.cf_cnt[par], queue);
     }
     int head = 0, sp = 0, nn = 0;
     bool bad = false;
@@ -248,6 +310,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
           set_status(a.status, SFMM_ST_CHILDLIST);
           la.cf_cnt_out[A] = 0;
         }
+        push_children(A, rA);
         continue;
       }
       cfw = la.cf_out + cfbase;
@@ -278,7 +341,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
     // the inherited list is read through a two-stage pipeline: ids one chunk
     // ahead of the node records, records one chunk ahead of their use, so the
     // loads of a chunk overlap the work on the previous one
-    auto fin_id = [&](int at) -> int { return (at + lane < nF) ? (fin ? fin[at + lane] : A) : -1; };
+    auto fin_id = [&](int at) -> int { return (at + lane < nF) ? (fin ? ld_parent(fin + at + lane, queue) : A) : -1; };
     int pf_s = fin_id(0), pf_s2 = fin_id(32), pf_r = -1;
     float4 pf_hi = make_float4(0.f, 0.f, 0.f, 0.f), pf_lo = pf_hi;
     if (pf_s >= 0) {
@@ -401,6 +464,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
         if (leafA) a.p2p_cnt[la.leaf_index[A]] = 0;
         else la.cf_cnt_out[A] = 0;
       }
+      if (!leafA) push_children(A, rA);
       continue;
     }
     if (lane == 0) {
@@ -425,7 +489,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
 #pragma unroll
       for (int b = 0; b < NCS; ++b) la.Cown[(size_t)A * la.tstride + lane + 32 * b] = (double)lev[b];
     } else {
-      node_coefficients<P, F32, false>(la, A, par, leafA, hiA, loA, cAx, cAy, cAz, lev, nullptr, Tn, Tl, s_T[warp],
+      node_coefficients<P, F32, false, QUEUE>(la, A, par, leafA, hiA, loA, cAx, cAy, cAz, lev, nullptr, Tn, Tl, s_T[warp],
                                        s_h[warp], s_tab, lane);
     }
 
@@ -436,11 +500,11 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level
         la.cf_cnt_out[A] = nn;
       }
       __syncwarp();
+      push_children(A, rA);
       continue;
     }
 
     // leaf: L2P (mode 2: in the finalize pass), then its neighbour list
-    const int fL = a.nfirst[A], nL = a.ncount[A];
     const int leaf = (int)la.leaf_index[A];
     if constexpr (!SYM) leaf_l2p<P, F32>(la, A, cAx, cAy, cAz, Tn, Tl, s_T[warp], lane);
     __syncwarp();
@@ -542,16 +606,42 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_finalize(const LevelArgs la, i
   }
 }
 
+// Queue walk: the system roots fill the first slots.
+__global__ void k_queue_seed(int nsys, const int* __restrict__ sys_root, const int* __restrict__ nright, int q_leaves,
+                             int* __restrict__ queue, int* __restrict__ tail) {
+  for (int i = threadIdx.x; i < nsys; i += blockDim.x) {
+    const int r = sys_root[i];
+    if (q_leaves || nright[r] >= 0) queue[atomicAdd(tail, 1)] = r;
+  }
+}
+
 template <int P, bool F32, bool SYM>
 static int run_levels(sfmm_ctx* c, double theta, int order) {
   using E = Exp<P>;
   constexpr int NCS = (E::NC + 31) / 32;
   const int nn = c->nnodes, nl = c->nleaves;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_level<P, F32, SYM>, WALK_NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_level<P, F32, SYM, false>, WALK_NT, 0);
+  // readiness queue or one launch per depth (walk mode 1): the queue runs
+  // nodes of all depths at once, so it pays when their walk records
+  // (geometry, moments, coefficients, list offsets) stay in L2; per-depth
+  // launches keep one depth's records resident otherwise
   if (per_sm < 1) per_sm = 1;
   const int max_blocks = per_sm * num_sms(c->device);
   const int tstride = NCS * 32;
+  bool queue = false;
+  if (!SYM) {
+    if (c->schedule == 2) queue = true;
+    else if (c->schedule == 0) {
+      int l2 = 0;
+      if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device) != cudaSuccess) l2 = 0;
+      // geometry and right child (36 B), list offset and count (12 B),
+      // moments, coefficients
+      const size_t mom = F32 ? 4 * (size_t)((ncoef(order) + 3) & ~3) : 24 + 8 * (size_t)E::NQ;
+      const size_t per_node = 48 + mom + 8 * (size_t)tstride;
+      queue = (double)per_node * nn <= 0.75 * (double)l2;
+    }
+  }
   int rc;
   for (int attempt = 0; attempt < SFMM_WALK_ATTEMPTS; ++attempt) {
     const int nwarps = max_blocks * WALK_WARPS;
@@ -633,9 +723,40 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     la.ndepth = c->ndepth.as<int>();
     la.Cown = SYM ? c->sym_own.as<double>() : nullptr;
     la.Erecv = SYM ? c->sym_recv.as<double>() : nullptr;
+    la.queue = nullptr;
+    if (queue) {
+      // one launch: a warp takes the next slot of the queue and waits until
+      // the parent of the node there has pushed it; the system roots start it
+      const int nint = c->h_level_off[nlev];
+      la.q_leaves = 1;
+      la.q_total = nint + (la.q_leaves ? nl : 0);
+      if ((rc = c->wqueue.ensure(sizeof(int) * (size_t)(la.q_total + 1)))) return rc;
+      la.queue = c->wqueue.as<int>();
+      la.q_head = reinterpret_cast<int*>(ctr + 14);
+      la.q_tail = reinterpret_cast<int*>(ctr + 15);
+      SFMM_CUDA_TRY(cudaMemsetAsync(la.queue, 0xff, sizeof(int) * (size_t)la.q_total, c->stream));
+      k_queue_seed<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), a.nright, la.q_leaves, la.queue, la.q_tail);
+      la.level = 0;
+      la.level_nodes = nullptr;
+      la.level_begin = 0;
+      la.level_count = la.q_total;
+      if (la.q_total > 0) {
+        // one block per resident slot (the queue needs none resident: a warp
+        // only takes a slot while it runs, and a node's parent always holds
+        // an earlier slot)
+        int q_per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_per_sm, k_walk_level<P, F32, false, true>, WALK_NT, 0);
+        const int q_blocks = std::max(1, std::min(q_per_sm, per_sm)) * num_sms(c->device);
+        k_walk_level<P, F32, false, true><<<q_blocks, WALK_NT, 0, c->stream>>>(la);
+        ++c->nlaunch;
+      }
+      ++c->nlaunch;
+      SFMM_CUDA_TRY(cudaGetLastError());
+      la.queue = nullptr;  // leaves left out of the queue run in one launch below
+    }
     // internal nodes level by level (each needs its parent's opened list and
     // coefficients), then every leaf in one launch, shallowest first
-    for (int k = 0; k <= nlev; ++k) {
+    for (int k = (queue && !la.q_leaves) ? nlev : 0; k <= nlev && !(queue && la.q_leaves); ++k) {
       const bool leaves = (k == nlev);
       la.level = k;
       if (leaves) {
@@ -650,7 +771,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
       if (la.level_count <= 0) continue;
       a.leaf_counter = reinterpret_cast<int*>(ctr + 18 + 2 * k);
       const int blocks = min(max_blocks, (la.level_count + WALK_WARPS - 1) / WALK_WARPS);
-      k_walk_level<P, F32, SYM><<<blocks, WALK_NT, 0, c->stream>>>(la);
+      k_walk_level<P, F32, SYM, false><<<blocks, WALK_NT, 0, c->stream>>>(la);
       ++c->nlaunch;
       if (SYM) {
         k_walk_finalize<P, F32><<<blocks, WALK_NT, 0, c->stream>>>(la, reinterpret_cast<int*>(ctr + 19 + 2 * k));
@@ -661,6 +782,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     int bits = 0;
     if ((rc = sync_status(c, &bits))) return rc;
     if (bits & SFMM_ST_DEPTH) return set_error(c, SFMM_ESTACK, "tree deeper than supported");
+    if (bits & SFMM_ST_INTERNAL) return set_error(c, SFMM_ECUDA, "walk: a queued node was not handed on in time");
     if (bits & (SFMM_ST_RING | SFMM_ST_ARENA | SFMM_ST_CHILDLIST)) {
       if (attempt == SFMM_WALK_ATTEMPTS - 1)
         return set_error(c, SFMM_ECAPACITY, "walk buffers too small after the last regrow");

@@ -24,7 +24,17 @@ def momentum_residual(m, acc):
     return np.linalg.norm(ma.sum(0)) / np.abs(ma).sum()
 
 
-def solver(prec, **opts):
+# walk forms under test: 0 per-leaf replay (Algorithm 1), 1 per-node shared
+# pairs with one launch per depth, 2 one-sided symmetric pairs, 3 per-node
+# shared pairs taken from the readiness queue
+WALKS = {0: {"walk": 0}, 1: {"walk": 1, "schedule": 1}, 2: {"walk": 2}, 3: {"walk": 1, "schedule": 2}}
+
+
+def solver(prec, walk=None, **opts):
+    """A solver of the given precision; `walk` picks one of WALKS (absent:
+    the library's defaults)."""
     from paper_2602_05804_gb300 import sfmm
 
+    if walk is not None:
+        opts = {**WALKS[walk], **opts}
     return sfmm.Solver(0, prec, **opts)

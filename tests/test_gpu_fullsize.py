@@ -64,7 +64,7 @@ def test_full_size_tree_leaves_match_oracle():
 ])
 def test_full_size_sampled_leaves_match_oracle(name, prec, theta):
     pos, m, h, w, t = _system(name)
-    s = solver(prec, walk=1)
+    s = solver(prec)  # the library's defaults, as the benchmark runs it
     s.build(pos, m, h, w["leaf_size"])
     acc, pot = s.gravity(theta, 2)
     acc, pot = acc.cpu().numpy(), pot.cpu().numpy()
@@ -85,3 +85,21 @@ def test_full_size_sampled_leaves_match_oracle(name, prec, theta):
     else:
         assert math.sqrt((e**2).mean()) <= TOL_FP32_RMS, math.sqrt((e**2).mean())
         assert math.sqrt((ep**2).mean()) <= TOL_FP32_RMS, math.sqrt((ep**2).mean())
+
+
+@pytest.mark.parametrize("name", ["plummer_1e6", "clustered_1.6e7"])
+def test_full_size_schedules_agree_bitwise(name):
+    """One launch per depth and the readiness queue give bitwise the same
+    result at full size (the automatic choice takes the queue for the first
+    tree and per-depth launches for the second)."""
+    pos, m, h, w, t = _system(name)
+    out = []
+    for sched in (1, 2):
+        s = solver("fp32", walk=1, schedule=sched)
+        s.build(pos, m, h, w["leaf_size"])
+        acc, pot = s.gravity(w["theta"], 2)
+        out.append((acc.cpu().numpy(), pot.cpu().numpy(), s.stats()["m2l"]))
+        s.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]

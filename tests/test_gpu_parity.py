@@ -121,7 +121,7 @@ PARITY = [("uniform", 6000, 10, 0.5, 2), ("plummer", 8001, 16, 0.5, 2), ("plumme
           ("plummer", 2500, 1, 0.5, 2), ("uniform", 1000, 64, 0.9, 2)]
 
 
-@pytest.mark.parametrize("walk", [0, 1, 2])
+@pytest.mark.parametrize("walk", [0, 1, 2, 3])
 @pytest.mark.parametrize("kind,n,ls,theta,p", PARITY)
 def test_fp64_form_matches_oracle(kind, n, ls, theta, p, walk):
     pos, m, h = _set(kind, n, 17)
@@ -141,7 +141,7 @@ def test_fp64_form_matches_oracle(kind, n, ls, theta, p, walk):
     assert abs(st["W"] - 0.5 * (m * pot_o).sum()) <= 1e-10 * abs(st["W"])
 
 
-@pytest.mark.parametrize("walk", [0, 1, 2])
+@pytest.mark.parametrize("walk", [0, 1, 2, 3])
 @pytest.mark.parametrize("kind,n,ls,theta,p", PARITY)
 def test_fp32_form_matches_oracle(kind, n, ls, theta, p, walk):
     pos, m, h = _set(kind, n, 17)
@@ -289,17 +289,18 @@ def test_shared_walk_equals_replay(prec, tol):
     assert pot_rel(p1, p0).max() <= tol
 
 
-def test_shared_walk_capacity_regrow():
+@pytest.mark.parametrize("walk", [1, 3])
+def test_shared_walk_capacity_regrow(walk):
     pos, m, h = workloads.plummer(6000, 12)
     acc_o, pot_o, _ = oracle.sfmm(pos, m, h, theta=0.3, p=2, leaf_size=16)
-    s = solver("fp64", walk=1, ring_capacity=256, list_capacity=64)
+    s = solver("fp64", walk=walk, ring_capacity=256, list_capacity=64)
     s.build(pos, m, h, 16)
     acc, pot = s.gravity(0.3, 2)
     assert acc_rel(acc.cpu().numpy(), acc_o).max() <= TOL_FP64
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("walk", [0, 1])
+@pytest.mark.parametrize("walk", [0, 1, 3])
 def test_long_lists_split_into_chunks(prec, walk):
     """Neighbour lists longer than one chunk are evaluated as several work
     items and recombined in chunk order: the result still matches the
@@ -348,7 +349,7 @@ def test_one_sided_symmetric_pairs_equal_shared_walk(prec, tol):
         assert momentum_residual(m, a2) <= TOL_MOM_FP64
 
 
-@pytest.mark.parametrize("walk", [0, 1, 2])
+@pytest.mark.parametrize("walk", [0, 1, 2, 3])
 def test_small_theta_grows_buffers_and_matches_oracle(walk):
     """theta = 0.1: almost every pair is done pairwise, lists are long and
     several work buffers must grow (regrow and retry inside the call)."""
@@ -361,3 +362,42 @@ def test_small_theta_grows_buffers_and_matches_oracle(walk):
     assert st["p2p_pairs"] == st_o["p2p_pairs"] and st["m2l"] == st_o["m2l"]
     e = acc_rel(acc.cpu().numpy(), acc_o)
     assert math.sqrt((e**2).mean()) <= TOL_FP32_RMS
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind,n,theta", [("plummer", 40000, 0.5), ("binary", 30000, 0.3)])
+def test_queue_walk_equals_level_walk(prec, kind, n, theta):
+    """The readiness queue runs the per-node shared walk as one launch over
+    nodes whose parents are done, instead of one launch per depth: every
+    node does the same arithmetic on the same inherited list, so the
+    results are bitwise the same, and so are those of the automatic
+    choice."""
+    pos, m, h = _set(kind, n, 47)
+    out = []
+    for walk in (1, 3):
+        s = solver(prec, walk=walk)
+        s.build(pos, m, h, 16)
+        acc, pot = s.gravity(theta, 2)
+        out.append((acc.cpu().numpy(), pot.cpu().numpy(), s.stats()))
+    s = solver(prec)  # automatic schedule
+    s.build(pos, m, h, 16)
+    acc, pot = s.gravity(theta, 2)
+    out.append((acc.cpu().numpy(), pot.cpu().numpy(), s.stats()))
+    (a1, p1, s1) = out[0]
+    for a3, p3, s3 in out[1:]:
+        for k in ("m2l", "m2l_unique", "p2p_pairs", "p2p_leaves", "mac_fallbacks"):
+            assert s1[k] == s3[k], k
+        np.testing.assert_array_equal(a3, a1)
+        np.testing.assert_array_equal(p3, p1)
+
+
+def test_schedule_option_is_checked():
+    from paper_2602_05804_gb300 import sfmm
+
+    s = solver("fp32")
+    for bad in (-1, 3, 0.5):
+        with pytest.raises(sfmm.SFMMError) as e:
+            s.set_option("schedule", bad)
+        assert e.value.code == sfmm.SFMM_EINVAL
+    with pytest.raises(sfmm.SFMMError):
+        s.set_option("walk", 3)
