@@ -60,32 +60,28 @@ struct P2PArgs {
   unsigned long long* pair_counter;  // pair evaluations (statistics)
 };
 
-// M4 softening kernel of one particle (compact support 2h), evaluated with
-// coefficients selected per piece: g = phi'(r)/r and phi, -> 1/r^3 and
-// -1/r outside 2h.  q = r/h, hinv = 1/h, ri = 1/r.
+// M4 softening kernel of one particle (compact support 2h): g = phi'(r)/r
+// and phi, -> 1/r^3 and -1/r outside 2h.  Both pieces' polynomials are
+// evaluated in full and the piece chosen afterwards (fewer instructions than
+// choosing coefficients).  q = r/h, hinv = 1/h, ri = 1/r.
 template <typename R>
 __device__ __forceinline__ void m4_kernel(R q, R hinv, R ri, R& g, R& phi) {
-  const bool in1 = q < R(1);
-  const bool out2 = q >= R(2);
-  // g h^3 = c0 + c1 q + c2 q^2 + c3 q^3 (- 1/(15 q^3) for 1 <= q < 2)
-  const R c0 = in1 ? R(4.0 / 3.0) : R(8.0 / 3.0);
-  const R c1 = in1 ? R(0) : R(-3);
-  const R c2 = in1 ? R(-1.2) : R(1.2);
-  const R c3 = in1 ? R(0.5) : R(-1.0 / 6.0);
-  // phi h = d0 + d2 q^2 + d3 q^3 + d4 q^4 + d5 q^5 (+ 1/(15 q) for 1 <= q < 2)
-  const R d0 = in1 ? R(-1.4) : R(-1.6);
-  const R d2 = in1 ? R(2.0 / 3.0) : R(4.0 / 3.0);
-  const R d3 = in1 ? R(0) : R(-1);
-  const R d4 = in1 ? R(-0.3) : R(0.3);
-  const R d5 = in1 ? R(0.1) : R(-1.0 / 30.0);
   const R hinv3 = hinv * hinv * hinv;
   const R ri3 = ri * ri * ri;
-  const R gp = hinv3 * fma(q, fma(q, fma(q, c3, c2), c1), c0);
-  const R pp = hinv * fma(q * q, fma(q, fma(q, fma(q, d5, d4), d3), d2), d0);
-  const R gm = in1 ? gp : fma(R(-1.0 / 15.0), ri3, gp);
-  const R pm = in1 ? pp : fma(R(1.0 / 15.0), ri, pp);
-  g = out2 ? ri3 : gm;
-  phi = out2 ? -ri : pm;
+  const R q2 = q * q;
+  // q < 1: g h^3 = 4/3 - 6/5 q^2 + 1/2 q^3, phi h = -7/5 + 2/3 q^2 - 3/10 q^4 + 1/10 q^5
+  const R gA = fma(q2, fma(R(0.5), q, R(-1.2)), R(4.0 / 3.0));
+  const R pA = fma(q2, fma(q2, fma(R(0.1), q, R(-0.3)), R(2.0 / 3.0)), R(-1.4));
+  // 1 <= q < 2: g h^3 = 8/3 - 3 q + 6/5 q^2 - 1/6 q^3 - 1/(15 q^3),
+  //             phi h = -8/5 + 4/3 q^2 - q^3 + 3/10 q^4 - 1/30 q^5 + 1/(15 q)
+  const R gB = fma(q, fma(q, fma(R(-1.0 / 6.0), q, R(1.2)), R(-3)), R(8.0 / 3.0));
+  const R pB = fma(q2, fma(q, fma(q, fma(R(-1.0 / 30.0), q, R(0.3)), R(-1)), R(4.0 / 3.0)), R(-1.6));
+  const bool in1 = q < R(1);
+  const R gk = fma(hinv3, in1 ? gA : gB, in1 ? R(0) : R(-1.0 / 15.0) * ri3);
+  const R pk = fma(hinv, in1 ? pA : pB, in1 ? R(0) : R(1.0 / 15.0) * ri);
+  const bool out2 = q >= R(2);
+  g = out2 ? ri3 : gk;
+  phi = out2 ? -ri : pk;
 }
 
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
@@ -191,8 +187,10 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
   __shared__ V s_far[NW][SB];
   __shared__ V s_near[NW][SB];
   __shared__ V2 s_nhh[NW][SB];
-  __shared__ int s_nidx[NW][SB];
-  __shared__ R s_red[NW][4][32];
+  __shared__ short s_nloc[NW][SB];  // candidate's index in the target leaf, -1 outside it
+  __shared__ unsigned short s_sq[NW][F32 ? 1 : 64];  // FP64 softened pairs: candidate slot << 5 | owner lane
+  // phase sums at the end of a leaf; the FP64 softened-pair results during its loop
+  __shared__ __align__(4 * sizeof(R)) R s_red[NW][4][32];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
@@ -326,7 +324,7 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
           const int q = nnear + __popc(bn & lt);
           s_near[warp][q] = v;
           s_nhh[warp][q] = hh;
-          s_nidx[warp][q] = i;
+          s_nloc[warp][q] = (short)((i >= fL && i < fL + nL) ? i - fL : -1);
         } else if (valid) {
           s_far[warp][nfar + __popc(bf & lt)] = v;
         }
@@ -354,14 +352,110 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
           pair_far<R>(xi0, yi0, zi0, s0, ax0, ay0, az0, pt0);
           if (nL > 32) pair_far<R>(xi1, yi1, zi1, s0, ax1, ay1, az1, pt1);
         }
-        // candidates inside some kernel of the leaf
-        for (int jn = ph; jn < nnear; jn += nph) {
-          const V s0 = s_near[warp][jn];
-          const V2 hh = s_nhh[warp][jn];
-          const int ij = s_nidx[warp][jn];
-          pair_cand<R>(xi0, yi0, zi0, hinvi0, h2i0, ij == fL + t0, s0, hh, ax0, ay0, az0, pt0);
-          if (nL > 32) pair_cand<R>(xi1, yi1, zi1, hinvi1, h2i1, ij == fL + t1, s0, hh, ax1, ay1, az1, pt1);
+        // candidates inside some kernel of the leaf, softened in place
+        if (F32 || nL > 32) {
+          for (int jn = ph; jn < nnear; jn += nph) {
+            const V s0 = s_near[warp][jn];
+            const V2 hh = s_nhh[warp][jn];
+            const int loc = s_nloc[warp][jn];
+            pair_cand<R>(xi0, yi0, zi0, hinvi0, h2i0, loc == t0, s0, hh, ax0, ay0, az0, pt0);
+            if (nL > 32) pair_cand<R>(xi1, yi1, zi1, hinvi1, h2i1, loc == t1, s0, hh, ax1, ay1, az1, pt1);
+          }
         }
+      }
+      if (!F32 && nL <= 32 && nnear > 0) {
+        // FP64 form, up to 32 targets: the unsoftened candidates in place; a
+        // pair inside a kernel goes to the warp's queue, and every 32 queued
+        // pairs are evaluated one per lane (target records by shuffle from the
+        // lane holding them) and handed back to their owner lanes, which add
+        // them in queue order.  The FP64 pipe costs the same per warp
+        // instruction whatever the active lanes, so the softened branch pays
+        // only once per 32 pairs; in the FP32 form the in-place branch is
+        // faster (measured)
+        V* const s_soft = reinterpret_cast<V*>(&s_red[warp][0][0]);
+        auto soft_batch = [&](int cnt, unsigned mine) {
+          __syncwarp();
+          const int ent = (lane < cnt) ? (int)s_sq[warp][lane] : 0;
+          const int o = ent & 31, jn = ent >> 5;
+          const int t = o - (o / ntl) * ntl;  // the owner's target, held by lane t
+          const R tx = __shfl_sync(SFMM_FULL, xi0, t), ty = __shfl_sync(SFMM_FULL, yi0, t),
+                  tz = __shfl_sync(SFMM_FULL, zi0, t), thinv = __shfl_sync(SFMM_FULL, hinvi0, t);
+          V c;
+          c.x = c.y = c.z = c.w = R(0);
+          if (lane < cnt) {
+            const V s0 = s_near[warp][jn];
+            const V2 hh = s_nhh[warp][jn];
+            const R dx = tx - s0.x, dy = ty - s0.y, dz = tz - s0.z;
+            const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            const R ri = (r2 > R(0)) ? rsq(r2) : R(0);
+            const R r = r2 * ri;
+            R gi, pi, gj, pj;
+            m4_kernel<R>(r * thinv, thinv, ri, gi, pi);
+            m4_kernel<R>(r * hh.x, hh.x, ri, gj, pj);
+            const R mg = s0.w * (R(0.5) * (gi + gj));
+            c.x = -mg * dx;
+            c.y = -mg * dy;
+            c.z = -mg * dz;
+            c.w = s0.w * (R(0.5) * (pi + pj));
+          }
+          s_soft[lane] = c;
+          __syncwarp();
+          while (mine) {
+            const int e = __ffs(mine) - 1;
+            mine &= mine - 1;
+            const V v = s_soft[e];
+            ax0 += v.x;
+            ay0 += v.y;
+            az0 += v.z;
+            pt0 += v.w;
+          }
+          __syncwarp();
+        };
+        int qn = 0;
+        unsigned m0 = 0u, m1 = 0u;  // queue positions [0, 32) and [32, 64) this lane owns
+        for (int base = 0; base < nnear; base += nph) {
+          const int jn = base + ph;
+          bool ins = false;
+          if (lane_on && jn < nnear) {
+            const V s0 = s_near[warp][jn];
+            const V2 hh = s_nhh[warp][jn];
+            const bool self = s_nloc[warp][jn] == t0;
+            const R dx = xi0 - s0.x, dy = yi0 - s0.y, dz = zi0 - s0.z;
+            const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            ins = !self && r2 < fmax(h2i0, hh.y);
+            // outside both kernels: unsoftened (r >= 2 h > 0); else nothing here
+            const bool skip = self || ins;
+            const R ri = rsq(skip ? R(1) : r2);
+            const R mr = (skip ? R(0) : s0.w) * ri;
+            const R mr3 = mr * (ri * ri);
+            ax0 = fma(-mr3, dx, ax0);
+            ay0 = fma(-mr3, dy, ay0);
+            az0 = fma(-mr3, dz, az0);
+            pt0 -= mr;
+          }
+          const unsigned b = __ballot_sync(SFMM_FULL, ins);
+          if (b) {
+            if (ins) {
+              const int pos = qn + __popc(b & lt);
+              s_sq[warp][pos] = (unsigned short)((jn << 5) | lane);
+              if (pos < 32) m0 |= 1u << pos;
+              else m1 |= 1u << (pos - 32);
+            }
+            qn += __popc(b);
+            if (qn >= 32) {
+              soft_batch(32, m0);
+              // carry the queued pairs beyond the batch to the front
+              const int rest = qn - 32;
+              const unsigned short carry = (lane < rest) ? s_sq[warp][32 + lane] : (unsigned short)0;
+              __syncwarp();
+              if (lane < rest) s_sq[warp][lane] = carry;
+              qn = rest;
+              m0 = m1;
+              m1 = 0u;
+            }
+          }
+        }
+        if (qn > 0) soft_batch(qn, m0);
       }
       __syncwarp();
       nfar = 0;
