@@ -106,6 +106,22 @@ __device__ __forceinline__ void pair_far(R xi, R yi, R zi, const typename Vec4<R
   pt -= mr;
 }
 
+// Two unsoftened pairs of one target in the packed FP32 instructions (two
+// lanes of FP32 per register pair, one issue slot): sources given negated,
+// (-x, -y, -z, -m), so that every operation rounds exactly as pair_far's.
+__device__ __forceinline__ void pair_far2(float2 xi, float2 yi, float2 zi, float2 nx, float2 ny, float2 nz,
+                                          float2 nm, float2& ax, float2& ay, float2& az, float2& pt) {
+  const float2 dx = __fadd2_rn(xi, nx), dy = __fadd2_rn(yi, ny), dz = __fadd2_rn(zi, nz);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+  const float2 mr = __fmul2_rn(nm, ri);                     // -m / r
+  const float2 mr3 = __fmul2_rn(mr, __fmul2_rn(ri, ri));    // -m / r^3
+  ax = __ffma2_rn(mr3, dx, ax);
+  ay = __ffma2_rn(mr3, dy, ay);
+  az = __ffma2_rn(mr3, dz, az);
+  pt = __fadd2_rn(pt, mr);
+}
+
 // Candidate pair: softened when r < 2 max(h_i, h_j) (mean of both kernels),
 // unsoftened otherwise; the self pair contributes nothing.
 template <typename R>
@@ -326,7 +342,19 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
           s_nhh[warp][q] = hh;
           s_nloc[warp][q] = (short)((i >= fL && i < fL + nL) ? i - fL : -1);
         } else if (valid) {
-          s_far[warp][nfar + __popc(bf & lt)] = v;
+          const int q = nfar + __popc(bf & lt);
+          if constexpr (F32) {
+            // pairs of sources, negated: {x0, x1, y0, y1}, {z0, z1, m0, m1}
+            float* const fxy = reinterpret_cast<float*>(&s_far[warp][q >> 1]);
+            float* const fzm = reinterpret_cast<float*>(&s_far[warp][SB / 2 + (q >> 1)]);
+            const int hb = q & 1;
+            fxy[hb] = -v.x;
+            fxy[2 + hb] = -v.y;
+            fzm[hb] = -v.z;
+            fzm[2 + hb] = -v.w;
+          } else {
+            s_far[warp][q] = v;
+          }
         }
         nnear += __popc(bn);
         nfar += __popc(bf);
@@ -335,8 +363,43 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
       const bool last = !((pdone < tot) || (e < cnt));
       if (!(nfar > SB - 32 || nnear > SB - 32 || last)) continue;
       __syncwarp();
+      if constexpr (F32) {
+        if (nfar & 1) {
+          // odd count: the last pair's second source repeats the first with
+          // no mass (outside every kernel, so r > 0)
+          if (lane == 0) {
+            float* const fxy = reinterpret_cast<float*>(&s_far[warp][nfar >> 1]);
+            float* const fzm = reinterpret_cast<float*>(&s_far[warp][SB / 2 + (nfar >> 1)]);
+            fxy[1] = fxy[0];
+            fxy[3] = fxy[2];
+            fzm[1] = fzm[0];
+            fzm[3] = 0.0f;
+          }
+          __syncwarp();
+        }
+      }
       if (lane_on) {
         // unsoftened sources
+        if constexpr (F32) {
+          // one pass per target slot (the second only for leaves of more
+          // than 32 particles)
+          const int np = (nfar + 1) >> 1;
+          auto far_pass = [&](float xi, float yi, float zi, float& ax, float& ay, float& az, float& pt) {
+            const float2 x2 = make_float2(xi, xi), y2 = make_float2(yi, yi), z2 = make_float2(zi, zi);
+            float2 fx = make_float2(0.0f, 0.0f), fy = fx, fz = fx, fp = fx;
+            for (int pj = ph; pj < np; pj += nph) {
+              const float4 a = s_far[warp][pj], b = s_far[warp][SB / 2 + pj];
+              pair_far2(x2, y2, z2, make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                        make_float2(b.z, b.w), fx, fy, fz, fp);
+            }
+            ax += fx.x + fx.y;
+            ay += fy.x + fy.y;
+            az += fz.x + fz.y;
+            pt += fp.x + fp.y;
+          };
+          far_pass(xi0, yi0, zi0, ax0, ay0, az0, pt0);
+          if (nL > 32) far_pass(xi1, yi1, zi1, ax1, ay1, az1, pt1);
+        } else {
         int j = ph;
         for (; j + nph < nfar; j += 2 * nph) {
           const V s0 = s_far[warp][j], s1 = s_far[warp][j + nph];
@@ -351,6 +414,7 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
           const V s0 = s_far[warp][j];
           pair_far<R>(xi0, yi0, zi0, s0, ax0, ay0, az0, pt0);
           if (nL > 32) pair_far<R>(xi1, yi1, zi1, s0, ax1, ay1, az1, pt1);
+        }
         }
         // candidates inside some kernel of the leaf, softened in place
         if (F32 || nL > 32) {
