@@ -477,7 +477,7 @@ int sfmm_moments_export(sfmm_ctx* c, int order, double* Q, int32_t* mi) {
   if (order < 0 || order > SFMM_PMAX) return SFMM_EINVAL;
   DeviceGuard g(c->device);
   int rc;
-  if (c->moments_order != order && (rc = compute_moments(c, order))) return rc;
+  if ((c->moments_order != order || !c->moments_fp64) && (rc = compute_moments(c, order))) return rc;
   const int nq = ncoef(order);
   SFMM_CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (Q) SFMM_CUDA_TRY(cudaMemcpy(Q, c->Qd.p, sizeof(double) * (size_t)c->nnodes * nq, cudaMemcpyDeviceToHost));

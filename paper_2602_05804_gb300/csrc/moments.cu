@@ -111,7 +111,10 @@ int compute_moments(sfmm_ctx* c, int order) {
     case 4: rc = moments_p<4>(c); break;
     default: return SFMM_EINVAL;
   }
-  if (rc == SFMM_OK) c->moments_order = order;
+  if (rc == SFMM_OK) {
+    c->moments_order = order;
+    c->moments_fp64 = true;
+  }
   return rc;
 }
 

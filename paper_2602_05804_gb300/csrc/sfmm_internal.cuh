@@ -45,6 +45,7 @@ struct sfmm_ctx {
   DevBuf sys_off, sys_lsz, psys, sys_root, wparent, sys_leaf_off, sys_sums;
   int32_t nnodes = 0, nleaves = 0;
   int moments_order = -1;  // order of the cached moments (-1: none)
+  bool moments_fp64 = false;  // the cached moments include the FP64 rows (else FP32 only)
   int pref_order = 2;      // order the build computes moments for (the last gravity call's)
   int walk_mode = 1;        // 1: per-node shared pairs (default), 0: per-leaf replay (Algorithm 1),
                             // 2: per-node pairs, each evaluated once for both sides

@@ -5,6 +5,8 @@
 #include <cfloat>
 
 #include "mom_ops.cuh"
+#include <type_traits>
+
 #include "sfmm_internal.cuh"
 
 namespace sfmm {
@@ -594,11 +596,40 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// A node's moments: FP64 (the FP64 form; FP32 rows rounded from them) or
+// FP32 only (the FP32 form, whose walk reads nothing else; the monopole is
+// the FP64 mass, rounded once).
+template <int NQ, typename QT>
+__device__ __forceinline__ void store_moments(int v, QT (&q)[NQ], double M, double* __restrict__ Qd,
+                                              float* __restrict__ Qf) {
+  constexpr int NQS = (NQ + 3) & ~3;
+  if constexpr (std::is_same<QT, double>::value) {
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) Qd[(int64_t)v * NQ + k] = q[k];
+  } else {
+    q[0] = __double2float_rn(M);
+  }
+#pragma unroll
+  for (int k = 0; k < NQS; ++k) Qf[(int64_t)v * NQS + k] = (k < NQ) ? (float)q[k] : 0.0f;
+}
+
+// A child's moments, read through L2 (written by another thread of the same
+// launch in the climb).
+template <int NQ, typename QT>
+__device__ __forceinline__ void load_moments(int u, QT (&q)[NQ], const double* Qd, const float* Qf) {
+  constexpr int NQS = (NQ + 3) & ~3;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    if constexpr (std::is_same<QT, double>::value) q[k] = __ldcg(&Qd[(int64_t)u * NQ + k]);
+    else q[k] = __ldcg(&Qf[(int64_t)u * NQS + k]);
+  }
+}
+
 // One thread per leaf (the FP64 sums of a leaf are short; warp reductions in
 // FP64 would cost more than the sums themselves).
 // P >= 0: also the leaf's scaled moments of order P about its centre of mass
 // (P2M, Eq. massmom) in FP64 and their FP32 copy; P < 0: geometry only.
-template <int P>
+template <int P, typename QT>
 __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
                             const int* __restrict__ ncount, const double* __restrict__ px,
                             const double* __restrict__ py, const double* __restrict__ pz,
@@ -644,28 +675,24 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
   nlu[v] = 1;
   if constexpr (P >= 0) {
     constexpr int NQ = MomOps<P>::NQ;
-    double acc[NQ];
+    QT acc[NQ];
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NQ; ++k) acc[k] = QT(0);
     for (int i = f; i < f + cnt; ++i) {
-      double mono[NQ];
-      MomOps<P>::mono(px[i] - cx, py[i] - cy, pz[i] - cz, mono);
-      const double m = pm[i];
+      QT mono[NQ];
+      MomOps<P>::mono((QT)(px[i] - cx), (QT)(py[i] - cy), (QT)(pz[i] - cz), mono);
+      const QT m = (QT)pm[i];
 #pragma unroll
       for (int k = 0; k < NQ; ++k) acc[k] = fma(m, mono[k], acc[k]);
     }
-#pragma unroll
-    for (int k = 0; k < NQ; ++k) Qd[(int64_t)v * NQ + k] = acc[k];
-    constexpr int NQS = (NQ + 3) & ~3;  // == nqs
-#pragma unroll
-    for (int k = 0; k < NQS; ++k) Qf[(int64_t)v * NQS + k] = (k < NQ) ? __double2float_rn(acc[k]) : 0.0f;
+    store_moments<NQ>(v, acc, M, Qd, Qf);
   }
 }
 
 // Bottom-up: the second child to finish computes its parent (P >= 0: also
 // the parent's moments, both children's translated to its centre, Eq.
 // massmomtrans).
-template <int P>
+template <int P, typename QT>
 __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nparent,
                          const int* __restrict__ nright, double* ncx, double* ncy, double* ncz, double* nmass,
                          double* nhmax, int* nlu, int* flags, double* extv, int* exti, double* Qd, float* Qf,
@@ -690,24 +717,19 @@ __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const i
     ncz[v] = cz;
     if constexpr (P >= 0) {
       constexpr int NQ = MomOps<P>::NQ;
-      double qp[NQ];
+      QT qp[NQ];
 #pragma unroll
-      for (int k = 0; k < NQ; ++k) qp[k] = 0.0;
+      for (int k = 0; k < NQ; ++k) qp[k] = QT(0);
       const int kids[2] = {L, R};
       const double kx[2] = {cLx, cRx}, ky[2] = {cLy, cRy}, kz[2] = {cLz, cRz};
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        double g[NQ], qc[NQ];
-        MomOps<P>::mono(kx[c] - cx, ky[c] - cy, kz[c] - cz, g);
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) qc[k] = __ldcg(&Qd[(int64_t)kids[c] * NQ + k]);
+        QT g[NQ], qc[NQ];
+        MomOps<P>::mono((QT)(kx[c] - cx), (QT)(ky[c] - cy), (QT)(kz[c] - cz), g);
+        load_moments<NQ>(kids[c], qc, Qd, Qf);
         MomOps<P>::m2m(g, qc, qp);
       }
-#pragma unroll
-      for (int k = 0; k < NQ; ++k) Qd[(int64_t)v * NQ + k] = qp[k];
-      constexpr int NQS = (NQ + 3) & ~3;  // == nqs
-#pragma unroll
-      for (int k = 0; k < NQS; ++k) Qf[(int64_t)v * NQS + k] = (k < NQ) ? __double2float_rn(qp[k]) : 0.0f;
+      store_moments<NQ>(v, qp, M, Qd, Qf);
     }
     nmass[v] = M;
     nhmax[v] = fmax(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
@@ -727,7 +749,7 @@ __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const i
 // the level combines its two finished children -- mass, centre of mass,
 // h_max, leaves below, axis-extreme particles and (P >= 0) the moments
 // translated to the new centre (Eq. massmomtrans).
-template <int P>
+template <int P, typename QT>
 __device__ __forceinline__ void upward_node(int v, const int* __restrict__ nright, double* __restrict__ ncx,
                                             double* __restrict__ ncy, double* __restrict__ ncz,
                                             double* __restrict__ nmass, double* __restrict__ nhmax,
@@ -756,35 +778,30 @@ __device__ __forceinline__ void upward_node(int v, const int* __restrict__ nrigh
   }
   if constexpr (P >= 0) {
     constexpr int NQ = MomOps<P>::NQ;
-    double qp[NQ];
+    QT qp[NQ];
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) qp[k] = 0.0;
+    for (int k = 0; k < NQ; ++k) qp[k] = QT(0);
     const int kids[2] = {L, R};
     const double kx[2] = {cLx, cRx}, ky[2] = {cLy, cRy}, kz[2] = {cLz, cRz};
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      double g[NQ], qc[NQ];
-      MomOps<P>::mono(kx[c] - cx, ky[c] - cy, kz[c] - cz, g);
-#pragma unroll
-      for (int k = 0; k < NQ; ++k) qc[k] = Qd[(int64_t)kids[c] * NQ + k];
+      QT g[NQ], qc[NQ];
+      MomOps<P>::mono((QT)(kx[c] - cx), (QT)(ky[c] - cy), (QT)(kz[c] - cz), g);
+      load_moments<NQ>(kids[c], qc, Qd, Qf);
       MomOps<P>::m2m(g, qc, qp);
     }
-#pragma unroll
-    for (int k = 0; k < NQ; ++k) Qd[(int64_t)v * NQ + k] = qp[k];
-    constexpr int NQS = (NQ + 3) & ~3;
-#pragma unroll
-    for (int k = 0; k < NQS; ++k) Qf[(int64_t)v * NQS + k] = (k < NQ) ? __double2float_rn(qp[k]) : 0.0f;
+    store_moments<NQ>(v, qp, M, Qd, Qf);
   }
 }
 
-template <int P>
+template <int P, typename QT>
 __global__ void k_upward_level(int count, const int* __restrict__ nodes, const int* __restrict__ nright,
                                double* __restrict__ ncx, double* __restrict__ ncy, double* __restrict__ ncz,
                                double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ nlu,
                                double* __restrict__ extv, int* __restrict__ exti, double* __restrict__ Qd,
                                float* __restrict__ Qf) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < count) upward_node<P>(nodes[t], nright, ncx, ncy, ncz, nmass, nhmax, nlu, extv, exti, Qd, Qf);
+  if (t < count) upward_node<P, QT>(nodes[t], nright, ncx, ncy, ncz, nmass, nhmax, nlu, extv, exti, Qd, Qf);
 }
 
 
@@ -1023,11 +1040,11 @@ int compute_depth(sfmm_ctx* c) {
 // GB300 the climb wins below about half a million leaves.
 #define UP_LEVEL_MIN_LEAVES (1 << 19)
 
-template <int P>
-static int geom_upward(sfmm_ctx* c, int nqs) {
+template <int P, typename QT>
+static int geom_upward_t(sfmm_ctx* c, int nqs) {
   cudaStream_t st = c->stream;
   const int nl = c->nleaves;
-  k_leaf_geom<P><<<nblk(nl, 128), 128, 0, st>>>(
+  k_leaf_geom<P, QT><<<nblk(nl, 128), 128, 0, st>>>(
       nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
       c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
       c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),
@@ -1038,7 +1055,7 @@ static int geom_upward(sfmm_ctx* c, int nqs) {
     for (int d = c->max_depth; d >= 0; --d) {
       const int lo = c->h_level_off[d], cnt = c->h_level_off[d + 1] - lo;
       if (cnt <= 0) continue;
-      k_upward_level<P><<<nblk(cnt, 128), 128, 0, st>>>(
+      k_upward_level<P, QT><<<nblk(cnt, 128), 128, 0, st>>>(
           cnt, c->level_nodes.as<int>() + lo, c->nright.as<int>(), c->ncx.as<double>(), c->ncy.as<double>(),
           c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
           c->n_extv.as<double>(), c->n_exti.as<int>(), c->Qd.as<double>(), c->Qf.as<float>());
@@ -1047,7 +1064,7 @@ static int geom_upward(sfmm_ctx* c, int nqs) {
   } else {
     // fewer leaves: one launch, the second child to finish climbs on
     SFMM_CUDA_TRY(cudaMemsetAsync(c->flags.p, 0, sizeof(int) * (size_t)c->nnodes, st));
-    k_upward<P><<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
+    k_upward<P, QT><<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
                                                c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
                                                c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
                                                c->flags.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(),
@@ -1056,6 +1073,13 @@ static int geom_upward(sfmm_ctx* c, int nqs) {
   }
   SFMM_CUDA_TRY(cudaGetLastError());
   return SFMM_OK;
+}
+
+// Moments in the context's form: FP32 for the FP32 form, FP64 otherwise.
+template <int P>
+static int geom_upward(sfmm_ctx* c, int nqs) {
+  if (P >= 0 && c->precision == SFMM_FP32) return geom_upward_t<P, float>(c, nqs);
+  return geom_upward_t<P, double>(c, nqs);
 }
 
 // Depth, the per-depth lists of walkable internal nodes (the upward pass and
@@ -1315,6 +1339,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   c->moments_order = P;
+  c->moments_fp64 = (P >= 0 && c->precision != SFMM_FP32);
   if (c->keys_a.p != (void*)ka_final) {
     // keep the sorted keys in keys_a for export (even number of passes: no-op)
     SFMM_CUDA_TRY(cudaMemcpyAsync(c->keys_a.p, ka_final, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
