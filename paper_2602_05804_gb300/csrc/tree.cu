@@ -596,6 +596,20 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Order-preserving integer key of a finite double (signed comparison of keys
+// orders the values; -0 sorts just below +0): the axis-extreme comparisons
+// run on the integer pipe instead of GB300's narrow FP64 pipe.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+// The larger of two non-negative doubles, compared as bit patterns (exact).
+__device__ __forceinline__ double dmax_pos(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
+}
+
 // A node's moments: FP64 (the FP64 form; FP32 rows rounded from them) or
 // FP32 only (the FP32 form, whose walk reads nothing else; the monopole is
 // the FP64 mass, rounded once).
@@ -645,6 +659,9 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
   double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, hm = 0.0;
   // extreme particles per axis (min x, y, z, max x, y, z; first one on ties)
   double ev[6] = {px[f], py[f], pz[f], px[f], py[f], pz[f]};
+  long long ek[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) ek[c] = dkey(ev[c]);
   int ei[6] = {f, f, f, f, f, f};
   for (int i = f; i < f + cnt; ++i) {
     const double m = pm[i];
@@ -652,13 +669,14 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
     sx = dadd(sx, dmul(m, px[i]));
     sy = dadd(sy, dmul(m, py[i]));
     sz = dadd(sz, dmul(m, pz[i]));
-    hm = fmax(hm, ph[i]);
+    hm = dmax_pos(hm, ph[i]);
     pnode[i] = v;
     const double xc[3] = {px[i], py[i], pz[i]};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      if (xc[c] < ev[c]) { ev[c] = xc[c]; ei[c] = i; }
-      if (xc[c] > ev[3 + c]) { ev[3 + c] = xc[c]; ei[3 + c] = i; }
+      const long long k = dkey(xc[c]);
+      if (k < ek[c]) { ek[c] = k; ev[c] = xc[c]; ei[c] = i; }
+      if (k > ek[3 + c]) { ek[3 + c] = k; ev[3 + c] = xc[c]; ei[3 + c] = i; }
     }
   }
 #pragma unroll
@@ -709,9 +727,12 @@ __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const i
     double M = dadd(mL, mR);
     const double cLx = __ldcg(&ncx[L]), cLy = __ldcg(&ncy[L]), cLz = __ldcg(&ncz[L]);
     const double cRx = __ldcg(&ncx[R]), cRy = __ldcg(&ncy[R]), cRz = __ldcg(&ncz[R]);
-    const double cx = __ddiv_rn(dadd(dmul(mL, cLx), dmul(mR, cRx)), M);
-    const double cy = __ddiv_rn(dadd(dmul(mL, cLy), dmul(mR, cRy)), M);
-    const double cz = __ddiv_rn(dadd(dmul(mL, cLz), dmul(mR, cRz)), M);
+    // one division per node (GB300's FP64 pipe is narrow): the centre is
+    // within rounding of the quotient, like the oracle's own sum
+    const double iM = 1.0 / M;
+    const double cx = dmul(dadd(dmul(mL, cLx), dmul(mR, cRx)), iM);
+    const double cy = dmul(dadd(dmul(mL, cLy), dmul(mR, cRy)), iM);
+    const double cz = dmul(dadd(dmul(mL, cLz), dmul(mR, cRz)), iM);
     ncx[v] = cx;
     ncy[v] = cy;
     ncz[v] = cz;
@@ -732,12 +753,13 @@ __global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const i
       store_moments<NQ>(v, qp, M, Qd, Qf);
     }
     nmass[v] = M;
-    nhmax[v] = fmax(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
+    nhmax[v] = dmax_pos(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
     nlu[v] = __ldcg(&nlu[L]) + __ldcg(&nlu[R]);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const double a = __ldcg(&extv[6 * (size_t)L + c]), b = __ldcg(&extv[6 * (size_t)R + c]);
-      const bool right = (c < 3) ? (b < a) : (b > a);
+      const long long ka = dkey(a), kb = dkey(b);
+      const bool right = (c < 3) ? (kb < ka) : (kb > ka);
       extv[6 * (size_t)v + c] = right ? b : a;
       exti[6 * (size_t)v + c] = __ldcg(&exti[6 * (size_t)(right ? R : L) + c]);
     }
@@ -760,19 +782,21 @@ __device__ __forceinline__ void upward_node(int v, const int* __restrict__ nrigh
   const double M = dadd(mL, mR);
   const double cLx = ncx[L], cLy = ncy[L], cLz = ncz[L];
   const double cRx = ncx[R], cRy = ncy[R], cRz = ncz[R];
-  const double cx = __ddiv_rn(dadd(dmul(mL, cLx), dmul(mR, cRx)), M);
-  const double cy = __ddiv_rn(dadd(dmul(mL, cLy), dmul(mR, cRy)), M);
-  const double cz = __ddiv_rn(dadd(dmul(mL, cLz), dmul(mR, cRz)), M);
+  const double iM = 1.0 / M;  // one division per node
+  const double cx = dmul(dadd(dmul(mL, cLx), dmul(mR, cRx)), iM);
+  const double cy = dmul(dadd(dmul(mL, cLy), dmul(mR, cRy)), iM);
+  const double cz = dmul(dadd(dmul(mL, cLz), dmul(mR, cRz)), iM);
   ncx[v] = cx;
   ncy[v] = cy;
   ncz[v] = cz;
   nmass[v] = M;
-  nhmax[v] = fmax(nhmax[L], nhmax[R]);
+  nhmax[v] = dmax_pos(nhmax[L], nhmax[R]);
   nlu[v] = nlu[L] + nlu[R];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     const double a = extv[6 * (size_t)L + c], b = extv[6 * (size_t)R + c];
-    const bool right = (c < 3) ? (b < a) : (b > a);
+    const long long ka = dkey(a), kb = dkey(b);
+    const bool right = (c < 3) ? (kb < ka) : (kb > ka);
     extv[6 * (size_t)v + c] = right ? b : a;
     exti[6 * (size_t)v + c] = exti[6 * (size_t)(right ? R : L) + c];
   }
@@ -825,19 +849,37 @@ __device__ __forceinline__ double exact_d2(double x, double y, double z, double 
 __global__ void k_node_lb(int nn, const int* __restrict__ wparent, const int* __restrict__ exti,
                           const double* __restrict__ px, const double* __restrict__ py,
                           const double* __restrict__ pz, const double* __restrict__ ncx,
-                          const double* __restrict__ ncy, const double* __restrict__ ncz, double* __restrict__ lb) {
+                          const double* __restrict__ ncy, const double* __restrict__ ncz, double* __restrict__ lb,
+                          float4* __restrict__ geo_hi, float4* __restrict__ geo_lo) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nn) return;
   double m = 0.0;
+  const double cx = ncx[v], cy = ncy[v], cz = ncz[v];
   if (wparent[v] != -2) {
-    const double cx = ncx[v], cy = ncy[v], cz = ncz[v];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const int e = exti[6 * (size_t)v + c];
       m = fmax(m, exact_d2(px[e], py[e], pz[e], cx, cy, cz));
     }
   }
-  lb[v] = __dsqrt_rn(m);
+  const double l = __dsqrt_rn(m);
+  lb[v] = l;
+  // the centre as double-float (final records; w: the size, written last)
+  // and, until then, LB rounded down for the FP32 candidate tests
+  float xh, xl, yh, yl, zh, zl;
+  split_double(cx, xh, xl);
+  split_double(cy, yh, yl);
+  split_double(cz, zh, zl);
+  geo_hi[v] = make_float4(xh, yh, zh, __double2float_rd(l));
+  geo_lo[v] = make_float4(xl, yl, zl, 0.0f);
+}
+
+// Upper bound on the error of an FP32 distance assembled from double-float
+// centre differences (each within a few units of 2^-24 of its value, the
+// centres within 2^-48 of theirs) and FP32 offsets: generous by two orders.
+__device__ __forceinline__ float df_dist_err(float ox, float oy, float oz, float4 a, float4 b) {
+  return 2e-6f * (fabsf(ox) + fabsf(oy) + fabsf(oz)) +
+         1e-13f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + fabsf(b.x) + fabsf(b.y) + fabsf(b.z));
 }
 
 // Thread per leaf: the leaf's exact size, and which ancestors it is a
@@ -848,8 +890,8 @@ __global__ void k_size_leaf(int nleaves, const int* __restrict__ leaf_node, cons
                             const double* __restrict__ px, const double* __restrict__ py,
                             const double* __restrict__ pz, const double* __restrict__ ncx,
                             const double* __restrict__ ncy, const double* __restrict__ ncz,
-                            const double* __restrict__ lb, unsigned long long* __restrict__ l2bits,
-                            unsigned long long* __restrict__ cand) {
+                            const float4* __restrict__ geo_hi, const float4* __restrict__ geo_lo,
+                            unsigned long long* __restrict__ l2bits, unsigned long long* __restrict__ cand) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nleaves) return;
   const int L = leaf_node[q];
@@ -858,13 +900,21 @@ __global__ void k_size_leaf(int nleaves, const int* __restrict__ leaf_node, cons
   double l2 = 0.0;
   for (int i = f; i < f + cnt; ++i) l2 = fmax(l2, exact_d2(px[i], py[i], pz[i], cx, cy, cz));
   l2bits[L] = (unsigned long long)__double_as_longlong(l2);
-  const double lL = __dsqrt_rn(l2) * (1.0 + 1e-12);
+  const float lL = __double2float_ru(__dsqrt_rn(l2));
+  const float4 hL = geo_hi[L], oL = geo_lo[L];
+  // an ancestor v is skipped when every particle of the leaf is certainly
+  // closer to s_v than LB(v) (a real particle's distance): |s_L - s_v| + l_L,
+  // with its error bound and one more relative margin for the FP32 sums,
+  // below LB(v) rounded down
   unsigned long long m0 = 0ull, m1 = 0ull;
   int k = 1;
   for (int v = (wparent[L] >= 0) ? wparent[L] : -1; v >= 0; v = wparent[v], ++k) {
-    const double bound = lb[v] * (1.0 - 1e-12) - lL;
-    const bool skip = bound > 0.0 && exact_d2(cx, cy, cz, ncx[v], ncy[v], ncz[v]) * (1.0 + 1e-12) < bound * bound;
-    if (!skip) {
+    const float4 hv = geo_hi[v], ov = geo_lo[v];
+    const float dx = df_diff(hL.x, oL.x, hv.x, ov.x), dy = df_diff(hL.y, oL.y, hv.y, ov.y),
+                dz = df_diff(hL.z, oL.z, hv.z, ov.z);
+    const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    const float reach = (d + df_dist_err(dx, dy, dz, hL, hv) + lL) * (1.0f + 1e-6f);
+    if (!(reach < hv.w)) {
       if (k < 64) m0 |= 1ull << k;
       else if (k < 128) m1 |= 1ull << (k - 64);
     }
@@ -880,12 +930,14 @@ __global__ void k_size(int n, const double* __restrict__ px, const double* __res
                        const uint32_t* __restrict__ leaf_index, const unsigned long long* __restrict__ cand,
                        const int* __restrict__ wparent, const double* __restrict__ ncx,
                        const double* __restrict__ ncy, const double* __restrict__ ncz,
-                       unsigned long long* __restrict__ l2bits) {
+                       const float4* __restrict__ geo_hi, const float4* __restrict__ geo_lo,
+                       const float4* __restrict__ prel, unsigned long long* __restrict__ l2bits) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   int v = -1;
   unsigned long long m0 = 0ull, m1 = 0ull;
   double x = 0.0, y = 0.0, z = 0.0;
+  float4 hL = make_float4(0.f, 0.f, 0.f, 0.f), oL = hL, r = hL;
   if (i < n) {
     const int L = pnode[i];
     v = wparent[L];  // the leaf itself was done by k_size_leaf
@@ -895,12 +947,25 @@ __global__ void k_size(int n, const double* __restrict__ px, const double* __res
     x = px[i];
     y = py[i];
     z = pz[i];
+    hL = geo_hi[L];
+    oL = geo_lo[L];
+    r = prel[i];  // x - s_L in FP32
   }
+  const float er = 2e-6f * (fabsf(r.x) + fabsf(r.y) + fabsf(r.z));
   int k = 1;
   while (true) {
     const unsigned act = __ballot_sync(SFMM_FULL, v >= 0);
     if (act == 0u) break;
-    const bool want = v >= 0 && (k >= 128 || ((k < 64 ? (m0 >> k) : (m1 >> (k - 64))) & 1ull));
+    bool want = v >= 0 && (k >= 128 || ((k < 64 ? (m0 >> k) : (m1 >> (k - 64))) & 1ull));
+    if (want) {
+      // certainly closer than LB(v)? then not the maximum: skip the exact test
+      const float4 hv = geo_hi[v], ov = geo_lo[v];
+      const float ox = df_diff(hL.x, oL.x, hv.x, ov.x), oy = df_diff(hL.y, oL.y, hv.y, ov.y),
+                  oz = df_diff(hL.z, oL.z, hv.z, ov.z);
+      const float dx = r.x + ox, dy = r.y + oy, dz = r.z + oz;
+      const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      want = !((d + er + df_dist_err(ox, oy, oz, hL, hv)) * (1.0f + 1e-6f) < hv.w);
+    }
     const unsigned actw = __ballot_sync(SFMM_FULL, want);
     if (want) {
       const double d2 = exact_d2(x, y, z, ncx[v], ncy[v], ncz[v]);
@@ -1313,29 +1378,30 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   k_node_lb<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->wparent.as<int>(), c->n_exti.as<int>(),
                                                c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
                                                c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                               c->n_lb.as<double>());
+                                               c->n_lb.as<double>(), c->geo_hi.as<float4>(), c->geo_lo.as<float4>());
+  // FP32 particle records (offsets from the leaf centre) first: the size
+  // tests use them
+  k_particles_f32<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
+                                                c->pm.as<double>(), c->ph.as<double>(), c->pnode.as<int>(),
+                                                c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
+                                                c->prel.as<float4>(), c->ph32.as<float>(), c->phh.as<float2>());
   k_size_leaf<<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(),
                                              c->wparent.as<int>(), c->px.as<double>(), c->py.as<double>(),
                                              c->pz.as<double>(), c->ncx.as<double>(), c->ncy.as<double>(),
-                                             c->ncz.as<double>(), c->n_lb.as<double>(),
+                                             c->ncz.as<double>(), c->geo_hi.as<float4>(), c->geo_lo.as<float4>(),
                                              c->l2bits.as<unsigned long long>(),
                                              c->size_cand.as<unsigned long long>());
   k_size<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
                                        c->pnode.as<int>(), c->isleaf.as<uint32_t>(),
                                        c->size_cand.as<unsigned long long>(), c->wparent.as<int>(),
                                        c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
+                                       c->geo_hi.as<float4>(), c->geo_lo.as<float4>(), c->prel.as<float4>(),
                                        c->l2bits.as<unsigned long long>());
-  c->nlaunch += 2;
-  ++c->nlaunch;
+  c->nlaunch += 4;
   k_finalize_nodes<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->l2bits.as<unsigned long long>(), c->ncx.as<double>(),
                                                       c->ncy.as<double>(), c->ncz.as<double>(), c->nhmax.as<double>(),
                                                       c->nsize.as<double>(), c->geo_hi.as<float4>(),
                                                       c->geo_lo.as<float4>());
-  ++c->nlaunch;
-  k_particles_f32<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
-                                                c->pm.as<double>(), c->ph.as<double>(), c->pnode.as<int>(),
-                                                c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                                c->prel.as<float4>(), c->ph32.as<float>(), c->phh.as<float2>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   c->moments_order = P;
