@@ -170,7 +170,7 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_leaf_off, &c->sys_sums,
                     &c->p2p_extra, &c->p2p_split, &c->p2p_slist, &c->p2p_part, &c->lf_acc, &c->lf_part,
                     &c->kd_ord, &c->kd_node, &c->kd_act, &c->kd_work, &c->kd_chunk, &c->kd_part, &c->kd_split,
-                    &c->sym_own, &c->sym_recv, &c->wqueue, &c->n_extv, &c->n_exti, &c->n_lb, &c->size_cand};
+                    &c->sym_own, &c->sym_recv, &c->wqueue, &c->sort_aux, &c->n_extv, &c->n_exti, &c->n_lb, &c->size_cand};
   for (DevBuf* b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);

@@ -59,6 +59,7 @@ struct sfmm_ctx {
 
   // sort / build temporaries
   DevBuf keys_a, keys_b, idx_a, idx_b, sort_counts, scan_tmp, bbox_part;
+  DevBuf sort_aux;  // radix sort: digit histograms of every pass, tile counters
   DevBuf k_left, k_right, k_first, k_last, par_int, par_leaf, chain, pre_int, pre_leaf;
   DevBuf misc;  // device-side scalars: bbox, counters
 

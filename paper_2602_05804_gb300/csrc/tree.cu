@@ -350,6 +350,155 @@ __global__ void __launch_bounds__(RS_NT) k_rs_scatter(const uint64_t* __restrict
   }
 }
 
+// Onesweep passes (Adinets and Merrill's single-pass radix sort): the digit
+// histograms of every pass are counted once up front; each pass is then one
+// launch in which a tile (numbered in start order by an atomic counter)
+// publishes its digit counts, adds those of all earlier tiles by decoupled
+// look-back and scatters its keys stably.  A published word holds a 2-bit
+// flag (1: this tile's count, 2: inclusive of all earlier tiles) and a
+// 30-bit count.
+#define RS_FLAG_AGG (1u << 30)
+#define RS_FLAG_INC (2u << 30)
+#define RS_COUNT_MASK ((1u << 30) - 1u)
+// Bounded wait on an earlier tile's word (it is running, so the wait ends;
+// the limit only turns a fault into an error status)
+#define RS_SPIN (1 << 22)
+#ifndef OS_ITEMS
+#define OS_ITEMS 8  // keys per thread of a onesweep tile (4, 8, 16 measured: 8 best)
+#endif
+#define OS_TILE (RS_NT * OS_ITEMS)
+
+__global__ void __launch_bounds__(RS_NT) k_rs_upfront(const uint64_t* __restrict__ keys,
+                                                      const uint32_t* __restrict__ vals,
+                                                      const int* __restrict__ psys, int n, int nkey,
+                                                      int nsysd, uint32_t* __restrict__ gh) {
+  __shared__ uint32_t h[12][256];
+  const int npass = nkey + nsysd;
+  for (int t = threadIdx.x; t < npass * 256; t += RS_NT) (&h[0][0])[t] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * RS_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RS_NT) {
+    const uint64_t k = keys[i];
+    for (int p = 0; p < nkey; ++p) atomicAdd(&h[p][(unsigned)(k >> (8 * p)) & 255u], 1u);
+    if (nsysd) {
+      const unsigned sv = (unsigned)psys[vals[i]];
+      for (int p = 0; p < nsysd; ++p) atomicAdd(&h[nkey + p][(sv >> (8 * p)) & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < npass * 256; t += RS_NT) {
+    const uint32_t v = (&h[0][0])[t];
+    if (v) atomicAdd(&gh[t], v);
+  }
+}
+
+__global__ void __launch_bounds__(RS_NT) k_rs_onesweep(const uint64_t* __restrict__ kin,
+                                                       const uint32_t* __restrict__ vin,
+                                                       uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                       const int* __restrict__ psys, int n, int shift,
+                                                       const uint32_t* __restrict__ ghist, uint32_t* tstat,
+                                                       int* tile_ctr, int* status) {
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wc[RS_WARPS][256];
+  __shared__ uint32_t s_tot[256];
+  __shared__ int s_tile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1);
+  for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_NT) (&wc[0][0])[t] = 0;
+  __syncthreads();
+  const int tile = s_tile;
+  const int64_t base = (int64_t)tile * OS_TILE;
+  // the tile's keys and digits, and its digit counts
+  uint64_t key[OS_ITEMS];
+  uint32_t val[OS_ITEMS];
+  int dig[OS_ITEMS];
+#pragma unroll
+  for (int r = 0; r < OS_ITEMS; ++r) {
+    const int64_t i = base + (int64_t)r * RS_NT + threadIdx.x;
+    const bool valid = i < n;
+    key[r] = valid ? kin[i] : 0ull;
+    val[r] = valid ? vin[i] : 0u;
+    dig[r] = valid ? (int)(psys ? (((unsigned)psys[val[r]] >> shift) & 255u) : ((unsigned)(key[r] >> shift) & 255u))
+                   : 256;
+    if (valid) atomicAdd(&wc[warp][dig[r]], 1u);
+  }
+  __syncthreads();
+  // publish, look back, and the digit's start in the output
+  if (threadIdx.x < 256) {
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
+    for (int w = 0; w < RS_WARPS; ++w) cnt += wc[w][d];
+    volatile uint32_t* st = tstat;
+    st[(int64_t)tile * 256 + d] = (tile == 0 ? RS_FLAG_INC : RS_FLAG_AGG) | cnt;
+    uint32_t excl = 0;
+    int t = tile - 1, spins = 0;
+    while (t >= 0) {
+      const uint32_t w = st[(int64_t)t * 256 + d];
+      if ((w & ~RS_COUNT_MASK) == 0u) {
+        if (++spins > RS_SPIN) {
+          set_status(status, SFMM_ST_INTERNAL);
+          break;
+        }
+        continue;
+      }
+      excl += w & RS_COUNT_MASK;
+      if ((w & ~RS_COUNT_MASK) == RS_FLAG_INC) break;
+      --t;
+    }
+    if (tile > 0) st[(int64_t)tile * 256 + d] = RS_FLAG_INC | (excl + cnt);
+    s_tot[d] = ghist[d];
+    run[d] = excl;
+  }
+  __syncthreads();
+  // exclusive scan of the pass's digit totals (the digit starts), added in
+  if (threadIdx.x < 256) {
+    uint32_t v = s_tot[threadIdx.x];
+    // warp-level inclusive scan, then across the 8 warps
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(SFMM_FULL, v, o);
+      if (lane >= o) v += y;
+    }
+    wc[0][threadIdx.x] = v;  // inclusive within the warp
+  }
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; ++w) pre += wc[0][32 * w + 31];
+    run[threadIdx.x] += pre + wc[0][threadIdx.x] - s_tot[threadIdx.x];
+  }
+  __syncthreads();
+  // stable scatter in input order: item r of every thread, warp by warp
+#pragma unroll
+  for (int r = 0; r < OS_ITEMS; ++r) {
+    for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_NT) (&wc[0][0])[t] = 0;
+    __syncthreads();
+    const int d = dig[r];
+    const unsigned peers = __match_any_sync(SFMM_FULL, d);
+    const unsigned rank = __popc(peers & lanemask_lt());
+    const bool leader = (__ffs(peers) - 1) == lane;
+    if (d < 256 && leader) wc[warp][d] = __popc(peers);
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      uint32_t s = run[threadIdx.x];
+      for (int w = 0; w < RS_WARPS; ++w) {
+        const uint32_t c = wc[w][threadIdx.x];
+        wc[w][threadIdx.x] = s;
+        s += c;
+      }
+      run[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (d < 256) {
+      const uint32_t dst = wc[warp][d] + rank;
+      if (dst < (uint32_t)n) {  // always, unless a look-back gave up (status set)
+        kout[dst] = key[r];
+        vout[dst] = val[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Gather the sorted particles (float64 SoA)
 // ---------------------------------------------------------------------------
@@ -1274,17 +1423,40 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     // the result is ordered by (system, key, input index)
     int sys_bits = 0;
     while ((1 << sys_bits) < nsys) ++sys_bits;
-    const int npass = 8 + (sys_bits + 7) / 8;
+    const int nsysd = (sys_bits + 7) / 8;
+    const int npass = 8 + nsysd;
+    // digit histograms of all passes at once, then one launch per pass (the
+    // published counts have 30 bits; larger sets take the three-step passes)
+    const bool onesweep = n < (1 << 30);
+    const size_t aux = sizeof(uint32_t) * 256 * (size_t)npass + sizeof(int) * (size_t)npass;
+    if ((rc = c->sort_aux.ensure(aux))) return rc;
+    uint32_t* gh = c->sort_aux.as<uint32_t>();
+    int* tctr = reinterpret_cast<int*>(gh + 256 * (size_t)npass);
+    SFMM_CUDA_TRY(cudaMemsetAsync(gh, 0, aux, st));
+    if (onesweep) {
+      k_rs_upfront<<<std::min(ntiles, 4 * num_sms(c->device)), RS_NT, 0, st>>>(ka, va, psys, n, 8,
+                                                                             psys ? nsysd : 0, gh);
+      ++c->nlaunch;
+    }
     for (int pass = 0; pass < npass; ++pass) {
       const bool by_sys = pass >= 8;
       const int shift = by_sys ? 8 * (pass - 8) : 8 * pass;
       const int* dsys = by_sys ? psys : nullptr;
-      k_rs_hist<<<ntiles, RS_NT, 0, st>>>(ka, va, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
-      ++c->nlaunch;
-      SFMM_CUDA_TRY(cudaGetLastError());
-      if ((rc = exclusive_scan_u32(c, c->sort_counts.as<uint32_t>(), (int64_t)256 * ntiles, nullptr))) return rc;
-      k_rs_scatter<<<ntiles, RS_NT, 0, st>>>(ka, va, kb, vb, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
-      ++c->nlaunch;
+      if (onesweep) {
+        const int otiles = (n + OS_TILE - 1) / OS_TILE;
+        SFMM_CUDA_TRY(cudaMemsetAsync(c->sort_counts.p, 0, sizeof(uint32_t) * 256 * (size_t)otiles, st));
+        k_rs_onesweep<<<otiles, RS_NT, 0, st>>>(ka, va, kb, vb, dsys, n, shift, gh + 256 * (size_t)pass,
+                                                c->sort_counts.as<uint32_t>(), tctr + pass, c->d_status);
+        ++c->nlaunch;
+      } else {
+        k_rs_hist<<<ntiles, RS_NT, 0, st>>>(ka, va, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
+        ++c->nlaunch;
+        SFMM_CUDA_TRY(cudaGetLastError());
+        if ((rc = exclusive_scan_u32(c, c->sort_counts.as<uint32_t>(), (int64_t)256 * ntiles, nullptr))) return rc;
+        k_rs_scatter<<<ntiles, RS_NT, 0, st>>>(ka, va, kb, vb, dsys, n, shift, c->sort_counts.as<uint32_t>(),
+                                               ntiles);
+        ++c->nlaunch;
+      }
       SFMM_CUDA_TRY(cudaGetLastError());
       std::swap(ka, kb);
       std::swap(va, vb);
