@@ -198,8 +198,11 @@ __device__ __forceinline__ void leaf_l2p(const LevelArgs& la, int A, double cAx,
   }
 }
 
+// Blocks per SM (FP32, p <= 2): 5 for the queue walk, 4 per depth -- measured:
+// the queue walk gains from the fifth block despite a few spilled registers,
+// the per-depth walk loses.
 template <int P, bool F32, bool SYM, bool QUEUE>
-__global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_level(const LevelArgs la) {
+__global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1) k_walk_level(const LevelArgs la) {
   static_assert(!(SYM && QUEUE), "the queue walk runs walk mode 1 only");
   using E = Exp<P>;
   using R = typename std::conditional<F32, float, double>::type;
@@ -620,14 +623,16 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
   using E = Exp<P>;
   constexpr int NCS = (E::NC + 31) / 32;
   const int nn = c->nnodes, nl = c->nleaves;
-  int per_sm = 0;
+  int per_sm = 0, q_per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_level<P, F32, SYM, false>, WALK_NT, 0);
+  if (!SYM) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_per_sm, k_walk_level<P, F32, false, true>, WALK_NT, 0);
   // readiness queue or one launch per depth (walk mode 1): the queue runs
   // nodes of all depths at once, so it pays when their walk records
   // (geometry, moments, coefficients, list offsets) stay in L2; per-depth
   // launches keep one depth's records resident otherwise
   if (per_sm < 1) per_sm = 1;
-  const int max_blocks = per_sm * num_sms(c->device);
+  if (q_per_sm < 1) q_per_sm = 1;
+  const int max_blocks = per_sm * num_sms(c->device), q_blocks = q_per_sm * num_sms(c->device);
   const int tstride = NCS * 32;
   bool queue = false;
   if (!SYM) {
@@ -644,7 +649,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
   }
   int rc;
   for (int attempt = 0; attempt < SFMM_WALK_ATTEMPTS; ++attempt) {
-    const int nwarps = max_blocks * WALK_WARPS;
+    const int nwarps = std::max(max_blocks, q_blocks) * WALK_WARPS;  // one ring per resident warp
     if ((rc = c->ring.ensure(sizeof(int) * (size_t)nwarps * 2 * c->ring_capacity))) return rc;
     long long arena_cap = c->list_capacity > 0 ? c->list_capacity : (long long)nl * 96 + 1024;
     if ((rc = c->arena.ensure(sizeof(int) * (size_t)arena_cap))) return rc;
@@ -744,9 +749,6 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
         // one block per resident slot (the queue needs none resident: a warp
         // only takes a slot while it runs, and a node's parent always holds
         // an earlier slot)
-        int q_per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_per_sm, k_walk_level<P, F32, false, true>, WALK_NT, 0);
-        const int q_blocks = std::max(1, std::min(q_per_sm, per_sm)) * num_sms(c->device);
         k_walk_level<P, F32, false, true><<<q_blocks, WALK_NT, 0, c->stream>>>(la);
         ++c->nlaunch;
       }
