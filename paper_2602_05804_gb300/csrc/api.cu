@@ -161,7 +161,7 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->idx_a, &c->idx_b, &c->sort_counts, &c->scan_tmp, &c->bbox_part, &c->k_left,
                     &c->k_right, &c->k_first, &c->k_last, &c->par_int, &c->par_leaf, &c->chain,
                     &c->pre_int, &c->pre_leaf, &c->misc, &c->px, &c->py, &c->pz, &c->pm, &c->ph,
-                    &c->perm, &c->pnode, &c->prel, &c->ph32, &c->phh, &c->nfirst, &c->ncount, &c->nright,
+                    &c->perm, &c->pnode, &c->prel, &c->phh, &c->nfirst, &c->ncount, &c->nright,
                     &c->nparent, &c->ndepth, &c->ncx, &c->ncy, &c->ncz, &c->nsize, &c->nhmax, &c->nmass,
                     &c->l2bits, &c->flags, &c->geo_hi, &c->geo_lo, &c->leaf_node, &c->isleaf, &c->Qd,
                     &c->Qf, &c->ring, &c->far, &c->arena, &c->p2p_off, &c->p2p_cnt, &c->counters,

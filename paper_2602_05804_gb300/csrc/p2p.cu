@@ -29,8 +29,7 @@ struct P2PArgs {
   const long long* p2p_off;
   const int* p2p_cnt;
   const float4* prel;
-  const float* ph32;
-  const float2* phh;
+  const float4* phh;  // {1/h, (2h)^2, 2h rounded up, 0}
   const double* px;
   const double* py;
   const double* pz;
@@ -245,7 +244,7 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
     auto load_target = [&](int i, R& x, R& y, R& z, R& hinv, R& h2) {
       if constexpr (F32) {
         const float4 p = a.prel[i];
-        const float2 hh = a.phh[i];
+        const float4 hh = a.phh[i];
         x = p.x; y = p.y; z = p.z; hinv = hh.x; h2 = hh.y;
       } else {
         const double h = a.ph[i];
@@ -288,7 +287,7 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
           const int y = __shfl_up_sync(SFMM_FULL, incl, o);
           if (lane >= o) incl += y;
         }
-        cum = incl - nS;
+        cum = (nS > 0) ? incl - nS : INT_MAX;  // padding entries start nowhere
         tot = __shfl_sync(SFMM_FULL, incl, 31);
         pdone = 0;
         e += 32;
@@ -297,29 +296,34 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
         // stage one window of up to 32 particles of the stream
         const int p = pdone + lane;
         const bool valid = p < tot;
-        int l = 0;
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-          const int c = __shfl_sync(SFMM_FULL, cum, l + step);
-          if (c <= p) l += step;
-        }
-        const int c_l = __shfl_sync(SFMM_FULL, cum, l);
-        const int f_l = __shfl_sync(SFMM_FULL, fS, l);
+        // the entry holding position p: entries starting before the window
+        // plus those starting inside it at or before p (every entry holds at
+        // least one particle; the padding entries past the list hold none)
+        const bool pre = cum < pdone;
+        const int rs = cum - pdone;  // (no overflow: padding lanes test as neither)
+        const unsigned starts = __reduce_or_sync(SFMM_FULL, (!pre && rs < 32) ? (1u << rs) : 0u);
+        const int before = __popc(__ballot_sync(SFMM_FULL, pre));
+        const int l = before + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+        const int d_l = __shfl_sync(SFMM_FULL, fS - cum, l);  // particle index minus stream position
         const R ox_l = __shfl_sync(SFMM_FULL, ox, l), oy_l = __shfl_sync(SFMM_FULL, oy, l),
                 oz_l = __shfl_sync(SFMM_FULL, oz, l);
         V v;
         V2 hh;
+        R h2j = R(0);  // 2 h_j (FP32 form: rounded up)
         int i = 0;
         if (valid) {
-          i = f_l + (p - c_l);
+          i = d_l + p;
           if constexpr (F32) {
             const float4 q = a.prel[i];
             v = make_float4(q.x + ox_l, q.y + oy_l, q.z + oz_l, q.w);
-            hh = a.phh[i];
+            const float4 hr = a.phh[i];
+            hh = make_float2(hr.x, hr.y);
+            h2j = hr.z;
           } else {
             const double h = a.ph[i];
             v = make_double4(a.px[i], a.py[i], a.pz[i], a.pm[i]);
             hh = make_double2(1.0 / h, 4.0 * h * h);
+            h2j = 2.0 * h;
           }
         } else {
           v.x = v.y = v.z = v.w = R(0);
@@ -331,9 +335,8 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
           ry -= cLy;
           rz -= cLz;
         }
-        // reach^2 = (l_L + 2 max(h_L, h_j))^2, with h_j from (2h_j)^2
-        // 2 h_j = sqrt((2 h_j)^2) via rsqrt: the 1.0001 factor covers its error
-        const R reach = lL + fmax(R(2) * hL, valid ? hh.y * rsq(hh.y) * R(1.0001) : R(0));
+        // reach = l_L + 2 max(h_L, h_j) (l_L and h_L carry a 1.0001 margin)
+        const R reach = lL + fmax(R(2) * hL, h2j);
         const bool near = valid && (fma(rx, rx, fma(ry, ry, rz * rz)) < reach * reach);
         const unsigned bn = __ballot_sync(SFMM_FULL, near), bf = __ballot_sync(SFMM_FULL, valid && !near);
         if (near) {
@@ -748,8 +751,7 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   a.p2p_off = c->p2p_off.as<long long>();
   a.p2p_cnt = c->p2p_cnt.as<int>();
   a.prel = c->prel.as<float4>();
-  a.ph32 = c->ph32.as<float>();
-  a.phh = c->phh.as<float2>();
+  a.phh = c->phh.as<float4>();
   a.px = c->px.as<double>();
   a.py = c->py.as<double>();
   a.pz = c->pz.as<double>();

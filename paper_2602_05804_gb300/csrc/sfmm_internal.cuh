@@ -68,8 +68,7 @@ struct sfmm_ctx {
   DevBuf perm;                  // int32 sorted position -> input index
   DevBuf pnode;                 // int32 sorted position -> leaf node
   DevBuf prel;                  // float4 {x - s_leaf, y - s_leaf, z - s_leaf, m}
-  DevBuf ph32;                  // float h
-  DevBuf phh;                   // float2 {1/h, (2h)^2}
+  DevBuf phh;                   // float4 {1/h, (2h)^2, 2h rounded up, 0}
 
   // nodes (pre-order)
   DevBuf nfirst, ncount, nright, nparent, ndepth;

@@ -1094,15 +1094,14 @@ __global__ void k_particles_f32(int n, const double* __restrict__ px, const doub
                                 const double* __restrict__ ph, const int* __restrict__ pnode,
                                 const double* __restrict__ ncx, const double* __restrict__ ncy,
                                 const double* __restrict__ ncz, float4* __restrict__ prel,
-                                float* __restrict__ ph32, float2* __restrict__ phh) {
+                                float4* __restrict__ phh) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int v = pnode[i];
   prel[i] = make_float4(__double2float_rn(dsub(px[i], ncx[v])), __double2float_rn(dsub(py[i], ncy[v])),
                         __double2float_rn(dsub(pz[i], ncz[v])), __double2float_rn(pm[i]));
   const double h = ph[i];
-  ph32[i] = __double2float_rn(h);
-  phh[i] = make_float2(__double2float_rn(1.0 / h), __double2float_rn(4.0 * h * h));
+  phh[i] = make_float4(__double2float_rn(1.0 / h), __double2float_rn(4.0 * h * h), __double2float_ru(2.0 * h), 0.0f);
 }
 
 __global__ void k_depth(int nn, const int* __restrict__ nparent, int* __restrict__ depth) {
@@ -1271,8 +1270,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ENS(perm, sizeof(int) * n);
   ENS(pnode, sizeof(int) * n);
   ENS(prel, sizeof(float4) * n);
-  ENS(ph32, sizeof(float) * n);
-  ENS(phh, sizeof(float2) * n);
+  ENS(phh, sizeof(float4) * n);
   ENS(k_left, sizeof(int) * n);
   ENS(k_right, sizeof(int) * n);
   ENS(k_first, sizeof(int) * n);
@@ -1483,7 +1481,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   k_particles_f32<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
                                                 c->pm.as<double>(), c->ph.as<double>(), c->pnode.as<int>(),
                                                 c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                                c->prel.as<float4>(), c->ph32.as<float>(), c->phh.as<float2>());
+                                                c->prel.as<float4>(), c->phh.as<float4>());
   k_size_leaf<<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(),
                                              c->wparent.as<int>(), c->px.as<double>(), c->py.as<double>(),
                                              c->pz.as<double>(), c->ncx.as<double>(), c->ncy.as<double>(),
