@@ -144,6 +144,7 @@ int sfmm_create(sfmm_ctx** out, int device, int precision, void* stream) {
             cudaMallocHost(&c->h_scalars, 64 * sizeof(double)) == cudaSuccess &&
             cudaMemset(c->d_status, 0, sizeof(int)) == cudaSuccess;
   for (int i = 0; ok && i < 8; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
+  if (ok) ok = cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     sfmm_destroy(c);
@@ -174,9 +175,12 @@ void sfmm_destroy(sfmm_ctx* c) {
   for (DevBuf* b : bufs) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->ev_stage) cudaEventDestroy(c->ev_stage);
   if (c->d_status) cudaFree(c->d_status);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  if (c->h_level_pin) cudaFreeHost(c->h_level_pin);
+  if (c->h_sys_pin) cudaFreeHost(c->h_sys_pin);
   if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -245,13 +249,30 @@ int build_common(sfmm_ctx* c, const double* pos, const double* mass, const doubl
       (rc = c->sys_lsz.ensure(sizeof(int) * (size_t)c->nsys)))
     return set_error(c, rc, "allocation failed");
   {
-    std::vector<int> off32(c->h_sys_off.begin(), c->h_sys_off.end());
-    SFMM_CUDA_TRY(cudaMemcpyAsync(c->sys_off.p, off32.data(), sizeof(int) * off32.size(), cudaMemcpyHostToDevice,
+    // system offsets and leaf sizes through a pinned staging buffer: the
+    // copies run in stream order without a wait here; the buffer is reused
+    // once the previous build's copies have run (an event marks them)
+    SFMM_CUDA_TRY(cudaEventSynchronize(c->ev_stage));
+    const size_t need = (size_t)c->nsys + 1 + (size_t)c->nsys;
+    if (need > c->h_sys_pin_cap) {
+      if (c->h_sys_pin) cudaFreeHost(c->h_sys_pin);
+      c->h_sys_pin = nullptr;
+      c->h_sys_pin_cap = 0;
+      if (cudaMallocHost(&c->h_sys_pin, sizeof(int) * need) != cudaSuccess) {
+        c->h_sys_pin = nullptr;
+        return set_error(c, SFMM_ENOMEM, "pinned allocation failed");
+      }
+      c->h_sys_pin_cap = need;
+    }
+    int* off32 = c->h_sys_pin;
+    int* lsz = c->h_sys_pin + c->nsys + 1;
+    for (int s = 0; s <= c->nsys; ++s) off32[s] = (int)c->h_sys_off[s];
+    for (int s = 0; s < c->nsys; ++s) lsz[s] = c->h_sys_lsz[s];
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->sys_off.p, off32, sizeof(int) * ((size_t)c->nsys + 1), cudaMemcpyHostToDevice,
                                   c->stream));
-    SFMM_CUDA_TRY(cudaMemcpyAsync(c->sys_lsz.p, c->h_sys_lsz.data(), sizeof(int) * c->h_sys_lsz.size(),
-                                  cudaMemcpyHostToDevice, c->stream));
-    // the host vectors must live until the copies have run: synchronise below
-    SFMM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    SFMM_CUDA_TRY(cudaMemcpyAsync(c->sys_lsz.p, lsz, sizeof(int) * (size_t)c->nsys, cudaMemcpyHostToDevice,
+                                  c->stream));
+    SFMM_CUDA_TRY(cudaEventRecord(c->ev_stage, c->stream));
   }
   if (c->profile) cudaEventRecord(c->ev[0], c->stream);
   rc = build_tree(c, pos, mass, h);
@@ -262,6 +283,7 @@ int build_common(sfmm_ctx* c, const double* pos, const double* mass, const doubl
   if (bits & (SFMM_ST_NONFINITE | SFMM_ST_NONPOSITIVE))
     return set_error(c, SFMM_ENONFINITE, "non-finite position/mass/h or non-positive mass/h");
   if (bits) return set_error(c, SFMM_ECUDA, "internal consistency check of the tree failed");
+  if ((rc = levels_finish(c))) return set_error(c, rc, "tree deeper than supported");
   c->built = true;
   c->stats = sfmm_stats{};
   c->stats.n = c->n;

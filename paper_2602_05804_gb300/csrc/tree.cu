@@ -1222,23 +1222,34 @@ static int geom_upward(sfmm_ctx* c, int nqs) {
   return geom_upward_t<P, double>(c, nqs);
 }
 
-// Depth, the per-depth lists of walkable internal nodes (the upward pass and
-// the walk run over them) and their offsets on the host (one synchronisation).
-static int levels_to_host(sfmm_ctx* c) {
+// Depth and the per-depth lists of walkable internal nodes (the walk runs
+// over them); their offsets are copied to pinned host memory without waiting:
+// levels_finish reads them once the build's closing status check has
+// synchronised the stream.
+#define SFMM_LEVEL_COPY 130  // the tree is at most 128 levels deep
+static int levels_issue(sfmm_ctx* c) {
   int rc;
   if ((rc = build_levels(c))) return rc;
-  // the tree is at most 128 levels deep: system, key and position bits
-  // distinguish every particle
-  const int ncopy = (int)std::min<int64_t>((int64_t)c->nnodes + 1, 130);
-  c->h_level_off.assign(ncopy, 0);
-  uint32_t h_tot = 0;
-  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_off.data(), c->level_off.p, sizeof(int) * ncopy, cudaMemcpyDeviceToHost,
+  if (!c->h_level_pin && cudaMallocHost(&c->h_level_pin, sizeof(int) * (SFMM_LEVEL_COPY + 1)) != cudaSuccess) {
+    c->h_level_pin = nullptr;
+    return SFMM_ENOMEM;
+  }
+  // system, key and position bits distinguish every particle: at most 128
+  // levels, so 130 offsets cover every depth
+  const int ncopy = (int)std::min<int64_t>((int64_t)c->nnodes + 1, SFMM_LEVEL_COPY);
+  c->level_ncopy = ncopy;
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_pin, c->level_off.p, sizeof(int) * ncopy, cudaMemcpyDeviceToHost,
                                 c->stream));
-  SFMM_CUDA_TRY(cudaMemcpyAsync(&h_tot, c->level_off.as<uint32_t>() + 2 * ((size_t)c->nnodes + 1), sizeof(uint32_t),
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_pin + SFMM_LEVEL_COPY,
+                                c->level_off.as<uint32_t>() + 2 * ((size_t)c->nnodes + 1), sizeof(uint32_t),
                                 cudaMemcpyDeviceToHost, c->stream));
-  SFMM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return SFMM_OK;
+}
+
+int levels_finish(sfmm_ctx* c) {
   // deepest level holding a walkable internal node (-1: none)
-  const int nint = (int)h_tot;
+  const int nint = c->h_level_pin[SFMM_LEVEL_COPY];
+  c->h_level_off.assign(c->h_level_pin, c->h_level_pin + c->level_ncopy);
   c->max_depth = -2;
   for (int d = 0; d < (int)c->h_level_off.size(); ++d)
     if (c->h_level_off[d] >= nint) {
@@ -1462,7 +1473,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   if ((rc = c->Qd.ensure(sizeof(double) * (size_t)nnodes * NQ)) ||
       (rc = c->Qf.ensure(sizeof(float) * (size_t)nnodes * nqs)))
     return rc;
-  if ((rc = levels_to_host(c))) return rc;
+  if ((rc = levels_issue(c))) return rc;
   switch (P) {
     case 0: rc = geom_upward<0>(c, nqs); break;
     case 1: rc = geom_upward<1>(c, nqs); break;
