@@ -56,11 +56,14 @@ def test_tree_matches_oracle(kind, n, ls):
     np.testing.assert_allclose(g["size"], t.size, rtol=0, atol=2e-12 * scale)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
-def test_moments_match_oracle(p):
+def test_moments_match_oracle(p, prec):
+    """FP64 moments against the oracle's.  In the FP32 form the build keeps
+    FP32 rows only; the export recomputes the FP64 moments."""
     pos, m, h = workloads.plummer(3000, 5)
     t = oracle.Tree(pos, m, h, 12, p=p)
-    s = solver("fp64")
+    s = solver(prec)
     s.build(pos, m, h, 12)
     Q, mi = s.moments(p)
     fact = np.array([math.factorial(a) * math.factorial(b) * math.factorial(c) for a, b, c in mi])
