@@ -47,7 +47,6 @@ struct LevelArgs {
   int* q_head;
   int* q_tail;
   int q_total;
-  int q_leaves;  // leaves go through the queue too (else one launch afterwards)
 };
 
 // Data a parent's warp wrote earlier in the same launch (the queue walk) is
@@ -240,12 +239,9 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
       __threadfence();
       __syncwarp();
       if (lane == 0) {
-        const bool pl = la.q_leaves || a.nright[node + 1] >= 0, pr = la.q_leaves || a.nright[right] >= 0;
-        if (pl || pr) {
-          int t = atomicAdd(la.q_tail, (int)pl + (int)pr);
-          if (pl) la.queue[t++] = node + 1;
-          if (pr) la.queue[t] = right;
-        }
+        const int t = atomicAdd(la.q_tail, 2);
+        la.queue[t] = node + 1;
+        la.queue[t + 1] = right;
       }
     }
   };
@@ -610,12 +606,10 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_finalize(const LevelArgs la, i
 }
 
 // Queue walk: the system roots fill the first slots.
-__global__ void k_queue_seed(int nsys, const int* __restrict__ sys_root, const int* __restrict__ nright, int q_leaves,
-                             int* __restrict__ queue, int* __restrict__ tail) {
-  for (int i = threadIdx.x; i < nsys; i += blockDim.x) {
-    const int r = sys_root[i];
-    if (q_leaves || nright[r] >= 0) queue[atomicAdd(tail, 1)] = r;
-  }
+__global__ void k_queue_seed(int nsys, const int* __restrict__ sys_root, int* __restrict__ queue,
+                             int* __restrict__ tail) {
+  for (int i = threadIdx.x; i < nsys; i += blockDim.x) queue[i] = sys_root[i];
+  if (threadIdx.x == 0) *tail = nsys;
 }
 
 template <int P, bool F32, bool SYM>
@@ -733,14 +727,13 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
       // one launch: a warp takes the next slot of the queue and waits until
       // the parent of the node there has pushed it; the system roots start it
       const int nint = c->h_level_off[nlev];
-      la.q_leaves = 1;
-      la.q_total = nint + (la.q_leaves ? nl : 0);
+      la.q_total = nint + nl;  // every walkable node, leaves included
       if ((rc = c->wqueue.ensure(sizeof(int) * (size_t)(la.q_total + 1)))) return rc;
       la.queue = c->wqueue.as<int>();
       la.q_head = reinterpret_cast<int*>(ctr + 14);
       la.q_tail = reinterpret_cast<int*>(ctr + 15);
       SFMM_CUDA_TRY(cudaMemsetAsync(la.queue, 0xff, sizeof(int) * (size_t)la.q_total, c->stream));
-      k_queue_seed<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), a.nright, la.q_leaves, la.queue, la.q_tail);
+      k_queue_seed<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), la.queue, la.q_tail);
       la.level = 0;
       la.level_nodes = nullptr;
       la.level_begin = 0;
@@ -754,11 +747,10 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
       }
       ++c->nlaunch;
       SFMM_CUDA_TRY(cudaGetLastError());
-      la.queue = nullptr;  // leaves left out of the queue run in one launch below
     }
     // internal nodes level by level (each needs its parent's opened list and
     // coefficients), then every leaf in one launch, shallowest first
-    for (int k = (queue && !la.q_leaves) ? nlev : 0; k <= nlev && !(queue && la.q_leaves); ++k) {
+    for (int k = 0; k <= nlev && !queue; ++k) {
       const bool leaves = (k == nlev);
       la.level = k;
       if (leaves) {
