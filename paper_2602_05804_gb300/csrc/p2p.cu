@@ -402,7 +402,8 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
           };
           far_pass(xi0, yi0, zi0, ax0, ay0, az0, pt0);
           if (nL > 32) far_pass(xi1, yi1, zi1, ax1, ay1, az1, pt1);
-        } else {
+        } else if (nL > 32) {
+        // FP64 form, more than 32 targets (up to 32: balanced, below)
         int j = ph;
         for (; j + nph < nfar; j += 2 * nph) {
           const V s0 = s_far[warp][j], s1 = s_far[warp][j + nph];
@@ -429,6 +430,79 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
             if (nL > 32) pair_cand<R>(xi1, yi1, zi1, hinvi1, h2i1, loc == t1, s0, hh, ax1, ay1, az1, pt1);
           }
         }
+      }
+      if (!F32 && nL <= 32 && nfar > 0) {
+        // FP64 form, up to 32 targets: the nL x nfar unsoftened pairs (target
+        // major) cut into 32 equal runs, one per lane -- every lane busy, and
+        // FP64 work costs per warp instruction whatever the active lanes.  A
+        // run spans at most two targets; the partials go back to the lane
+        // holding each target (lane t: target t, phase 0), which adds them in
+        // lane order
+        const int P = nL * nfar;
+        const int b0 = (lane * P) >> 5, b1 = ((lane + 1) * P) >> 5;
+        R fx = R(0), fy = R(0), fz = R(0), fp = R(0);  // the run's current target
+        R gx = R(0), gy = R(0), gz = R(0), gp = R(0);  // its first target, once it moved on
+        bool moved = false;
+        if (b0 < b1) {
+          int t = b0 / nfar, j = b0 - t * nfar;
+          R x = a.px[fL + t], y = a.py[fL + t], z = a.pz[fL + t];
+          for (int k = b0; k < b1; ++k) {
+            if (j == nfar) {
+              gx = fx; gy = fy; gz = fz; gp = fp;
+              fx = fy = fz = fp = R(0);
+              moved = true;
+              ++t;
+              j = 0;
+              x = a.px[fL + t];
+              y = a.py[fL + t];
+              z = a.pz[fL + t];
+            }
+            pair_far<R>(x, y, z, s_far[warp][j], fx, fy, fz, fp);
+            ++j;
+          }
+        }
+        // lanes covering target t: from the one holding pair t nfar (which
+        // may have started in target t - 1: then its second partial) to the
+        // one holding pair (t + 1) nfar - 1
+        int l0 = 0, l1 = -1;
+        bool second = false;
+        if (lane < nL) {
+          l0 = (32 * lane * nfar + 31) / P;
+          l1 = (32 * ((lane + 1) * nfar - 1) + 31) / P;
+          second = ((l0 * P) >> 5) < lane * nfar;
+        }
+        R sx = R(0), sy = R(0), sz = R(0), sp = R(0);
+        __syncwarp();
+        s_red[warp][0][lane] = moved ? fx : R(0);
+        s_red[warp][1][lane] = moved ? fy : R(0);
+        s_red[warp][2][lane] = moved ? fz : R(0);
+        s_red[warp][3][lane] = moved ? fp : R(0);
+        __syncwarp();
+        if (second) {
+          sx = s_red[warp][0][l0];
+          sy = s_red[warp][1][l0];
+          sz = s_red[warp][2][l0];
+          sp = s_red[warp][3][l0];
+        }
+        __syncwarp();
+        s_red[warp][0][lane] = moved ? gx : fx;
+        s_red[warp][1][lane] = moved ? gy : fy;
+        s_red[warp][2][lane] = moved ? gz : fz;
+        s_red[warp][3][lane] = moved ? gp : fp;
+        __syncwarp();
+        for (int l = second ? l0 + 1 : l0; l <= l1; ++l) {
+          sx += s_red[warp][0][l];
+          sy += s_red[warp][1][l];
+          sz += s_red[warp][2][l];
+          sp += s_red[warp][3][l];
+        }
+        if (lane < nL) {
+          ax0 += sx;
+          ay0 += sy;
+          az0 += sz;
+          pt0 += sp;
+        }
+        __syncwarp();
       }
       if (!F32 && nL <= 32 && nnear > 0) {
         // FP64 form, up to 32 targets: the unsoftened candidates in place; a
