@@ -275,7 +275,10 @@ __global__ void k_morton(const double* __restrict__ pos, int n, const double* __
 }
 
 // ---------------------------------------------------------------------------
-// S2: stable LSD radix sort of (key, index), 8-bit digits
+// S2: stable LSD radix sort of (key, index), 8-bit digits.  Sets below 2^30
+// particles take the onesweep passes further down (k_rs_upfront,
+// k_rs_onesweep); larger ones the reduce-then-scan passes here (per-tile
+// histograms, a scan over them, the scatter).
 // ---------------------------------------------------------------------------
 #define RS_NT 256
 #define RS_ITEMS 4
