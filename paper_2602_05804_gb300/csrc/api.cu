@@ -283,7 +283,6 @@ int build_common(sfmm_ctx* c, const double* pos, const double* mass, const doubl
   if (bits & (SFMM_ST_NONFINITE | SFMM_ST_NONPOSITIVE))
     return set_error(c, SFMM_ENONFINITE, "non-finite position/mass/h or non-positive mass/h");
   if (bits) return set_error(c, SFMM_ECUDA, "internal consistency check of the tree failed");
-  if ((rc = levels_finish(c))) return set_error(c, rc, "tree deeper than supported");
   c->built = true;
   c->stats = sfmm_stats{};
   c->stats.n = c->n;

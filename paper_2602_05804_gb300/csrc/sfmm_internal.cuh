@@ -53,10 +53,10 @@ struct sfmm_ctx {
   int max_depth = 0;
   std::vector<int> h_level_off;  // host copy: internal nodes per depth, max_depth + 2 entries
   int* h_level_pin = nullptr;     // pinned landing buffer of the level offsets (and their total)
+  bool levels_ready = false;      // per-depth lists built for the current tree
   int* h_sys_pin = nullptr;       // pinned staging of system offsets and leaf sizes
   size_t h_sys_pin_cap = 0;
   cudaEvent_t ev_stage = nullptr;  // after the last staged copies
-  int level_ncopy = 0;
 
   // inputs staged from host (sfmm_solve_host)
   DevBuf in_pos, in_mass, in_h;
@@ -119,8 +119,8 @@ int set_error(sfmm_ctx* c, int code, const char* msg);
 
 // tree.cu
 int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double* h);
-// after the stream has synchronised past build_tree: host level offsets
-int levels_finish(sfmm_ctx* c);
+// per-depth node lists and their host offsets, on first use after a build
+int ensure_levels(sfmm_ctx* c);
 // kdtree.cu: kd-tree topology, sorted particles and pre-order node layout
 int build_kd_topology(sfmm_ctx* c, const double* pos, const double* mass, const double* h);
 int compute_depth(sfmm_ctx* c);

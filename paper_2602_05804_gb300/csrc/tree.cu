@@ -1152,7 +1152,6 @@ static inline unsigned nblk(int64_t n, int nt) { return (unsigned)((n + nt - 1) 
 int build_levels(sfmm_ctx* c) {
   const int nn = c->nnodes;
   int rc;
-  if ((rc = compute_depth(c))) return rc;
   // depth < nn always; counts sized for the worst case.  Layout of level_off:
   // [0, nn + 1) internal-node offsets by depth, [nn + 1, 2 nn + 2) leaf offsets
   const size_t nc = (size_t)nn + 1;
@@ -1225,12 +1224,14 @@ static int geom_upward(sfmm_ctx* c, int nqs) {
   return geom_upward_t<P, double>(c, nqs);
 }
 
-// Depth and the per-depth lists of walkable internal nodes (the walk runs
-// over them); their offsets are copied to pinned host memory without waiting:
-// levels_finish reads them once the build's closing status check has
-// synchronised the stream.
+// The per-depth lists of walkable internal nodes and the leaves by depth,
+// built on first use: the per-depth walk launches and the one-sided
+// symmetric walk run over them; the readiness-queue walk needs only the
+// number of walkable nodes.  Their offsets come back to pinned host memory
+// (one synchronisation).
 #define SFMM_LEVEL_COPY 130  // the tree is at most 128 levels deep
-static int levels_issue(sfmm_ctx* c) {
+int ensure_levels(sfmm_ctx* c) {
+  if (c->levels_ready) return SFMM_OK;
   int rc;
   if ((rc = build_levels(c))) return rc;
   if (!c->h_level_pin && cudaMallocHost(&c->h_level_pin, sizeof(int) * (SFMM_LEVEL_COPY + 1)) != cudaSuccess) {
@@ -1240,19 +1241,15 @@ static int levels_issue(sfmm_ctx* c) {
   // system, key and position bits distinguish every particle: at most 128
   // levels, so 130 offsets cover every depth
   const int ncopy = (int)std::min<int64_t>((int64_t)c->nnodes + 1, SFMM_LEVEL_COPY);
-  c->level_ncopy = ncopy;
   SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_pin, c->level_off.p, sizeof(int) * ncopy, cudaMemcpyDeviceToHost,
                                 c->stream));
   SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_level_pin + SFMM_LEVEL_COPY,
                                 c->level_off.as<uint32_t>() + 2 * ((size_t)c->nnodes + 1), sizeof(uint32_t),
                                 cudaMemcpyDeviceToHost, c->stream));
-  return SFMM_OK;
-}
-
-int levels_finish(sfmm_ctx* c) {
+  SFMM_CUDA_TRY(cudaStreamSynchronize(c->stream));
   // deepest level holding a walkable internal node (-1: none)
   const int nint = c->h_level_pin[SFMM_LEVEL_COPY];
-  c->h_level_off.assign(c->h_level_pin, c->h_level_pin + c->level_ncopy);
+  c->h_level_off.assign(c->h_level_pin, c->h_level_pin + ncopy);
   c->max_depth = -2;
   for (int d = 0; d < (int)c->h_level_off.size(); ++d)
     if (c->h_level_off[d] >= nint) {
@@ -1261,6 +1258,7 @@ int levels_finish(sfmm_ctx* c) {
     }
   if (c->max_depth < -1) return SFMM_ESTACK;
   c->h_level_off.resize(c->max_depth + 2);
+  c->levels_ready = true;
   return SFMM_OK;
 }
 
@@ -1476,7 +1474,10 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   if ((rc = c->Qd.ensure(sizeof(double) * (size_t)nnodes * NQ)) ||
       (rc = c->Qf.ensure(sizeof(float) * (size_t)nnodes * nqs)))
     return rc;
-  if ((rc = levels_issue(c))) return rc;
+  // node depths (exported, and ranks of the one-sided symmetric walk); the
+  // per-depth lists are built when a walk first needs them
+  if ((rc = compute_depth(c))) return rc;
+  c->levels_ready = false;
   switch (P) {
     case 0: rc = geom_upward<0>(c, nqs); break;
     case 1: rc = geom_upward<1>(c, nqs); break;

@@ -642,6 +642,9 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     }
   }
   int rc;
+  // per-depth launches (and the symmetric walk) run over the per-depth lists
+  if (!queue && (rc = ensure_levels(c)))
+    return set_error(c, rc, rc == SFMM_ESTACK ? "tree deeper than supported" : "per-depth node lists failed");
   for (int attempt = 0; attempt < SFMM_WALK_ATTEMPTS; ++attempt) {
     const int nwarps = std::max(max_blocks, q_blocks) * WALK_WARPS;  // one ring per resident warp
     if ((rc = c->ring.ensure(sizeof(int) * (size_t)nwarps * 2 * c->ring_capacity))) return rc;
@@ -663,7 +666,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     }
     if ((rc = c->p2p_off.ensure(sizeof(long long) * (size_t)nl))) return rc;
     if ((rc = c->p2p_cnt.ensure(sizeof(int) * (size_t)nl))) return rc;
-    const int nlev = c->max_depth + 1;  // levels holding internal nodes
+    const int nlev = queue ? 0 : c->max_depth + 1;  // levels holding internal nodes
     if ((rc = c->counters.ensure(sizeof(unsigned long long) * (20 + 2 * (size_t)nlev)))) return rc;
     if ((rc = c->far.ensure((F32 ? sizeof(float4) : 4 * sizeof(double)) * (size_t)c->n))) return rc;
     unsigned long long* ctr = c->counters.as<unsigned long long>();
@@ -726,8 +729,9 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     if (queue) {
       // one launch: a warp takes the next slot of the queue and waits until
       // the parent of the node there has pushed it; the system roots start it
-      const int nint = c->h_level_off[nlev];
-      la.q_total = nint + nl;  // every walkable node, leaves included
+      // every walkable node, leaves included: all nodes but the nsys - 1 that
+      // span several systems (the binary tree above the system roots)
+      la.q_total = nn - (c->nsys - 1);
       if ((rc = c->wqueue.ensure(sizeof(int) * (size_t)(la.q_total + 1)))) return rc;
       la.queue = c->wqueue.as<int>();
       la.q_head = reinterpret_cast<int*>(ctr + 14);
