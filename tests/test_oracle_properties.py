@@ -3,8 +3,8 @@
 Exact invariants of the method as the oracle implements it:
 - scaling every position and smoothing length by 2 scales every rounding
   step by a power of two, so accelerations come out exactly /4 and
-  potentials exactly /2 (Morton keys, opening decisions, kernel pieces and
-  expansions all unchanged);
+  potentials exactly /2 (Morton keys or kd pivots, opening decisions, kernel
+  pieces and expansions all unchanged);
 - scaling every mass by 2 scales accelerations and potentials exactly by 2;
 - permuting the input particles leaves the tree, and so every result,
   unchanged (distinct keys);
@@ -32,26 +32,27 @@ def _system(seed, n, spread):
 
 systems = st.tuples(st.integers(0, 2**31 - 1), st.integers(2, 40), st.sampled_from([0.5, 1.0, 3.0]))
 thetas = st.sampled_from([0.0, 0.3, 0.5, 0.8])
+trees = st.sampled_from(["morton", "kd"])
 orders = st.integers(0, 4)
 leaf_sizes = st.integers(1, 8)
 
 
 @SETTINGS
-@given(systems, thetas, orders, leaf_sizes)
-def test_length_scaling_is_exact(sysargs, theta, p, ls):
+@given(systems, thetas, orders, leaf_sizes, trees)
+def test_length_scaling_is_exact(sysargs, theta, p, ls, tree):
     pos, m, h = _system(*sysargs)
-    a1, p1, _ = oracle.sfmm(pos, m, h, theta=theta, p=p, leaf_size=ls)
-    a2, p2, _ = oracle.sfmm(2.0 * pos, m, 2.0 * h, theta=theta, p=p, leaf_size=ls)
+    a1, p1, _ = oracle.sfmm(pos, m, h, theta=theta, p=p, leaf_size=ls, tree=tree)
+    a2, p2, _ = oracle.sfmm(2.0 * pos, m, 2.0 * h, theta=theta, p=p, leaf_size=ls, tree=tree)
     np.testing.assert_array_equal(a2, a1 / 4.0)
     np.testing.assert_array_equal(p2, p1 / 2.0)
 
 
 @SETTINGS
-@given(systems, thetas, orders, leaf_sizes)
-def test_mass_scaling_is_exact(sysargs, theta, p, ls):
+@given(systems, thetas, orders, leaf_sizes, trees)
+def test_mass_scaling_is_exact(sysargs, theta, p, ls, tree):
     pos, m, h = _system(*sysargs)
-    a1, p1, _ = oracle.sfmm(pos, m, h, theta=theta, p=p, leaf_size=ls)
-    a2, p2, _ = oracle.sfmm(pos, 2.0 * m, h, theta=theta, p=p, leaf_size=ls)
+    a1, p1, _ = oracle.sfmm(pos, m, h, theta=theta, p=p, leaf_size=ls, tree=tree)
+    a2, p2, _ = oracle.sfmm(pos, 2.0 * m, h, theta=theta, p=p, leaf_size=ls, tree=tree)
     np.testing.assert_array_equal(a2, 2.0 * a1)
     np.testing.assert_array_equal(p2, 2.0 * p1)
 
@@ -80,9 +81,9 @@ def test_theta_zero_is_the_direct_sum(sysargs, p, ls):
 
 
 @SETTINGS
-@given(systems, thetas, orders, leaf_sizes)
-def test_momentum_is_conserved(sysargs, theta, p, ls):
+@given(systems, thetas, orders, leaf_sizes, trees)
+def test_momentum_is_conserved(sysargs, theta, p, ls, tree):
     pos, m, h = _system(*sysargs)
-    a, _, _ = oracle.sfmm(pos, m, h, theta=theta, p=p, leaf_size=ls)
+    a, _, _ = oracle.sfmm(pos, m, h, theta=theta, p=p, leaf_size=ls, tree=tree)
     ma = m[:, None] * a
     assert np.linalg.norm(ma.sum(0)) <= 1e-13 * np.abs(ma).sum()
