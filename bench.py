@@ -161,28 +161,56 @@ def _cpu_baseline(pos, m, h, w, budget_s=20.0):
                       "%.1f s), scaled by particles" % (t_build, nl_done, t.nleaves, np_done, t_walk)}
 
 
+REF_SLICES = 8  # each reference step walks one eighth of the leaves
+
+
 def run_reference(args):
+    """The oracle as it stands, timed on the host cores, each step a bounded
+    slice of the headline workload: the full oracle tree build, then
+    Algorithms 1-2 for one eighth of the leaves (a seeded permutation cut in
+    eight; step k takes slice k mod 8).  Every leaf's result depends on the
+    read-only tree alone, so a slice is exact work of the same solve.  value =
+    particles whose forces the timed steps computed / their measured time;
+    ms_per_step = the measured mean step time."""
     ws, rank, local = _dist()
     if rank != 0:
         return 0
+    import oracle
     import workloads
 
     w = WORKLOAD
     pos, m, h = workloads.make(w["gen_name"], n=w["n"], seed=w["seed"])
-    times = []
-    base = None
+    threads = oracle.max_threads()
+    times, parts, builds = [], [], []
+    perm = None
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        base = _cpu_baseline(pos, m, h, w, budget_s=3.0 if it >= args.warmup else 1.0)
+        t = oracle.Tree(pos, m, h, w["leaf_size"], p=w["order"])
+        t1 = time.perf_counter()
+        if perm is None:
+            perm = np.random.default_rng(7).permutation(t.nleaves).astype(np.int32)
+        sel = np.sort(perm[it % REF_SLICES::REF_SLICES])
+        t.sfmm(w["theta"], leaf_sample=sel)
+        dt = time.perf_counter() - t0
         if it >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    value = base["value"]
+            times.append(dt)
+            builds.append(t1 - t0)
+            parts.append(int(t.count[t.leaves[sel]].sum()))
+        del t
+    value = sum(parts) / sum(times)
+    ms = 1e3 * float(np.mean(times))
+    base = {"value": value, "unit": "particles/s", "cores": threads, "kind": "oracle",
+            "sample": "per step: full FP64 oracle tree build of all %d particles (mean %.2f s) + Algorithms 1-2 "
+                      "on one eighth of the leaves (mean %d particles); value = particles computed / measured "
+                      "time over %d timed steps" % (w["n"], float(np.mean(builds)), int(np.mean(parts)),
+                                                     args.steps)}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * w["n"] / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded %s)" % w["gen_name"],
             "config": {"workload": w["name"], "n": w["n"], "theta": w["theta"], "order": w["order"],
-                       "leaf_size": w["leaf_size"], "form": "oracle FP64 (CPU)"},
+                       "leaf_size": w["leaf_size"], "form": "oracle FP64 (CPU)",
+                       "step": "tree build + one eighth of the leaves"},
             "cpu_baseline": base,
             "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -246,31 +274,37 @@ def time_steps(torch, solver, pos_d, m_d, h_d, acc, pot, w, theta, steps, warmup
 def ensemble_block(torch, local, flush, steps):
     """Batched ensemble: 256 independent systems (sizes log-uniform in
     [10^3, 10^5], alternating Plummer / uniform sphere), theta 0.5, p 2:
-    the FP32 form over the whole batch in the same launches, with autotuned
-    leaf sizes, against the FP64 form run system by system."""
+    the FP32 form over the whole batch in the same launches, with leaf sizes
+    and launch knobs from the library's autotuner (timed trials on these
+    systems; the timed builds pass NULL leaf sizes, which take the tuned
+    table), against the FP64 form run system by system."""
     import workloads
     from paper_2602_05804_gb300 import sfmm
-    from paper_2602_05804_gb300.autotune import Autotuner
+    from paper_2602_05804_gb300.autotune import DEFAULT_CACHE, autotuned_solver
 
     pos, m, h, off = workloads.ensemble(1004)
     sizes = np.diff(off)
     nsys, ntot = len(sizes), int(off[-1])
-    profiles = ["plummer" if k % 2 == 0 else "uniform" for k in range(nsys)]
-    tuner = Autotuner()
-    leaf = np.array(tuner.leaf_sizes(sizes, profiles, 0.5, 2, "fp32"), np.int32)
     dev = torch.device("cuda", local)
     pd, md, hd = (torch.from_numpy(x).to(dev) for x in (pos, m, h))
     acc = torch.empty((ntot, 3), dtype=torch.float64, device=dev)
     pot = torch.empty(ntot, dtype=torch.float64, device=dev)
-    sb = sfmm.Solver(local, "fp32")
+    t0 = time.perf_counter()
+    sb, leaf = autotuned_solver(local, "fp32", off, pd, md, hd, 0.5, 2, cache=DEFAULT_CACHE)
+    t_tune = time.perf_counter() - t0
+    try:
+        with open(DEFAULT_CACHE) as f:
+            knobs = json.load(f).get("knobs")
+    except (OSError, ValueError):
+        knobs = None
     for _ in range(2):
-        sfmm.sfmm_build_batch(sb.ctx, off, pd, md, hd, leaf)
+        sfmm.sfmm_build_batch(sb.ctx, off, pd, md, hd, None)
         sfmm.sfmm_gravity_batch(sb.ctx, 0.5, 2, acc, pot)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for k in range(steps):
         _flush(flush)
         ev[k][0].record(sb.stream)
-        sfmm.sfmm_build_batch(sb.ctx, off, pd, md, hd, leaf)
+        sfmm.sfmm_build_batch(sb.ctx, off, pd, md, hd, None)
         sfmm.sfmm_gravity_batch(sb.ctx, 0.5, 2, acc, pot)
         ev[k][1].record(sb.stream)
     torch.cuda.synchronize()
@@ -294,8 +328,121 @@ def ensemble_block(torch, local, flush, steps):
     return {"systems": nsys, "n_total": ntot, "n_min": int(sizes.min()), "n_max": int(sizes.max()),
             "batched_fp32": {"particles_per_s": ntot / (ms_b * 1e-3), "ms_per_step": ms_b, "steps": steps,
                              "leaf_sizes": hist, "max_momentum_residual": float(mom.max())},
+            "autotune": {"seconds": t_tune, "leaf_sizes": hist, "knobs": knobs,
+                         "how": "sfmm_autotune_batch: leaf size per (log2 N, profile class, theta, p, form) and "
+                                "walk schedule / near-field blocks per SM / list chunk per batch, from timed trials"},
             "sequential_fp64": {"particles_per_s": ntot / (ms_s * 1e-3), "ms_per_step": ms_s},
             "speedup": ms_s / ms_b}
+
+
+def measured_peaks(local, stream):
+    """FMA throughput of this GPU measured by the library's own FMA kernel
+    (eight independent chains per thread, every SM full): FP64, FP32 and
+    packed FP32, best of five 50 ms launches each, with the SM clock sampled
+    while it runs.  The FP32 peak is the larger of the scalar and packed
+    rates."""
+    from paper_2602_05804_gb300 import sfmm
+
+    out = {}
+    with ClockSampler(local) as clk:
+        for key, form in (("fp64_tflops", 0), ("fp32_scalar_tflops", 1), ("fp32_packed_tflops", 2)):
+            out[key], _ = sfmm.sfmm_fma_peak(local, form, stream, target_ms=50.0, reps=5)
+    out["fp32_tflops"] = max(out["fp32_scalar_tflops"], out["fp32_packed_tflops"])
+    out["clocks"] = clk.summary()
+    out["how"] = ("sfmm_fma_peak: 152 x 4 blocks of 256 threads, 8 independent FMA chains per thread, "
+                  "best of 5 launches of ~50 ms, CUDA events")
+    return out
+
+
+def _acc_rel(acc, ref):
+    """|da| / max(|a|, 1e-3 rms |a|) per particle (the parity tests' metric)."""
+    an = np.linalg.norm(ref, axis=1)
+    floor = 1e-3 * np.sqrt((an**2).mean())
+    return np.linalg.norm(acc - ref, axis=1) / np.maximum(an, floor)
+
+
+def _err_stats(e):
+    return {"rms": float(np.sqrt((e**2).mean())), "max": float(e.max()), "mean": float(e.mean())}
+
+
+def oracle_error_block(pos, m, h, w, results, nleaf=96, ntarget=4096):
+    """Error of each form against the FP64 oracle, per result: accelerations
+    and potentials on a seeded sample of leaves (the oracle runs Algorithms
+    1-2 for those leaves only: exact, since a leaf's result depends on the
+    read-only tree alone), plus the momentum residual over all particles.
+    Also each form's, and the oracle's, force error against the softened
+    direct sum on seeded targets: the truncation error both forms share,
+    which is what "equal force accuracy" compares."""
+    import oracle
+
+    t0 = time.perf_counter()
+    t = oracle.Tree(pos, m, h, w["leaf_size"], p=w["order"])
+    rng = np.random.default_rng(11)
+    sel = np.unique(np.concatenate([rng.choice(t.nleaves, min(nleaf, t.nleaves), replace=False),
+                                    [0, t.nleaves - 1]])).astype(np.int32)
+    a_o, p_o, _ = t.sfmm(w["theta"], leaf_sample=sel)
+    idx = np.concatenate([t.perm[t.first[L]:t.first[L] + t.count[L]] for L in t.leaves[sel]])
+    tg = np.sort(rng.choice(len(m), min(ntarget, len(m)), replace=False))
+    a_d, _ = oracle.direct(pos, m, h, targets=tg)
+    leaf_of = np.empty(len(m), np.int64)
+    for q, L in enumerate(t.leaves):
+        leaf_of[t.perm[t.first[L]:t.first[L] + t.count[L]]] = q
+    a_ot, _, _ = t.sfmm(w["theta"], leaf_sample=np.unique(leaf_of[tg]).astype(np.int32))
+    an = np.linalg.norm(a_d, axis=1)
+    out = {"sample": "%d leaves (%d particles) vs the oracle; %d seeded targets vs the direct sum"
+                     % (len(sel), len(idx), len(tg)),
+           "oracle_vs_direct": _err_stats(np.linalg.norm(a_ot[tg] - a_d, axis=1) / an)}
+    for form, (acc, pot, st) in results.items():
+        ep = np.abs(pot[idx] - p_o[idx]) / np.abs(p_o[idx])
+        out[form] = {"acc_rel_vs_oracle": _err_stats(_acc_rel(acc[idx], a_o[idx])),
+                     "pot_rel_vs_oracle": _err_stats(ep),
+                     "momentum_residual": float(np.linalg.norm(st["momentum"]) / st["abs_momentum"]),
+                     "acc_rel_vs_direct": _err_stats(np.linalg.norm(acc[tg] - a_d, axis=1) / an)}
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
+def uniform_1e4_block(torch, local, flush, steps):
+    """The small configuration: uniform sphere, N = 10^4, theta 0.5, leaf 10,
+    p 2.  Both forms on the GPU against the full FP64 oracle (every particle)
+    and the full softened direct sum; the oracle and the direct sum timed on
+    the host cores."""
+    import oracle
+    import workloads
+    from paper_2602_05804_gb300 import sfmm
+
+    name = "uniform_1e4"
+    wk = dict(workloads.WORKLOADS[name], order=2)
+    pos, m, h = workloads.make(name)
+    n = len(m)
+    t0 = time.perf_counter()
+    a_o, p_o, st_o = oracle.sfmm(pos, m, h, theta=wk["theta"], p=2, leaf_size=wk["leaf_size"])
+    t_oracle = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    a_d, p_d = oracle.direct(pos, m, h)
+    t_direct = time.perf_counter() - t0
+    an = np.linalg.norm(a_d, axis=1)
+    dev = torch.device("cuda", local)
+    pd, md, hd = (torch.from_numpy(x).to(dev) for x in (pos, m, h))
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    pot = torch.empty(n, dtype=torch.float64, device=dev)
+    out = {"n": n, "theta": wk["theta"], "leaf_size": wk["leaf_size"], "order": 2,
+           "oracle": {"seconds": t_oracle, "particles_per_s": n / t_oracle, "cores": oracle.max_threads(),
+                      "m2l": st_o["m2l"], "p2p_pairs": st_o["p2p_pairs"],
+                      "acc_rel_vs_direct": _err_stats(np.linalg.norm(a_o - a_d, axis=1) / an)},
+           "direct_seconds": t_direct}
+    for prec in ("fp64", "fp32"):
+        s = sfmm.Solver(local, prec, profile=1)
+        ms, st = time_steps(torch, s, pd, md, hd, acc, pot, wk, wk["theta"], steps, 3, flush)
+        s.close()
+        a, p = acc.cpu().numpy(), pot.cpu().numpy()
+        out[prec] = {"ms_per_step": float(np.mean(ms)), "particles_per_s": n / (np.mean(ms) * 1e-3),
+                     "counts_equal_oracle": bool(st["m2l"] == st_o["m2l"] and st["p2p_pairs"] == st_o["p2p_pairs"]),
+                     "acc_rel_vs_oracle": _err_stats(_acc_rel(a, a_o)),
+                     "pot_rel_vs_oracle": _err_stats(np.abs(p - p_o) / np.abs(p_o)),
+                     "acc_rel_vs_direct": _err_stats(np.linalg.norm(a - a_d, axis=1) / an),
+                     "momentum_residual": float(np.linalg.norm(st["momentum"]) / st["abs_momentum"])}
+    return out
 
 
 M2L_FLOPS_P2 = 136       # FP32 M2L at p = 2 without the dipole terms (counted from the kernel source)
@@ -452,6 +599,16 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    if args.only == "fp64":
+        ms64, st64 = time_steps(torch, s64, pos_d, m_d, h_d, acc, pot, w, w["theta"], args.steps, args.warmup, flush)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": w["n"] / (np.mean(ms64) * 1e-3), "unit": "particles/s",
+                              "n_gpus": ws, "ms_per_step": float(np.mean(ms64)),
+                              "stage_ms": {k: st64[k] for k in ("ms_build", "ms_moments", "ms_walk", "ms_p2p")},
+                              "partial": "FP64 form step only (for profiler launch lists)"}))
+        s32.close()
+        s64.close()
+        return 0
     # headline: FP32 form, theta = 0.5, whole step, max over ranks
     barrier()
     with ClockSampler(local) as clk:
@@ -463,6 +620,7 @@ def run_gpu(args):
     value = n_all / (step_ms * 1e-3)
     inter = st32["p2p_pairs"] + st32["m2l_unique"]
 
+    res_fp32 = (acc.cpu().numpy(), pot.cpu().numpy(), st32)
     if args.only == "fp32":
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
@@ -476,6 +634,8 @@ def run_gpu(args):
     k64 = max(1, min(args.steps, 3))
     ms64, st64 = time_steps(torch, s64, pos_d, m_d, h_d, acc, pot, w, w["theta"], k64, 1, flush)
     fp64_ms = float(np.mean(ms64))
+    res_fp64 = (acc.cpu().numpy(), pot.cpu().numpy(), st64)
+    peaks_meas = measured_peaks(local, s32.stream.cuda_stream)
     # theta sweep of the FP32 form
     sweep = {}
     for th in (0.3, 0.7):
@@ -527,7 +687,9 @@ def run_gpu(args):
 
     peaks, peak_kind = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, unit counts x max clock
+    fp32_unit_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, unit counts x max clock
+    fp32_peak = peaks_meas["fp32_tflops"]
+    fp64_peak = peaks_meas["fp64_tflops"]
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     leapfrog = None if args.no_leapfrog else leapfrog_block(torch, local)
     accuracy = None if args.no_accuracy else accuracy_sweep_block(torch, local, trees=("morton", "kd"))
@@ -559,6 +721,10 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
 
+    oracle_err = None if args.no_oracle_error else oracle_error_block(pos, m, h, w, {"fp32": res_fp32,
+                                                                                      "fp64": res_fp64})
+    small = None if args.no_configs else uniform_1e4_block(torch, local, flush, max(3, min(args.steps, 10)))
+
     # roofline of the dominant kernel
     clocks = clk.summary()
     shares = {"walk": st32["ms_walk"], "p2p": st32["ms_p2p"], "build": st32["ms_build"],
@@ -576,9 +742,19 @@ def run_gpu(args):
         src = _kernel_hash("walk_shared.cu" if args.walk >= 1 else "walk.cu", "walk_common.cuh", "expansion_gen.cuh")
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": _traffic(kname, src),
-            "peak_source": "FP32 FMA units: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock, %s peaks file)"
-                           % (sm_max, peak_kind),
-            "ms_per_launch": kms, "stage_ms": shares}
+            "peak_source": "measured: FP32 FMA throughput of sfmm_fma_peak in this run (max of scalar and packed)",
+            "peak_unit_count": fp32_unit_peak, "frac_of_unit_count": achieved / fp32_unit_peak,
+            "ms_per_launch": kms, "stage_ms": shares,
+            "work": ({"p2p_pairs": st32["p2p_pairs"], "flops_per_pair": FLOPS_PER_PAIR}
+                     if kname.startswith("k_p2p") else {"m2l": nm2l, "flops_per_m2l": M2L_FLOPS_P2})}
+    p64_ach = st64["p2p_pairs"] * FLOPS_PER_PAIR / (st64["ms_p2p"] * 1e-3) / 1e12
+    roof64 = {"kernel": "k_p2p<FP64>", "bound": "alu", "achieved": p64_ach, "peak": fp64_peak, "unit": "TFLOP/s",
+              "frac": p64_ach / fp64_peak, "traffic": _traffic("k_p2p<FP64>", _kernel_hash("p2p.cu")),
+              "peak_source": "measured: FP64 FMA throughput of sfmm_fma_peak in this run",
+              "ms_per_launch": st64["ms_p2p"],
+              "work": {"p2p_pairs": st64["p2p_pairs"], "flops_per_pair": FLOPS_PER_PAIR},
+              "stage_ms": {"walk": st64["ms_walk"], "p2p": st64["ms_p2p"], "build": st64["ms_build"],
+                           "moments": st64["ms_moments"]}}
 
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
@@ -596,6 +772,11 @@ def run_gpu(args):
                    "mac_fallbacks": st32["mac_fallbacks"], "nleaves": st32["nleaves"]},
         "fp64_form": {"particles_per_s": ws * w["n"] / (fp64_ms * 1e-3), "ms_per_step": fp64_ms,
                       "speedup_fp32_over_fp64": fp64_ms / step_ms,
+                      "speedup_at": ("same theta, p and tree: equal force accuracy, since both forms share the "
+                                     "truncation error against the direct sum (oracle_error.*.acc_rel_vs_direct)"),
+                      "acc_rel_vs_direct_mean": (None if oracle_err is None else
+                                                 {f: oracle_err[f]["acc_rel_vs_direct"]["mean"]
+                                                  for f in ("fp32", "fp64")}),
                       "stage_ms": {"walk": st64["ms_walk"], "p2p": st64["ms_p2p"], "build": st64["ms_build"]}},
         "momentum_residual": {"fp32": float(np.linalg.norm(st32["momentum"]) / st32["abs_momentum"]),
                               "fp64": float(np.linalg.norm(st64["momentum"]) / st64["abs_momentum"])},
@@ -612,6 +793,10 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(w["n"] * 40), "d2h_bytes_per_step": int(w["n"] * 32)},
         "gpu_launches": int(st32["kernel_launches_per_step"] * args.steps),
         "roofline": roof,
+        "roofline_fp64": roof64,
+        "measured_peaks": peaks_meas,
+        "oracle_error": oracle_err,
+        "uniform_1e4": small,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
     }
@@ -648,8 +833,10 @@ def main():
                          "2 one-sided symmetric pairs")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2],
                     help="walk 1 node order: 0 automatic (default), 1 one launch per depth, 2 readiness queue")
-    ap.add_argument("--only", default="all", choices=["all", "fp32"],
-                    help="fp32: time the headline FP32 step only (for profiler launch lists)")
+    ap.add_argument("--only", default="all", choices=["all", "fp32", "fp64"],
+                    help="fp32 / fp64: time the headline step of that form only (for profiler launch lists)")
+    ap.add_argument("--no-oracle-error", action="store_true",
+                    help="skip the per-result error against the oracle and the direct sum")
     args = ap.parse_args()
     if args.workload != "plummer_1e6":
         import workloads

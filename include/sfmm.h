@@ -121,6 +121,12 @@ int sfmm_set_stream(sfmm_ctx* ctx, void* stream);
  *   "tree"           0 (default): binary radix tree over Morton keys (Sect. 3);
  *                    1: centre-of-mass-pivot kd tree (Sect. 3; single
  *                    systems only, sfmm_build_batch returns ENOTIMPL)
+ *   "p2p_chunk"      neighbour-list entries per near-field work item: longer
+ *                    lists are cut into chunks evaluated as separate items
+ *                    and recombined in chunk order (default 256, 32..65536)
+ *   "p2p_blocks"     near-field blocks per SM (0, default: as many as fit)
+ *   "autotune_theta", "autotune_order"  theta and order that autotuned leaf
+ *                    sizes are chosen for (sfmm_build_batch with NULL sizes)
  *   "profile"        1 records per-stage device times into the stats
  * Errors: EINVAL (unknown key or out-of-range value). */
 int sfmm_set_option(sfmm_ctx* ctx, const char* key, double value);
@@ -155,7 +161,8 @@ int sfmm_build(sfmm_ctx* ctx, int64_t n, const double* pos, const double* mass, 
 int sfmm_gravity(sfmm_ctx* ctx, double theta, int order, double* acc, double* pot);
 
 /* Build one tree over a batch of nsys independent particle systems packed
- * back to back (survey row S10; not in the paper): system s owns particles
+ * back to back (an ensemble service; the paper solves one particle set at a
+ * time): system s owns particles
  * [offsets[s], offsets[s+1]).  Each system gets its own bounding box, Morton
  * keys and leaf size; the combined sort orders particles by (system, key,
  * input index) and nodes spanning several systems are always split and never
@@ -165,10 +172,48 @@ int sfmm_gravity(sfmm_ctx* ctx, double theta, int order, double* acc, double* po
  *   nsys in [1, 65536];  offsets HOST, nsys + 1 int64, offsets[0] = 0,
  *   strictly increasing, offsets[nsys] = total n <= 2^31 - 2;
  *   pos/mass/h device, packed as for sfmm_build;
- *   leaf_size HOST, nsys ints in [1, 64], or NULL for 16 everywhere.
+ *   leaf_size HOST, nsys ints in [1, 64], or NULL: autotuned.  With NULL
+ *             every system takes the leaf size the context's autotuner table
+ *             holds for its (size bucket floor(log2 N), profile class, theta,
+ *             order, form), theta and order being the options
+ *             "autotune_theta" / "autotune_order" (default 0.5 / 2, set by
+ *             sfmm_autotune_batch); groups of systems without an entry are
+ *             timed first (see sfmm_autotune_batch), so a first NULL call
+ *             takes longer.  The batch's cached launch knobs (walk schedule,
+ *             near-field blocks per SM and list chunk) are applied too, when
+ *             the table has them.
  * Errors: as sfmm_build. */
 int sfmm_build_batch(sfmm_ctx* ctx, int nsys, const int64_t* offsets, const double* pos, const double* mass,
                      const double* h, const int* leaf_size);
+
+/* Autotune a batch (an ensemble service; the paper has no counterpart) and
+ * build it: every system's leaf size and the batch's launch knobs are picked
+ * from timed trials on the caller's own systems at this theta and order, in
+ * this context's arithmetic form.
+ *   Leaf size in {8, 16, 32, 64} per (size bucket floor(log2 N), profile
+ *   class, theta, order, form); the profile class is cut from the ratio of the
+ *   rms to the mean distance from the system's centre of mass (<1.1: 0, e.g. a
+ *   homogeneous sphere; <1.25: 1; <1.6: 2, e.g. a Plummer sphere; else 3).
+ *   One trial per group without a table entry: the system nearest the group's
+ *   median size, built and solved with each candidate in a scratch context
+ *   (best of two timed runs after a warm-up run, CUDA events).
+ *   Launch knobs per (total-size bucket, log2 nsys, theta, order, form): walk
+ *   "schedule" {1, 2} x "p2p_blocks" {all that fit, one fewer} x "p2p_chunk"
+ *   {128, 256, 512}, each timed on a gravity call of the whole batch; the
+ *   best are set as this context's options.
+ * Arguments as sfmm_build_batch (leaf sizes are chosen, not given) plus
+ * theta and order as sfmm_gravity; leaf_size_out HOST nsys ints or NULL
+ * receives the chosen leaf sizes.  The batch is built on return (call
+ * sfmm_gravity_batch next); "autotune_theta"/"autotune_order" are set to
+ * theta/order.  Errors: as sfmm_build_batch and sfmm_gravity. */
+int sfmm_autotune_batch(sfmm_ctx* ctx, int nsys, const int64_t* offsets, const double* pos, const double* mass,
+                        const double* h, double theta, int order, int* leaf_size_out);
+
+/* Cache file of the context's autotuner table (JSON): entries in the file
+ * are loaded now (a missing file is an empty table) and the file is
+ * rewritten whenever a trial adds an entry.  NULL or "" stops caching.
+ * Errors: EINVAL (file not writable when an entry is added). */
+int sfmm_autotune_cache(sfmm_ctx* ctx, const char* path);
 
 /* Gravity of every system of the last build (batch or single), same
  * arguments, layout (packed caller order) and errors as sfmm_gravity. */
@@ -254,32 +299,46 @@ int sfmm_leapfrog(sfmm_ctx* ctx, int64_t n, double* pos, double* vel, const doub
 
 /* Momentum and energy sums of a particle set WITHOUT ANY DEVICE ALLOCATION:
  * out[0..2] = sum_i m_i a_i, out[3] = sum_i sum_d |m_i a_i,d|,
- * out[4] = 1/2 sum_i m_i Phi_i (0 when pot is NULL) -- the same sums that
- * sfmm_get_stats reports after sfmm_gravity, here over caller arrays.  The
- * paper has no counterpart: this is a service for callers that cannot call
- * cudaMalloc, such as code that must draw all device memory from its own
- * pre-reserved pool or must not change the device's memory footprint once it
- * is running.  No context is needed and nothing is allocated, freed or taken
- * from a library allocator.
+ * out[4] = 1/2 sum_i m_i Phi_i (0 when pot is NULL) -- the same compensated
+ * (Neumaier) sums that sfmm_get_stats reports after sfmm_gravity, here over
+ * caller arrays.  The paper has no counterpart: this is a service for callers
+ * that cannot call cudaMalloc, such as code that must draw all device memory
+ * from its own pre-reserved pool or must not change the device's memory
+ * footprint once it is running.  No context is needed and nothing is
+ * allocated, freed or taken from a library allocator.
  *   n     number of particles, 1 <= n <= SFMM_NOALLOC_MAX_N (larger n is
  *         rejected with SFMM_EINVAL);
  *   mass  device, n float64;  acc device, n x 3 float64;  pot device, n
  *         float64 or NULL;  out device, 5 float64, written;
  *   stream  cudaStream_t to run on (NULL: the default stream), on the
  *         current device.
- * Scratch: per-tile partial sums (one per 4096 particles) in a fixed 640 KB
+ * Scratch: per-tile partial sums (one per 4096 particles) in a fixed 1.25 MB
  * array of device memory inside this library, which every GPU that loads the
  * library holds until the process exits.  Every call shares that array, which
  * keeps the last call's contents; each call writes every partial it reads, so
  * nothing needs clearing.  Each GPU has its own copy of the array; calls that
  * overlap on the same GPU (for example on two streams) race on the partials,
- * so serialise them.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Unlike the other entry points this call
- * does not synchronise: out is ready when the stream reaches it.
+ * so serialise them.  The first call in a CUDA context looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  The address is cached per device
+ * and context: after cudaDeviceReset (a new context) the next call looks it
+ * up again.  Unlike the other entry points this call does not synchronise:
+ * out is ready when the stream reaches it.
  * Errors: EINVAL (n out of range, NULL pointer), ECUDA. */
 int sfmm_reduce_noalloc(int64_t n, const double* mass, const double* acc, const double* pot, double* out,
                         void* stream);
+
+/* Measured fused-multiply-add throughput of device `device` (a measurement
+ * aid for the arithmetic rooflines of the near-field and M2L kernels; the
+ * paper has no counterpart).  A kernel of eight independent FMA chains per
+ * thread, 32 warps on every SM, in form
+ *   0: FP64 fma,  1: FP32 fma,  2: packed FP32 (two fmas per instruction),
+ * calibrated to last about target_ms (0 < target_ms <= 1000) per launch and
+ * timed with CUDA events on `stream` (cudaStream_t, NULL: default stream);
+ * the best of `reps` launches (1..1000) gives *tflops (2 flops per fma) and
+ * *ms (its duration; may be NULL).  Allocates a small scratch buffer for the
+ * duration of the call.  Errors: EINVAL (bad argument or device), ECUDA. */
+int sfmm_fma_peak(int device, int form, void* stream, double target_ms, int reps, double* tflops, double* ms);
 
 /* Message describing an error code. */
 const char* sfmm_strerror(int code);

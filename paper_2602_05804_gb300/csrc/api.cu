@@ -168,7 +168,7 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->Qf, &c->ring, &c->far, &c->arena, &c->p2p_off, &c->p2p_cnt, &c->counters,
                     &c->red_part, &c->dump, &c->nlu, &c->level_nodes, &c->level_off, &c->level_cur,
                     &c->cf_arena, &c->cf_off, &c->cf_cnt, &c->Tnode, &c->leaf_order, &c->sys_off,
-                    &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_leaf_off, &c->sys_sums,
+                    &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_sums,
                     &c->p2p_extra, &c->p2p_split, &c->p2p_slist, &c->p2p_part, &c->lf_acc, &c->lf_part,
                     &c->kd_ord, &c->kd_node, &c->kd_act, &c->kd_work, &c->kd_chunk, &c->kd_part, &c->kd_split,
                     &c->sym_own, &c->sym_recv, &c->wqueue, &c->sort_aux, &c->n_extv, &c->n_exti, &c->n_lb, &c->size_cand};
@@ -182,6 +182,7 @@ void sfmm_destroy(sfmm_ctx* c) {
   if (c->h_level_pin) cudaFreeHost(c->h_level_pin);
   if (c->h_sys_pin) cudaFreeHost(c->h_sys_pin);
   if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
+  tune_table_free(c);
   delete c;
 }
 
@@ -225,6 +226,19 @@ int sfmm_set_option(sfmm_ctx* c, const char* key, double v) {
     if (v != 0.0 && v != 1.0 && v != 2.0)
       return set_error(c, SFMM_EINVAL, "schedule: 0 (automatic), 1 (one launch per depth), 2 (readiness queue)");
     c->schedule = (int)v;
+  } else if (!strcmp(key, "p2p_chunk")) {
+    if (v != std::floor(v) || v < 32 || v > 65536)
+      return set_error(c, SFMM_EINVAL, "p2p_chunk: integer in [32, 65536]");
+    c->p2p_chunk = (int)v;
+  } else if (!strcmp(key, "p2p_blocks")) {
+    if (v != std::floor(v) || v < 0 || v > 64) return set_error(c, SFMM_EINVAL, "p2p_blocks: integer in [0, 64]");
+    c->p2p_blocks = (int)v;
+  } else if (!strcmp(key, "autotune_theta")) {
+    if (!(v >= 0.0 && v < 1.0)) return set_error(c, SFMM_EINVAL, "autotune_theta must be in [0, 1)");
+    c->tune_theta = v;
+  } else if (!strcmp(key, "autotune_order")) {
+    if (v != std::floor(v) || v < 0 || v > SFMM_PMAX) return set_error(c, SFMM_EINVAL, "autotune_order must be in [0, 4]");
+    c->tune_order = (int)v;
   } else if (!strcmp(key, "tree")) {
     if (v != 0.0 && v != 1.0) return set_error(c, SFMM_EINVAL, "tree: 0 (Morton radix tree) or 1 (centre-of-mass kd tree)");
     c->tree_kind = (int)v;
@@ -328,12 +342,43 @@ int sfmm_build_batch(sfmm_ctx* c, int nsys, const int64_t* offsets, const double
       lsz[s] = leaf_size[s];
     }
   DeviceGuard g(c->device);
+  if (!leaf_size) {
+    // autotuned: table entries, trials for groups without one
+    c->built = false;
+    int rc = tuned_leaf_sizes(c, nsys, offsets, pos, mass, h, c->tune_theta, c->tune_order, lsz);
+    if (rc) return set_error(c, rc, c->last_error.empty() ? "autotune failed" : c->last_error.c_str());
+  }
   c->n = n;
   c->leaf_size = *std::max_element(lsz.begin(), lsz.end());
   c->nsys = nsys;
   c->h_sys_off.assign(offsets, offsets + nsys + 1);
   c->h_sys_lsz = lsz;
-  return build_common(c, pos, mass, h);
+  int rc = build_common(c, pos, mass, h);
+  // autotuned builds also take the batch's cached launch knobs, if any
+  if (rc == SFMM_OK && !leaf_size) rc = tuned_knobs(c, c->tune_theta, c->tune_order, nullptr, false);
+  return rc;
+}
+
+int sfmm_autotune_cache(sfmm_ctx* c, const char* path) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  return tune_set_cache(c, path);
+}
+
+int sfmm_autotune_batch(sfmm_ctx* c, int nsys, const int64_t* offsets, const double* pos, const double* mass,
+                        const double* h, double theta, int order, int* leaf_size_out) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (!(theta >= 0.0 && theta < 1.0)) return set_error(c, SFMM_EINVAL, "theta must be in [0, 1)");
+  if (order < 0 || order > SFMM_PMAX) return set_error(c, SFMM_EINVAL, "order must be in [0, 4]");
+  c->tune_theta = theta;
+  c->tune_order = order;
+  int rc = sfmm_build_batch(c, nsys, offsets, pos, mass, h, nullptr);
+  if (rc) return rc;
+  DeviceGuard g(c->device);
+  if ((rc = c->out_acc.ensure(sizeof(double) * 3 * (size_t)c->n))) return set_error(c, rc, "allocation failed");
+  if ((rc = tuned_knobs(c, theta, order, c->out_acc.as<double>(), true)))
+    return set_error(c, rc, c->last_error.empty() ? "autotune failed" : c->last_error.c_str());
+  if (leaf_size_out) std::copy(c->h_sys_lsz.begin(), c->h_sys_lsz.end(), leaf_size_out);
+  return SFMM_OK;
 }
 
 int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot) {

@@ -32,22 +32,32 @@ __global__ void k_kick_drift(int64_t n, double* __restrict__ pos, double* __rest
   pos[k] = dadd(pos[k], dmul(v, dt));
 }
 
-__device__ __forceinline__ void block_sum7(double (&s)[LF_NSUM], double (*sh)[LF_NT]) {
+// Compensated (Neumaier) merge of one partial per thread: sh holds s then c.
+__device__ __forceinline__ void block_sum7(csum (&s)[LF_NSUM], double (*sh)[LF_NT]) {
 #pragma unroll
-  for (int c = 0; c < LF_NSUM; ++c) sh[c][threadIdx.x] = s[c];
+  for (int c = 0; c < LF_NSUM; ++c) {
+    sh[c][threadIdx.x] = s[c].s;
+    sh[LF_NSUM + c][threadIdx.x] = s[c].c;
+  }
   __syncthreads();
   for (int w = LF_NT / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
-      for (int c = 0; c < LF_NSUM; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+      for (int c = 0; c < LF_NSUM; ++c) {
+        csum a{sh[c][threadIdx.x], sh[LF_NSUM + c][threadIdx.x]};
+        cs_merge(a, sh[c][threadIdx.x + w], sh[LF_NSUM + c][threadIdx.x + w]);
+        sh[c][threadIdx.x] = a.s;
+        sh[LF_NSUM + c][threadIdx.x] = a.c;
+      }
     __syncthreads();
   }
 }
 
-// Per-tile partial sums of m v, m x cross v and |m v_d| (fixed order).
+// Per-tile compensated partial sums of m v, m x cross v and |m v_d| (fixed
+// order): 2 x LF_NSUM doubles per tile (sums, then their error terms).
 __global__ void k_momentum_tiles(int64_t n, const double* __restrict__ pos, const double* __restrict__ vel,
                                  const double* __restrict__ mass, double* __restrict__ part) {
-  __shared__ double sh[LF_NSUM][LF_NT];
-  double s[LF_NSUM] = {0, 0, 0, 0, 0, 0, 0};
+  __shared__ double sh[2 * LF_NSUM][LF_NT];
+  csum s[LF_NSUM] = {};
   const int64_t base = (int64_t)blockIdx.x * LF_TILE;
   for (int k = threadIdx.x; k < LF_TILE; k += LF_NT) {
     const int64_t i = base + k;
@@ -55,25 +65,28 @@ __global__ void k_momentum_tiles(int64_t n, const double* __restrict__ pos, cons
     const double m = mass[i];
     const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
     const double px = m * vel[3 * i], py = m * vel[3 * i + 1], pz = m * vel[3 * i + 2];
-    s[0] += px;
-    s[1] += py;
-    s[2] += pz;
-    s[3] += y * pz - z * py;
-    s[4] += z * px - x * pz;
-    s[5] += x * py - y * px;
-    s[6] += fabs(px) + fabs(py) + fabs(pz);
+    cs_add(s[0], px);
+    cs_add(s[1], py);
+    cs_add(s[2], pz);
+    cs_add(s[3], y * pz - z * py);
+    cs_add(s[4], z * px - x * pz);
+    cs_add(s[5], x * py - y * px);
+    cs_add(s[6], fabs(px));
+    cs_add(s[6], fabs(py));
+    cs_add(s[6], fabs(pz));
   }
   block_sum7(s, sh);
-  if (threadIdx.x < LF_NSUM) part[(int64_t)LF_NSUM * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < 2 * LF_NSUM) part[(int64_t)2 * LF_NSUM * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 __global__ void k_momentum_final(int ntiles, const double* __restrict__ part, double* __restrict__ out) {
-  __shared__ double sh[LF_NSUM][LF_NT];
-  double s[LF_NSUM] = {0, 0, 0, 0, 0, 0, 0};
+  __shared__ double sh[2 * LF_NSUM][LF_NT];
+  csum s[LF_NSUM] = {};
   for (int t = threadIdx.x; t < ntiles; t += LF_NT)
-    for (int c = 0; c < LF_NSUM; ++c) s[c] += part[(int64_t)LF_NSUM * t + c];
+    for (int c = 0; c < LF_NSUM; ++c)
+      cs_merge(s[c], part[(int64_t)2 * LF_NSUM * t + c], part[(int64_t)2 * LF_NSUM * t + LF_NSUM + c]);
   block_sum7(s, sh);
-  if (threadIdx.x < LF_NSUM) out[threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < LF_NSUM) out[threadIdx.x] = cs_value(csum{sh[threadIdx.x][0], sh[LF_NSUM + threadIdx.x][0]});
 }
 
 int blocks3(int64_t n) { return (int)((3 * n + LF_NT - 1) / LF_NT); }
@@ -95,7 +108,7 @@ int record_state(sfmm_ctx* c, int64_t n, const double* pos, const double* vel, c
                  double* rec) {
   const int ntiles = (int)((n + LF_TILE - 1) / LF_TILE);
   double* part = c->lf_part.as<double>();
-  double* out = part + (size_t)LF_NSUM * ntiles;
+  double* out = part + (size_t)2 * LF_NSUM * ntiles;
   k_momentum_tiles<<<ntiles, LF_NT, 0, c->stream>>>(n, pos, vel, mass, part);
   k_momentum_final<<<1, LF_NT, 0, c->stream>>>(ntiles, part, out);
   c->nlaunch += 2;
@@ -125,7 +138,7 @@ extern "C" int sfmm_leapfrog(sfmm_ctx* c, int64_t n, double* pos, double* vel, c
   int rc;
   const int ntiles = (int)((n + LF_TILE - 1) / LF_TILE);
   if ((rc = c->lf_acc.ensure(sizeof(double) * 3 * (size_t)n)) ||
-      (rc = c->lf_part.ensure(sizeof(double) * LF_NSUM * ((size_t)ntiles + 1))))
+      (rc = c->lf_part.ensure(sizeof(double) * 2 * LF_NSUM * ((size_t)ntiles + 1))))
     return set_error(c, rc, "leapfrog allocation failed");
   double* a = c->lf_acc.as<double>();
   if ((rc = sfmm_build(c, n, pos, mass, h, leaf_size))) return rc;

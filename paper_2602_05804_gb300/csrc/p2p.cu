@@ -46,7 +46,6 @@ struct P2PArgs {
   int* leaf_counter;
   double* acc;
   double* pot;
-  double* leafsum;  // nleaves x 5: sum m a (3), sum |m a|, sum m Phi
   // long lists: work items [0, nextra) are the further chunks (leaf, chunk)
   // of split lists, items [nextra, nextra + nleaves) the first chunk of every
   // leaf; a split leaf's chunk k writes its sums to partial slot split[leaf] + k
@@ -56,6 +55,7 @@ struct P2PArgs {
   const int* slist;   // the split leaves
   void* part;         // [slot][lmax][4] partial sums in the form's type
   int lmax;
+  int chunk;          // neighbour-list entries per work item of a split list
   unsigned long long* pair_counter;  // pair evaluations (statistics)
 };
 
@@ -152,10 +152,10 @@ __device__ __forceinline__ void pair_cand(R xi, R yi, R zi, R hinvi, R h2i, bool
 
 template <bool F32> __host__ __device__ constexpr int p2p_warps() { return F32 ? P2P_WARPS : P2P_WARPS / 2; }
 
-// Near sums v (a, Phi) of sorted particle i plus its far field: scaled by G,
-// written in caller order, added to the leaf's momentum and energy sums.
+// Near sums v (a, Phi) of sorted particle i plus its far field: scaled by G
+// and written in caller order.
 template <bool F32, typename R>
-__device__ __forceinline__ void p2p_finish(const P2PArgs& a, int i, const R (&v)[4], double (&sm)[5]) {
+__device__ __forceinline__ void p2p_finish(const P2PArgs& a, int i, const R (&v)[4]) {
   double f[4];
   if constexpr (F32) {
     const float4 fr = a.far32[i];
@@ -167,23 +167,12 @@ __device__ __forceinline__ void p2p_finish(const P2PArgs& a, int i, const R (&v)
 #pragma unroll
     for (int c = 0; c < 4; ++c) f[c] = v[c] + a.far64[4 * (size_t)i + c];
   }
-  const double m = a.pm[i];
   double pot = a.G * f[3];
-  if (a.self_pot) pot += a.G * m * (-1.4 / a.ph[i]);
+  if (a.self_pot) pot += a.G * a.pm[i] * (-1.4 / a.ph[i]);
   const int o = a.perm[i];
-  double am[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double acc = a.G * f[c];
-    a.acc[3 * (size_t)o + c] = acc;
-    am[c] = m * acc;
-  }
+  for (int c = 0; c < 3; ++c) a.acc[3 * (size_t)o + c] = a.G * f[c];
   if (a.pot) a.pot[o] = pot;
-  sm[0] += am[0];
-  sm[1] += am[1];
-  sm[2] += am[2];
-  sm[3] += fabs(am[0]) + fabs(am[1]) + fabs(am[2]);
-  sm[4] += m * pot;
 }
 
 // One warp per target leaf.  Sources: the particles of the leaf's neighbour
@@ -256,8 +245,8 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
     R ax0 = R(0), ay0 = R(0), az0 = R(0), pt0 = R(0);
     R ax1 = R(0), ay1 = R(0), az1 = R(0), pt1 = R(0);
 
-    const long long off = a.p2p_off[leaf] + (long long)chunk * SFMM_P2P_CHUNK;
-    const int cnt = (pslot < 0) ? a.p2p_cnt[leaf] : min(SFMM_P2P_CHUNK, a.p2p_cnt[leaf] - chunk * SFMM_P2P_CHUNK);
+    const long long off = a.p2p_off[leaf] + (long long)chunk * a.chunk;
+    const int cnt = (pslot < 0) ? a.p2p_cnt[leaf] : min(a.chunk, a.p2p_cnt[leaf] - chunk * a.chunk);
     int nfar = 0, nnear = 0;
     int e = 0;                 // next list entry to load
     int tot = 0, pdone = 0;    // particles of the loaded entries / staged so far
@@ -607,7 +596,6 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
     if (!on1) { ax1 = ay1 = az1 = pt1 = R(0); }
 
     // combine the phases of each target, add the far field, write out
-    double sm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int slot = 0; slot < 2; ++slot) {
       if (slot == 1 && nL <= 32) break;
       s_red[warp][0][lane] = slot ? ax1 : ax0;
@@ -625,7 +613,7 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
           v[c] = sacc;
         }
         if (pslot < 0) {
-          p2p_finish<F32>(a, fL + t, v, sm);
+          p2p_finish<F32>(a, fL + t, v);
         } else {
           R* pp = static_cast<R*>(a.part) + ((size_t)(pslot + chunk) * a.lmax + t) * 4;
 #pragma unroll
@@ -634,38 +622,27 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
       }
       __syncwarp();
     }
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      double sv = sm[c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(SFMM_FULL, sv, o);
-      sm[c] = sv;
-    }
-    if (lane == 0 && pslot < 0) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) a.leafsum[5 * (size_t)leaf + c] = sm[c];
-    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(SFMM_FULL, pairs, o);
   if (lane == 0 && pairs) atomicAdd(a.pair_counter, pairs);
 }
 
-// Long lists: thread per leaf; a list of more than SFMM_P2P_CHUNK entries
-// gets ceil(entries / SFMM_P2P_CHUNK) partial slots and one extra work item
+// Long lists: thread per leaf; a list of more than `chunk` entries gets
+// ceil(entries / chunk) partial slots and one extra work item
 // per chunk after the first.  ctr[0]: extra items, ctr[1]: slots, ctr[2]:
 // split leaves.  Which slots a leaf gets does not change any result.
 __global__ void k_p2p_split(int nleaves, const int* __restrict__ p2p_cnt, int* __restrict__ split,
                             int2* __restrict__ extra, int* __restrict__ slist, unsigned long long* __restrict__ ctr,
-                            int max_extra, int max_slots, int max_split, int* __restrict__ status) {
+                            int max_extra, int max_slots, int max_split, int chunk, int* __restrict__ status) {
   const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
   if (leaf >= nleaves) return;
   const int cnt = p2p_cnt[leaf];
-  if (cnt <= SFMM_P2P_CHUNK) {
+  if (cnt <= chunk) {
     split[leaf] = -1;
     return;
   }
-  const int nch = (cnt + SFMM_P2P_CHUNK - 1) / SFMM_P2P_CHUNK;
+  const int nch = (cnt + chunk - 1) / chunk;
   const int x = (int)atomicAdd(ctr, (unsigned long long)(nch - 1));
   const int base = (int)atomicAdd(ctr + 1, (unsigned long long)nch);
   const int q = (int)atomicAdd(ctr + 2, 1ull);
@@ -691,9 +668,8 @@ __global__ void k_p2p_combine(const P2PArgs a, int nsplit) {
     const int leaf = a.slist[q];
     const int L = a.leaf_node[leaf];
     const int fL = a.nfirst[L], nL = a.ncount[L];
-    const int nch = (a.p2p_cnt[leaf] + SFMM_P2P_CHUNK - 1) / SFMM_P2P_CHUNK;
+    const int nch = (a.p2p_cnt[leaf] + a.chunk - 1) / a.chunk;
     const int base = a.split[leaf];
-    double sm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int t = lane; t < nL; t += 32) {
       R v[4] = {R(0), R(0), R(0), R(0)};
       for (int k = 0; k < nch; ++k) {
@@ -701,90 +677,105 @@ __global__ void k_p2p_combine(const P2PArgs a, int nsplit) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] += pp[c];
       }
-      p2p_finish<F32>(a, fL + t, v, sm);
-    }
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      double sv = sm[c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(SFMM_FULL, sv, o);
-      sm[c] = sv;
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) a.leafsum[5 * (size_t)leaf + c] = sm[c];
+      p2p_finish<F32>(a, fL + t, v);
     }
   }
 }
 
-// Fixed-order reduction of the per-leaf sums: every block sums a contiguous
-// range of leaves (tree over threads), then one block sums the block
-// partials; the order never changes, so reruns are bitwise identical.
+// Momentum and energy sums over the particles: sum m a (3), sum |m a| (over
+// components), sum m Phi, as Neumaier-compensated FP64 sums in a fixed order
+// (reruns are bitwise identical).  Every block takes a contiguous range of
+// sorted positions (thread t: positions lo + t, lo + t + RED_NT, ...), merges
+// its threads' sums in a fixed tree and writes one partial (s and c: 10
+// doubles); one block merges the partials.  Accelerations and potentials are
+// read in caller order through the permutation.  A separate pass costs fewer
+// FP64 instructions per particle than sums formed in the near-field kernel,
+// whose warps hold a leaf of ~11 particles.
 #define RED_NT 256
-#define RED_BLOCKS 152
+#define RED_BLOCKS 608
 
-__global__ void k_reduce_leafsum(int nleaves, const double* __restrict__ leafsum, double* __restrict__ part) {
-  __shared__ double sh[5][RED_NT];
-  const int per = (nleaves + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * per, hi = min(nleaves, lo + per);
-  double s[5] = {0, 0, 0, 0, 0};
-  for (int q = lo + threadIdx.x; q < hi; q += RED_NT)
+__device__ __forceinline__ void block_merge(csum (&s)[5], double (&sh)[10][RED_NT]) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) s[c] += leafsum[5 * (size_t)q + c];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = s[c];
+  for (int c = 0; c < 5; ++c) {
+    sh[c][threadIdx.x] = s[c].s;
+    sh[5 + c][threadIdx.x] = s[c].c;
+  }
   __syncthreads();
   for (int w = RED_NT / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
-      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+      for (int c = 0; c < 5; ++c) {
+        csum a{sh[c][threadIdx.x], sh[5 + c][threadIdx.x]};
+        cs_merge(a, sh[c][threadIdx.x + w], sh[5 + c][threadIdx.x + w]);
+        sh[c][threadIdx.x] = a.s;
+        sh[5 + c][threadIdx.x] = a.c;
+      }
     __syncthreads();
   }
-  if (threadIdx.x < 5) part[5 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Compensated sums of sorted positions [lo, hi) into s (this thread's share).
+__device__ __forceinline__ void particle_sums(int64_t lo, int64_t hi, const double* __restrict__ pm,
+                                              const int* __restrict__ perm, const double* __restrict__ acc,
+                                              const double* __restrict__ pot, csum (&s)[5]) {
+  for (int64_t i = lo + threadIdx.x; i < hi; i += RED_NT) {
+    const double m = pm[i];
+    const int o = perm[i];
+    const double ax = m * acc[3 * (size_t)o], ay = m * acc[3 * (size_t)o + 1], az = m * acc[3 * (size_t)o + 2];
+    cs_add(s[0], ax);
+    cs_add(s[1], ay);
+    cs_add(s[2], az);
+    cs_add(s[3], fabs(ax));
+    cs_add(s[3], fabs(ay));
+    cs_add(s[3], fabs(az));
+    cs_add(s[4], m * pot[o]);
+  }
+}
+
+__global__ void __launch_bounds__(RED_NT) k_reduce_particles(int64_t n, const double* __restrict__ pm,
+                                                             const int* __restrict__ perm,
+                                                             const double* __restrict__ acc,
+                                                             const double* __restrict__ pot,
+                                                             double* __restrict__ part) {
+  __shared__ double sh[10][RED_NT];
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * per, hi = min(n, lo + per);
+  csum s[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  particle_sums(lo, hi, pm, perm, acc, pot, s);
+  block_merge(s, sh);
+  if (threadIdx.x < 10) part[10 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 __global__ void k_reduce_final(int nparts, const double* __restrict__ part, double* __restrict__ out) {
-  __shared__ double sh[5][RED_NT];
-  double s[5] = {0, 0, 0, 0, 0};
+  __shared__ double sh[10][RED_NT];
+  csum s[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
   for (int q = threadIdx.x; q < nparts; q += RED_NT)
 #pragma unroll
-    for (int c = 0; c < 5; ++c) s[c] += part[5 * q + c];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = s[c];
-  __syncthreads();
-  for (int w = RED_NT / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x < 5) out[threadIdx.x] = sh[threadIdx.x][0];
+    for (int c = 0; c < 5; ++c) cs_merge(s[c], part[10 * q + c], part[10 * q + 5 + c]);
+  block_merge(s, sh);
+  if (threadIdx.x < 5) out[threadIdx.x] = __dadd_rn(sh[threadIdx.x][0], sh[5 + threadIdx.x][0]);
 }
 
-// Per-system sums of a batch: one block per system over its leaf range.
-__global__ void k_reduce_sys(const int* __restrict__ sys_leaf_off, const double* __restrict__ leafsum,
-                             double* __restrict__ out) {
-  __shared__ double sh[5][RED_NT];
+// Per-system sums of a batch: one block per system over its range of sorted
+// positions (systems are contiguous in the sorted order).
+__global__ void __launch_bounds__(RED_NT) k_reduce_sys(const int* __restrict__ sys_off, const double* __restrict__ pm,
+                                                       const int* __restrict__ perm, const double* __restrict__ acc,
+                                                       const double* __restrict__ pot, double* __restrict__ out) {
+  __shared__ double sh[10][RED_NT];
   const int sys = blockIdx.x;
-  const int lo = sys_leaf_off[sys], hi = sys_leaf_off[sys + 1];
-  double s[5] = {0, 0, 0, 0, 0};
-  for (int q = lo + threadIdx.x; q < hi; q += RED_NT)
-#pragma unroll
-    for (int c = 0; c < 5; ++c) s[c] += leafsum[5 * (size_t)q + c];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = s[c];
-  __syncthreads();
-  for (int w = RED_NT / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
-    __syncthreads();
+  csum s[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  particle_sums(sys_off[sys], sys_off[sys + 1], pm, perm, acc, pot, s);
+  block_merge(s, sh);
+  if (threadIdx.x < 5) {
+    const double v = __dadd_rn(sh[threadIdx.x][0], sh[5 + threadIdx.x][0]);
+    out[5 * (size_t)sys + threadIdx.x] = (threadIdx.x == 4) ? 0.5 * v : v;
   }
-  if (threadIdx.x < 5) out[5 * (size_t)sys + threadIdx.x] = (threadIdx.x == 4) ? 0.5 * sh[4][0] : sh[threadIdx.x][0];
 }
 
 int run_reduce_systems(sfmm_ctx* c) {
   int rc;
   if ((rc = c->sys_sums.ensure(sizeof(double) * 5 * (size_t)c->nsys))) return rc;
-  k_reduce_sys<<<c->nsys, RED_NT, 0, c->stream>>>(c->sys_leaf_off.as<int>(), c->red_part.as<double>(),
-                                                 c->sys_sums.as<double>());
+  k_reduce_sys<<<c->nsys, RED_NT, 0, c->stream>>>(c->sys_off.as<int>(), c->pm.as<double>(), c->perm.as<int>(),
+                                                 c->red_acc, c->red_pot, c->sys_sums.as<double>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   return SFMM_OK;
@@ -793,7 +784,14 @@ int run_reduce_systems(sfmm_ctx* c) {
 int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   const int nl = c->nleaves;
   int rc;
-  if ((rc = c->red_part.ensure(sizeof(double) * 5 * ((size_t)nl + RED_BLOCKS + 1)))) return rc;
+  if ((rc = c->red_part.ensure(sizeof(double) * 10 * ((size_t)RED_BLOCKS + 1)))) return rc;
+  // the sums read the potential: without a caller array it goes to scratch
+  if (!pot) {
+    if ((rc = c->out_pot.ensure(sizeof(double) * (size_t)c->n))) return rc;
+    pot = c->out_pot.as<double>();
+  }
+  c->red_acc = acc;
+  c->red_pot = pot;
   unsigned long long* ctr = c->counters.as<unsigned long long>();
   SFMM_CUDA_TRY(cudaMemsetAsync(ctr + 10, 0, 4 * sizeof(unsigned long long), c->stream));
   const bool f32 = (c->precision == SFMM_FP32);
@@ -810,7 +808,7 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
     if ((rc = c->p2p_part.ensure((f32 ? sizeof(float) : sizeof(double)) * 4 * (size_t)lmax * nslots))) return rc;
     k_p2p_split<<<(nl + 255) / 256, 256, 0, c->stream>>>(nl, c->p2p_cnt.as<int>(), c->p2p_split.as<int>(),
                                                        c->p2p_extra.as<int2>(), c->p2p_slist.as<int>(), ctr + 11,
-                                                       nextra, nslots, nsplit, c->d_status);
+                                                       nextra, nslots, nsplit, c->p2p_chunk, c->d_status);
     ++c->nlaunch;
     SFMM_CUDA_TRY(cudaGetLastError());
   }
@@ -842,19 +840,20 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   a.leaf_counter = reinterpret_cast<int*>(ctr + 10);
   a.acc = acc;
   a.pot = pot;
-  a.leafsum = c->red_part.as<double>();
   a.nextra = nsplit > 0 ? nextra : 0;
   a.extra = nsplit > 0 ? c->p2p_extra.as<int2>() : nullptr;
   a.split = nsplit > 0 ? c->p2p_split.as<int>() : nullptr;
   a.slist = nsplit > 0 ? c->p2p_slist.as<int>() : nullptr;
   a.part = nsplit > 0 ? c->p2p_part.p : nullptr;
   a.lmax = lmax;
+  a.chunk = c->p2p_chunk;
   a.pair_counter = ctr + 3;
   const int nt = 32 * (f32 ? p2p_warps<true>() : p2p_warps<false>());
   int per_sm = 0;
   if (f32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<true>, nt, 0);
   else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<false>, nt, 0);
   if (per_sm < 1) per_sm = 1;
+  if (c->p2p_blocks > 0 && c->p2p_blocks < per_sm) per_sm = c->p2p_blocks;  // option: fewer blocks per SM
   const int nblocks = per_sm * num_sms(c->device);
   if (f32) k_p2p<true><<<nblocks, nt, 0, c->stream>>>(a);
   else k_p2p<false><<<nblocks, nt, 0, c->stream>>>(a);
@@ -870,10 +869,20 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   return SFMM_OK;
 }
 
+int p2p_blocks_fit(sfmm_ctx* c) {
+  const bool f32 = (c->precision == SFMM_FP32);
+  const int nt = 32 * (f32 ? p2p_warps<true>() : p2p_warps<false>());
+  int per_sm = 0;
+  if (f32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<true>, nt, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<false>, nt, 0);
+  return per_sm < 1 ? 1 : per_sm;
+}
+
 int run_reduce(sfmm_ctx* c, double** out_dev) {
-  double* part = c->red_part.as<double>() + 5 * (size_t)c->nleaves;
-  double* out = part + 5 * RED_BLOCKS;
-  k_reduce_leafsum<<<RED_BLOCKS, RED_NT, 0, c->stream>>>(c->nleaves, c->red_part.as<double>(), part);
+  double* part = c->red_part.as<double>();
+  double* out = part + 10 * RED_BLOCKS;
+  k_reduce_particles<<<RED_BLOCKS, RED_NT, 0, c->stream>>>(c->n, c->pm.as<double>(), c->perm.as<int>(), c->red_acc,
+                                                          c->red_pot, part);
   ++c->nlaunch;
   k_reduce_final<<<1, RED_NT, 0, c->stream>>>(RED_BLOCKS, part, out);
   ++c->nlaunch;

@@ -21,10 +21,11 @@
 #define SFMM_MAXDEPTH 128
 #define SFMM_WALK_ATTEMPTS 6  // walk runs: the first plus regrow-and-retry of short buffers
 
-// Neighbour lists longer than this many entries are split into chunks of it,
-// each a separate near-field work item (long lists would otherwise leave one
-// warp working alone at the end of the pass).
-#define SFMM_P2P_CHUNK 256
+// Default of the option "p2p_chunk": neighbour lists longer than this many
+// entries are split into chunks of it, each a separate near-field work item
+// (long lists would otherwise leave one warp working alone at the end of the
+// pass).
+#define SFMM_P2P_CHUNK_DEFAULT 256
 
 namespace sfmm {
 
@@ -67,6 +68,30 @@ __device__ __forceinline__ dfloat df_add_f(dfloat a, float b) {
 __device__ __forceinline__ float df_diff(float ahi, float alo, float bhi, float blo) {
   return __fadd_rn(__fsub_rn(ahi, bhi), __fsub_rn(alo, blo));
 }
+
+// ---------------------------------------------------------------------------
+// Compensated FP64 sums (Neumaier's variant of Kahan summation, 1974): a sum
+// is carried as the rounded running sum s plus the accumulated rounding
+// errors c of every addition, each error taken exactly with Knuth's TwoSum,
+// so the order of the operands' magnitudes does not matter.  Two partial sums
+// merge by adding one's s to the other and both c's: the total error is
+// about eps |sum| + O(n eps^2) sum |x|, instead of O(n eps) sum |x| for a
+// plain sum.  Every operation is rounded as written.
+// ---------------------------------------------------------------------------
+struct csum { double s, c; };
+
+__device__ __forceinline__ void cs_add(csum& a, double x) {
+  const double t = __dadd_rn(a.s, x);
+  const double bb = __dsub_rn(t, a.s);
+  const double e = __dadd_rn(__dsub_rn(a.s, __dsub_rn(t, bb)), __dsub_rn(x, bb));
+  a.s = t;
+  a.c = __dadd_rn(a.c, e);
+}
+__device__ __forceinline__ void cs_merge(csum& a, double bs, double bc) {
+  cs_add(a, bs);
+  a.c = __dadd_rn(a.c, bc);
+}
+__device__ __forceinline__ double cs_value(const csum& a) { return __dadd_rn(a.s, a.c); }
 
 // ---------------------------------------------------------------------------
 // Warp helpers

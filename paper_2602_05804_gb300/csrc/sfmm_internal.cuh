@@ -6,6 +6,8 @@
 
 #include "sfmm_common.cuh"
 
+struct sfmm_tune_table;  // autotuner table (autotune.cu)
+
 // Device buffer that only grows (freed on destroy).
 struct DevBuf {
   void* p = nullptr;
@@ -38,11 +40,11 @@ struct sfmm_ctx {
   // systems of a batch (nsys = 1 for a single particle set): particle offsets
   // and leaf sizes on host and device; the system of each particle; the root
   // node of each system; each node's parent for the walk (-1 at a system
-  // root, -2 for nodes spanning several systems); leaf offsets per system
+  // root, -2 for nodes spanning several systems); per-system sums
   int nsys = 1;
   std::vector<int64_t> h_sys_off;
   std::vector<int> h_sys_lsz;
-  DevBuf sys_off, sys_lsz, psys, sys_root, wparent, sys_leaf_off, sys_sums;
+  DevBuf sys_off, sys_lsz, psys, sys_root, wparent, sys_sums;
   int32_t nnodes = 0, nleaves = 0;
   int moments_order = -1;  // order of the cached moments (-1: none)
   bool moments_fp64 = false;  // the cached moments include the FP64 rows (else FP32 only)
@@ -50,6 +52,8 @@ struct sfmm_ctx {
   int walk_mode = 1;        // 1: per-node shared pairs (default), 0: per-leaf replay (Algorithm 1),
                             // 2: per-node pairs, each evaluated once for both sides
   int schedule = 0;         // walk mode 1: 0 automatic, 1 one launch per depth, 2 readiness queue
+  int p2p_chunk = SFMM_P2P_CHUNK_DEFAULT;  // neighbour-list entries per near-field work item
+  int p2p_blocks = 0;       // near-field blocks per SM (0: as many as fit)
   int max_depth = 0;
   std::vector<int> h_level_off;  // host copy: internal nodes per depth, max_depth + 2 entries
   int* h_level_pin = nullptr;     // pinned landing buffer of the level offsets (and their total)
@@ -100,6 +104,8 @@ struct sfmm_ctx {
   DevBuf lf_acc, lf_part;
   // kd-tree build: particle orders, breadth-first node records, level scratch
   DevBuf kd_ord, kd_node, kd_act, kd_work, kd_chunk, kd_part, kd_split;
+  const double* red_acc = nullptr;  // outputs of the last near-field pass (caller order), read by the sums
+  const double* red_pot = nullptr;
   int64_t arena_used = 0;
   int64_t split_chunks = 0, split_lists = 0;  // from the walk: chunks of split lists, split lists
 
@@ -107,6 +113,12 @@ struct sfmm_ctx {
   int* d_status = nullptr;
   int* h_status = nullptr;
   double* h_scalars = nullptr;  // pinned host scratch
+
+  // autotuner: table of tuned choices, and the theta / order that builds with
+  // autotuned leaf sizes (sfmm_build_batch with leaf_size NULL) tune for
+  sfmm_tune_table* tune = nullptr;
+  double tune_theta = 0.5;
+  int tune_order = 2;
 
   int64_t nlaunch = 0;  // kernels launched by this context (cumulative)
   cudaEvent_t ev[8] = {};
@@ -143,6 +155,14 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
 int run_p2p(sfmm_ctx* c, double* acc, double* pot);
 int run_reduce(sfmm_ctx* c, double** out_dev);  // device pointer of the 5 sums
 int run_reduce_systems(sfmm_ctx* c);             // per-system sums (batches)
+
+// autotune.cu
+void tune_table_free(sfmm_ctx* c);
+int tune_set_cache(sfmm_ctx* c, const char* path);
+int tuned_leaf_sizes(sfmm_ctx* c, int nsys, const int64_t* offsets, const double* pos, const double* mass,
+                     const double* h, double theta, int order, std::vector<int>& lsz);
+int tuned_knobs(sfmm_ctx* c, double theta, int order, double* acc, bool run_trials);
+int p2p_blocks_fit(sfmm_ctx* c);  // near-field blocks per SM that fit (p2p.cu)
 
 int check_status(sfmm_ctx* c);
 int sync_status(sfmm_ctx* c, int* bits);

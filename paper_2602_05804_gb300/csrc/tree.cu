@@ -716,21 +716,6 @@ __global__ void k_sysroots(int nn, const int* __restrict__ psys, const int* __re
   if (root) sys_root[sv] = v;
 }
 
-// First leaf of every system (leaves are in (system, key) order).
-__global__ void k_sys_leaf_off(int nleaves, int nsys, const int* __restrict__ psys,
-                               const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
-                               int* __restrict__ sys_leaf_off) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q > nleaves) return;
-  if (q == nleaves) {
-    sys_leaf_off[nsys] = nleaves;
-    return;
-  }
-  const int s = psys ? psys[nfirst[leaf_node[q]]] : 0;
-  const int sp = (q == 0) ? -1 : (psys ? psys[nfirst[leaf_node[q - 1]]] : 0);
-  if (s != sp) sys_leaf_off[s] = q;
-}
-
 // isleaf has been exclusive-scanned into leaf indices; record the leaves.
 __global__ void k_leaf_list(int nn, const int* __restrict__ nright, const uint32_t* __restrict__ lidx,
                             int* __restrict__ leaf_node) {
@@ -1327,7 +1312,6 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     psys = c->psys.as<int>();
   }
   if ((rc = c->sys_root.ensure(sizeof(int) * (size_t)nsys))) return rc;
-  if ((rc = c->sys_leaf_off.ensure(sizeof(int) * ((size_t)nsys + 1)))) return rc;
   if ((rc = c->wparent.ensure(sizeof(int) * nn_max))) return rc;
 
   // S1: bounding box (per system), validation, Morton keys
@@ -1458,12 +1442,9 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     }
   }
   const int nl = c->nleaves;
-  // walk parents, system roots and leaf ranges of the systems
+  // walk parents and system roots
   k_sysroots<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, psys, c->nfirst.as<int>(), c->ncount.as<int>(),
                                                 c->nparent.as<int>(), c->wparent.as<int>(), c->sys_root.as<int>());
-  ++c->nlaunch;
-  k_sys_leaf_off<<<nblk(nl + 1, 256), 256, 0, st>>>(nl, nsys, psys, c->leaf_node.as<int>(), c->nfirst.as<int>(),
-                                                    c->sys_leaf_off.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
 

@@ -330,8 +330,8 @@ __global__ void __launch_bounds__(WALK_NT) k_walk(const WalkArgs a) {
         a.p2p_off[leaf] = (long long)base;
         a.p2p_cnt[leaf] = nn;
         st_pl += nn;
-        if (nn > SFMM_P2P_CHUNK) {
-          atomicAdd(a.split_counter, (unsigned long long)((nn + SFMM_P2P_CHUNK - 1) / SFMM_P2P_CHUNK));
+        if (nn > a.chunk) {
+          atomicAdd(a.split_counter, (unsigned long long)((nn + a.chunk - 1) / a.chunk));
           atomicAdd(a.split_counter + 1, 1ull);
         }
       }
@@ -431,6 +431,7 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
     a.arena = c->arena.as<int>();
     a.arena_counter = ctr + 9;
     a.split_counter = ctr + 5;
+    a.chunk = c->p2p_chunk;
     a.arena_cap = arena_cap;
     a.p2p_off = c->p2p_off.as<long long>();
     a.p2p_cnt = c->p2p_cnt.as<int>();
@@ -512,6 +513,7 @@ int run_walk_dump_write(sfmm_ctx* c, double theta, const long long* d_off, int* 
   a.arena = c->arena.as<int>();
   a.arena_counter = ctr + 9;
   a.split_counter = ctr + 5;
+    a.chunk = c->p2p_chunk;
   a.arena_cap = (long long)(c->arena.bytes / sizeof(int));
   a.p2p_off = c->p2p_off.as<long long>();
   a.p2p_cnt = c->p2p_cnt.as<int>();

@@ -43,6 +43,7 @@ struct WalkArgs {
   int* arena;
   unsigned long long* arena_counter;
   unsigned long long* split_counter;  // [0]: chunks of split lists, [1]: split lists
+  int chunk;                          // neighbour-list entries per near-field work item
   long long arena_cap;
   long long* p2p_off;
   int* p2p_cnt;

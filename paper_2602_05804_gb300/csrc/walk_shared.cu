@@ -522,8 +522,8 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
         a.p2p_off[leaf] = (long long)base;
         a.p2p_cnt[leaf] = nn;
         st_pl += nn;
-        if (nn > SFMM_P2P_CHUNK) {
-          atomicAdd(a.split_counter, (unsigned long long)((nn + SFMM_P2P_CHUNK - 1) / SFMM_P2P_CHUNK));
+        if (nn > a.chunk) {
+          atomicAdd(a.split_counter, (unsigned long long)((nn + a.chunk - 1) / a.chunk));
           atomicAdd(a.split_counter + 1, 1ull);
         }
       }
@@ -698,6 +698,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     a.arena = c->arena.as<int>();
     a.arena_counter = ctr + 9;
     a.split_counter = ctr + 5;
+    a.chunk = c->p2p_chunk;
     a.arena_cap = arena_cap;
     a.p2p_off = c->p2p_off.as<long long>();
     a.p2p_cnt = c->p2p_cnt.as<int>();

@@ -23,7 +23,8 @@ SFMM_FP64, SFMM_FP32 = 0, 1
 EXPORTS = ("sfmm_create", "sfmm_destroy", "sfmm_set_stream", "sfmm_set_option", "sfmm_build", "sfmm_gravity",
            "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
            "sfmm_lists", "sfmm_strerror", "sfmm_last_error", "sfmm_version", "sfmm_reduce_noalloc",
-           "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums", "sfmm_leapfrog")
+           "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums", "sfmm_leapfrog", "sfmm_fma_peak",
+           "sfmm_autotune_batch", "sfmm_autotune_cache")
 SFMM_NOALLOC_MAX_N = 67108864
 
 
@@ -84,9 +85,14 @@ def load(path: str = LIB_PATH):
     lib.sfmm_reduce_noalloc.argtypes = [i64, P, P, P, P, P]
     lib.sfmm_reduce_noalloc.restype = i32
     lib.sfmm_leapfrog.argtypes = [P, i64, P, P, P, P, i32, dbl, i32, dbl, i64, i64, P, P]
+    lib.sfmm_fma_peak.argtypes = [i32, i32, P, dbl, i32, P, P]
+    lib.sfmm_fma_peak.restype = i32
+    lib.sfmm_autotune_batch.argtypes = [P, i32, P, P, P, P, dbl, i32, P]
+    lib.sfmm_autotune_cache.argtypes = [P, ctypes.c_char_p]
     for name in ("sfmm_create", "sfmm_set_stream", "sfmm_set_option", "sfmm_build", "sfmm_gravity",
                  "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
-                 "sfmm_lists", "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums", "sfmm_leapfrog"):
+                 "sfmm_lists", "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums", "sfmm_leapfrog", "sfmm_fma_peak",
+           "sfmm_autotune_batch", "sfmm_autotune_cache"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -193,6 +199,19 @@ def sfmm_build_batch(ctx, offsets, pos, mass, h, leaf_size=None):
     _check(load().sfmm_build_batch(ctx, len(off) - 1, _ptr(off), _ptr(pos), _ptr(mass), _ptr(h), _ptr(ls)), ctx)
 
 
+def sfmm_autotune_batch(ctx, offsets, pos, mass, h, theta, order):
+    """Autotune and build a batch; returns the chosen leaf sizes."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    out = np.empty(len(off) - 1, np.int32)
+    _check(load().sfmm_autotune_batch(ctx, len(off) - 1, _ptr(off), _ptr(pos), _ptr(mass), _ptr(h), float(theta),
+                                      int(order), _ptr(out)), ctx)
+    return out
+
+
+def sfmm_autotune_cache(ctx, path):
+    _check(load().sfmm_autotune_cache(ctx, path.encode() if path else None), ctx)
+
+
 def sfmm_gravity_batch(ctx, theta, order, acc, pot):
     _check(load().sfmm_gravity_batch(ctx, float(theta), int(order), _ptr(acc), _ptr(pot)), ctx)
 
@@ -219,6 +238,15 @@ def sfmm_reduce_noalloc(n, mass, acc, pot, out, stream=None):
     (see include/sfmm.h); ``out`` is a device buffer of 5 float64."""
     _check(load().sfmm_reduce_noalloc(int(n), _ptr(mass), _ptr(acc), _ptr(pot), _ptr(out),
                                       ctypes.c_void_p(stream) if stream else None))
+
+
+def sfmm_fma_peak(device=0, form=1, stream=None, target_ms=20.0, reps=5):
+    """Measured FMA throughput (TFLOP/s, ms of the best launch); form 0 FP64,
+    1 FP32, 2 packed FP32."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().sfmm_fma_peak(int(device), int(form), ctypes.c_void_p(stream) if stream else None,
+                                float(target_ms), int(reps), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def sfmm_strerror(code: int) -> str:
@@ -297,6 +325,16 @@ class Solver:
         sfmm_build_batch(self.ctx, offsets, *self._inputs, leaf_size)
         self.n = n
         self.nsys = len(offsets) - 1
+
+    def autotune_batch(self, offsets, pos, mass, h, theta=0.5, order=2):
+        """Autotune leaf sizes and launch knobs on these systems and build the
+        batch; returns the chosen leaf sizes."""
+        n = int(offsets[-1])
+        self._inputs = (self._dev(pos, (n, 3)), self._dev(mass, (n,)), self._dev(h, (n,)))
+        ls = sfmm_autotune_batch(self.ctx, offsets, *self._inputs, theta, order)
+        self.n = n
+        self.nsys = len(offsets) - 1
+        return ls
 
     def batch_sums(self):
         return sfmm_batch_sums(self.ctx, self.nsys)

@@ -5,7 +5,7 @@ seeded inputs and compares element by element with the oracle:
   - the tree: keys, permutation, node ranges, links, depths, leaves exactly;
     centres/sizes to rounding, h_max exactly;
   - the mass moments to rounding;
-  - the interaction lists of Algorithm 2 exactly (per leaf, as sets);
+  - the interaction lists of Algorithm 2 exactly (per leaf, as multisets);
   - accelerations and potentials: FP64 form <= 1e-10 relative per particle,
     FP32 form <= 1e-5 rms relative, momentum residual <= 1e-14 / 1e-6.
 """
@@ -16,8 +16,8 @@ import pytest
 
 import oracle
 import workloads
-from gpu_helpers import (TOL_FP32_RMS, TOL_FP64, TOL_MOM_FP32, TOL_MOM_FP64, acc_rel, momentum_residual,
-                         pot_rel, solver)
+from gpu_helpers import (TOL_FP32_MAX, TOL_FP32_RMS, TOL_FP64, TOL_MOM_FP32, TOL_MOM_FP64, acc_rel,
+                         momentum_residual, pot_rel, solver)
 
 pytestmark = pytest.mark.gpu
 
@@ -79,8 +79,10 @@ def test_moments_match_oracle(p, prec):
 
 
 def _per_leaf_sets(mo, lv, src, po, ps):
-    m2l = [set(zip(lv[mo[q]:mo[q + 1]].tolist(), src[mo[q]:mo[q + 1]].tolist())) for q in range(len(mo) - 1)]
-    p2p = [set(ps[po[q]:po[q + 1]].tolist()) for q in range(len(po) - 1)]
+    """Per leaf, the sorted multiset of its M2L entries (level, source) and
+    of its neighbour leaves: a duplicated or missing entry changes it."""
+    m2l = [sorted(zip(lv[mo[q]:mo[q + 1]].tolist(), src[mo[q]:mo[q + 1]].tolist())) for q in range(len(mo) - 1)]
+    p2p = [sorted(ps[po[q]:po[q + 1]].tolist()) for q in range(len(po) - 1)]
     return m2l, p2p
 
 
@@ -156,8 +158,10 @@ def test_fp32_form_matches_oracle(kind, n, ls, theta, p, walk):
     st = s.stats()
     assert st["m2l"] == st_o["m2l"] and st["p2p_pairs"] == st_o["p2p_pairs"]
     e = acc_rel(acc, acc_o)
+    print("fp32 %s n %d leaf %d theta %.1f p %d walk %d: acc rel rms %.3e max %.3e" % (
+        kind, n, ls, theta, p, walk, math.sqrt((e**2).mean()), e.max()))
     assert math.sqrt((e**2).mean()) <= TOL_FP32_RMS, (math.sqrt((e**2).mean()), e.max())
-    assert e.max() <= 1e-3
+    assert e.max() <= TOL_FP32_MAX, e.max()
     pe = pot_rel(pot, pot_o)
     assert math.sqrt((pe**2).mean()) <= TOL_FP32_RMS
     assert momentum_residual(m, acc) <= TOL_MOM_FP32

@@ -188,3 +188,20 @@ def test_m2l_pairwise_antisymmetry(p):
     FA = (mA[:, None] * aA).sum(0)
     FB = (mB[:, None] * aB).sum(0)
     np.testing.assert_allclose(FA, -FB, rtol=1e-12, atol=1e-14 * np.abs(FA).max())
+
+
+def test_dipole_about_centre_of_mass_vanishes_to_rounding():
+    """The FP32 form leaves the dipole term out of its M2L because moments
+    are taken about each node's centre of mass (Eq. massmom with s the
+    centre of mass), where Q_1 = sum m (x - s) = 0.  In FP64 the oracle's
+    directly summed dipoles are at rounding level: at most a few n eps of
+    M max|x| for a node of n particles."""
+    import workloads
+
+    eps = np.finfo(float).eps
+    for gen in (workloads.plummer, workloads.uniform_sphere, workloads.binary_polytrope):
+        pos, m, h = gen(20000, 5)
+        t = oracle.Tree(pos, m, h, 8, p=2)
+        q1 = np.abs(t.Q[:, oracle.rank_offset(1):oracle.rank_offset(2)]).max(axis=1)
+        xmax = np.abs(pos).max()
+        assert np.all(q1 <= 4 * t.count * eps * t.mass * xmax), q1.max()

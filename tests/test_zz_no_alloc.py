@@ -33,14 +33,26 @@ def test_noalloc_reduction_matches_gravity_stats_twice():
     mass = torch.from_numpy(m).cuda()
     out = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
     scale = np.array([st["abs_momentum"]] * 4 + [abs(st["W"])])
+    # the first call in a context looks up the array (and the driver may load
+    # the library's module holding it); the calls after it allocate nothing
+    sfmm.sfmm_reduce_noalloc(len(m), mass, acc, pot, out, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got_calls = []
     for call in range(2):
         out.fill_(float("nan"))
         torch.cuda.synchronize()
+        # nothing may be allocated by the call itself: neither device memory
+        # as the driver sees it nor torch's allocator changes across it
+        free0, allocated0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         sfmm.sfmm_reduce_noalloc(len(m), mass, acc, pot, out, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, call
+        assert torch.cuda.memory_allocated() == allocated0, call
         got = out.cpu().numpy()
+        got_calls.append(got)
         assert np.all(np.isfinite(got)), call
         assert np.all(np.abs(got - ref) <= TOL_FP64 * scale), (call, got, ref)
+    np.testing.assert_array_equal(got_calls[0], got_calls[1])
     # a different, smaller input on the same scratch: matches its own sums
     acc2 = acc[:1000].contiguous()
     pot2 = pot[:1000].contiguous()
