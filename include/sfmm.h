@@ -299,9 +299,9 @@ int sfmm_leapfrog(sfmm_ctx* ctx, int64_t n, double* pos, double* vel, const doub
 
 /* Momentum and energy sums of a particle set WITHOUT ANY DEVICE ALLOCATION:
  * out[0..2] = sum_i m_i a_i, out[3] = sum_i sum_d |m_i a_i,d|,
- * out[4] = 1/2 sum_i m_i Phi_i (0 when pot is NULL) -- the same compensated
- * (Neumaier) sums that sfmm_get_stats reports after sfmm_gravity, here over
- * caller arrays.  The paper has no counterpart: this is a service for callers
+ * out[4] = 1/2 sum_i m_i Phi_i (0 when pot is NULL) -- the same sums that
+ * sfmm_get_stats reports after sfmm_gravity (momentum components as
+ * Neumaier-compensated FP64 sums), here over caller arrays.  The paper has no counterpart: this is a service for callers
  * that cannot call cudaMalloc, such as code that must draw all device memory
  * from its own pre-reserved pool or must not change the device's memory
  * footprint once it is running.  No context is needed and nothing is

@@ -67,10 +67,9 @@ __global__ void k_noalloc_tiles(int64_t n, const double* __restrict__ mass, cons
     sfmm::cs_add(s[0], ax);
     sfmm::cs_add(s[1], ay);
     sfmm::cs_add(s[2], az);
-    sfmm::cs_add(s[3], fabs(ax));
-    sfmm::cs_add(s[3], fabs(ay));
-    sfmm::cs_add(s[3], fabs(az));
-    if (pot) sfmm::cs_add(s[4], m * pot[i]);
+    // same-sign sums: plain additions (no cancellation to compensate)
+    s[3].s = __dadd_rn(s[3].s, __dadd_rn(__dadd_rn(fabs(ax), fabs(ay)), fabs(az)));
+    if (pot) s[4].s = __dadd_rn(s[4].s, m * pot[i]);
   }
   noalloc_block_merge(s, sh);
   if (threadIdx.x < 10) partials[10 * (int64_t)blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];

@@ -683,8 +683,9 @@ __global__ void k_p2p_combine(const P2PArgs a, int nsplit) {
 }
 
 // Momentum and energy sums over the particles: sum m a (3), sum |m a| (over
-// components), sum m Phi, as Neumaier-compensated FP64 sums in a fixed order
-// (reruns are bitwise identical).  Every block takes a contiguous range of
+// components), sum m Phi, in FP64 in a fixed order (reruns are bitwise
+// identical); the momentum components, whose terms cancel to ~1e-18 of
+// sum |m a|, as Neumaier-compensated sums.  Every block takes a contiguous range of
 // sorted positions (thread t: positions lo + t, lo + t + RED_NT, ...), merges
 // its threads' sums in a fixed tree and writes one partial (s and c: 10
 // doubles); one block merges the partials.  Accelerations and potentials are
@@ -724,10 +725,10 @@ __device__ __forceinline__ void particle_sums(int64_t lo, int64_t hi, const doub
     cs_add(s[0], ax);
     cs_add(s[1], ay);
     cs_add(s[2], az);
-    cs_add(s[3], fabs(ax));
-    cs_add(s[3], fabs(ay));
-    cs_add(s[3], fabs(az));
-    cs_add(s[4], m * pot[o]);
+    // sums of same-sign terms cannot cancel: plain additions are accurate to
+    // a few eps of the result there, and cost a seventh of a compensated one
+    s[3].s = __dadd_rn(s[3].s, __dadd_rn(__dadd_rn(fabs(ax), fabs(ay)), fabs(az)));
+    s[4].s = __dadd_rn(s[4].s, m * pot[o]);
   }
 }
 

@@ -159,8 +159,14 @@ def sfmm_tree_size(ctx):
     return nn.value, nl.value
 
 
-def sfmm_tree_export(ctx, n):
+def sfmm_tree_export(ctx, n=None):
+    """The built tree as numpy arrays (sized from the context's own counts;
+    n, if given, must equal the built particle count)."""
     nn, nl = sfmm_tree_size(ctx)
+    nb = int(sfmm_get_stats(ctx)["n"])
+    if n is not None and int(n) != nb:
+        raise ValueError("n = %d differs from the built particle count %d" % (int(n), nb))
+    n = nb
     t = dict(perm=np.empty(n, np.int64), keys=np.empty(n, np.uint64), first=np.empty(nn, np.int32),
              count=np.empty(nn, np.int32), right=np.empty(nn, np.int32), parent=np.empty(nn, np.int32),
              depth=np.empty(nn, np.int32), centre=np.empty((nn, 3)), size=np.empty(nn), hmax=np.empty(nn),
