@@ -669,12 +669,14 @@ def run_gpu(args):
                 "stage_ms": {"build": st_s["ms_build"], "moments": st_s["ms_moments"], "walk": st_s["ms_walk"],
                              "p2p": st_s["ms_p2p"]}}
 
-    # the shared walk under both node orders (bitwise the same results): one
-    # launch per depth, and one launch over a queue of nodes whose parent is
-    # done; the automatic choice takes the queue while the walk's per-node
-    # records fit in L2
+    # the shared walk under its three node orders (bitwise the same results):
+    # one launch per depth, one launch over a queue of nodes whose parent is
+    # done, and the same over a queue of sibling pairs; the automatic choice
+    # takes the node queue while the walk's per-node records fit in L2, else
+    # the pair queue
     schedules = {}
-    for sched, label in ((1, "one launch per depth"), (2, "readiness queue")):
+    for sched, label in ((1, "one launch per depth"), (2, "readiness queue of nodes"),
+                         (3, "readiness queue of sibling pairs")):
         sq = sfmm.Solver(local, "fp32", profile=1, walk=1, schedule=sched)
         ms_q, st_q = time_steps(torch, sq, pos_d, m_d, h_d, acc, pot, w, w["theta"], max(1, min(args.steps, 3)), 1,
                                 flush)
@@ -764,7 +766,8 @@ def run_gpu(args):
                    "leaf_size": w["leaf_size"], "form": "FP32 (FP64 centres, decisions, reductions)",
                    "walk": {0: "per-leaf replay (Algorithm 1)", 1: "per-node shared pairs",
                             2: "one-sided symmetric pairs"}[args.walk],
-                   "schedule": {0: "automatic", 1: "one launch per depth", 2: "readiness queue"}[args.schedule],
+                   "schedule": {0: "automatic", 1: "one launch per depth", 2: "readiness queue of nodes",
+                                3: "readiness queue of sibling pairs"}[args.schedule],
                    "l2": "flushed between timed steps (512 MB write outside the events)"},
         "interactions_per_s": ws * inter / (step_ms * 1e-3),
         "counts": {"m2l_replicated": st32["m2l"], "m2l_unique": st32["m2l_unique"],
@@ -831,8 +834,9 @@ def main():
     ap.add_argument("--walk", type=int, default=1, choices=[0, 1, 2],
                     help="headline walk: 1 per-node shared pairs (default), 0 per-leaf replay (Algorithm 1), "
                          "2 one-sided symmetric pairs")
-    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2],
-                    help="walk 1 node order: 0 automatic (default), 1 one launch per depth, 2 readiness queue")
+    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="walk 1 node order: 0 automatic (default), 1 one launch per depth, 2 readiness queue of "
+                         "nodes, 3 readiness queue of sibling pairs")
     ap.add_argument("--only", default="all", choices=["all", "fp32", "fp64"],
                     help="fp32 / fp64: time the headline step of that form only (for profiler launch lists)")
     ap.add_argument("--no-oracle-error", action="store_true",

@@ -115,9 +115,11 @@ int sfmm_set_stream(sfmm_ctx* ctx, void* stream);
  *   "schedule"       order of the nodes in walk 1 (a node needs its parent's
  *                    opened list and coefficients): 1 one launch per depth;
  *                    2 one launch in which a warp takes the next node whose
- *                    parent is done from a queue; 0 (default) chooses 2 when
+ *                    parent is done from a queue; 3 the same with both
+ *                    children of a node taken by one warp (their common
+ *                    inherited list read once); 0 (default) chooses 2 when
  *                    the walk's per-node records fit in three quarters of the
- *                    L2 cache, else 1; bitwise the same results
+ *                    L2 cache, else 3; bitwise the same results
  *   "tree"           0 (default): binary radix tree over Morton keys (Sect. 3);
  *                    1: centre-of-mass-pivot kd tree (Sect. 3; single
  *                    systems only, sfmm_build_batch returns ENOTIMPL)
@@ -198,7 +200,7 @@ int sfmm_build_batch(sfmm_ctx* ctx, int nsys, const int64_t* offsets, const doub
  *   median size, built and solved with each candidate in a scratch context
  *   (best of two timed runs after a warm-up run, CUDA events).
  *   Launch knobs per (total-size bucket, log2 nsys, theta, order, form): walk
- *   "schedule" {1, 2} x "p2p_blocks" {all that fit, one fewer} x "p2p_chunk"
+ *   "schedule" {1, 2, 3} x "p2p_blocks" {all that fit, one fewer} x "p2p_chunk"
  *   {128, 256, 512}, each timed on a gravity call of the whole batch; the
  *   best are set as this context's options.
  * Arguments as sfmm_build_batch (leaf sizes are chosen, not given) plus

@@ -223,8 +223,9 @@ int sfmm_set_option(sfmm_ctx* c, const char* key, double v) {
       return set_error(c, SFMM_EINVAL, "walk: 0 (per-leaf replay), 1 (per-node shared pairs), 2 (one-sided symmetric pairs)");
     c->walk_mode = (int)v;
   } else if (!strcmp(key, "schedule")) {
-    if (v != 0.0 && v != 1.0 && v != 2.0)
-      return set_error(c, SFMM_EINVAL, "schedule: 0 (automatic), 1 (one launch per depth), 2 (readiness queue)");
+    if (v != 0.0 && v != 1.0 && v != 2.0 && v != 3.0)
+      return set_error(c, SFMM_EINVAL,
+                       "schedule: 0 (automatic), 1 (one launch per depth), 2 (queue of nodes), 3 (queue of sibling pairs)");
     c->schedule = (int)v;
   } else if (!strcmp(key, "p2p_chunk")) {
     if (v != std::floor(v) || v < 32 || v > 65536)

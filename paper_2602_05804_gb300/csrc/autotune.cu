@@ -9,7 +9,8 @@
 // the fastest (best of two runs, CUDA events) wins.
 //
 // Launch knobs, per (total-size bucket, log2 systems, theta, order, form):
-// walk schedule {per depth, readiness queue} x near-field blocks per SM
+// walk schedule {per depth, queue of nodes, queue of sibling pairs} x
+// near-field blocks per SM
 // {all that fit, one fewer} x neighbour-list chunk {128, 256, 512}, each timed
 // on a gravity call of the whole batch.
 //
@@ -197,7 +198,7 @@ static int load_table(sfmm_ctx* c) {
       if (mp) sscanf(mp + 7, "%lf , %lf , %lf , %lf", &e.ms[0], &e.ms[1], &e.ms[2], &e.ms[3]);
       t->leaf[key] = e;
     } else if (section == 2 && field_int(line, "\"schedule\"", &a) && field_int(line, "\"p2p_blocks\"", &b) &&
-               field_int(line, "\"p2p_chunk\"", &d) && a >= 0 && a <= 2 && b >= 0 && b <= 64 && d >= 32 &&
+               field_int(line, "\"p2p_chunk\"", &d) && a >= 0 && a <= 3 && b >= 0 && b <= 64 && d >= 32 &&
                d <= 65536) {
       sfmm_tune_table::Knobs e;
       e.schedule = (int)a;
@@ -337,11 +338,11 @@ int tuned_knobs(sfmm_ctx* c, double theta, int order, double* acc, bool run_tria
     sfmm_tune_table::Knobs best;
     best.ms = 1e300;
     int rc = SFMM_OK;
-    const int schedules[2] = {1, 2};
+    const int schedules[3] = {1, 2, 3};
     const int chunks[3] = {128, 256, 512};
     const int fit = p2p_blocks_fit(c);  // near-field blocks per SM that fit
     const int nb = fit > 1 ? 2 : 1;     // all that fit, and one fewer
-    for (int si = 0; rc == SFMM_OK && si < 2; ++si)
+    for (int si = 0; rc == SFMM_OK && si < 3; ++si)
       for (int bi = 0; rc == SFMM_OK && bi < nb; ++bi)
         for (int ci = 0; rc == SFMM_OK && ci < 3; ++ci) {
           c->schedule = schedules[si];

@@ -197,6 +197,8 @@ __device__ __forceinline__ void leaf_l2p(const LevelArgs& la, int A, double cAx,
   }
 }
 
+#include "walk_pair.cuh"
+
 // Blocks per SM (FP32, p <= 2): 5 for the queue walk, 4 per depth -- measured:
 // the queue walk gains from the fifth block despite a few spilled registers,
 // the per-depth walk loses.
@@ -619,35 +621,45 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
   const int nn = c->nnodes, nl = c->nleaves;
   int per_sm = 0, q_per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_level<P, F32, SYM, false>, WALK_NT, 0);
-  if (!SYM) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_per_sm, k_walk_level<P, F32, false, true>, WALK_NT, 0);
-  // readiness queue or one launch per depth (walk mode 1): the queue runs
-  // nodes of all depths at once, so it pays when their walk records
-  // (geometry, moments, coefficients, list offsets) stay in L2; per-depth
-  // launches keep one depth's records resident otherwise
+  int p_per_sm = 0;
+  if (!SYM) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_per_sm, k_walk_level<P, F32, false, true>, WALK_NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p_per_sm, k_walk_pair<P, F32>, WALK_NT, 0);
+  }
   if (per_sm < 1) per_sm = 1;
   if (q_per_sm < 1) q_per_sm = 1;
-  const int max_blocks = per_sm * num_sms(c->device), q_blocks = q_per_sm * num_sms(c->device);
+  if (p_per_sm < 1) p_per_sm = 1;
+  const int max_blocks = per_sm * num_sms(c->device);
   const int tstride = NCS * 32;
-  bool queue = false;
-  if (!SYM) {
-    if (c->schedule == 2) queue = true;
-    else if (c->schedule == 0) {
-      int l2 = 0;
-      if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device) != cudaSuccess) l2 = 0;
-      // geometry and right child (36 B), list offset and count (12 B),
-      // moments, coefficients
-      const size_t mom = F32 ? 4 * (size_t)((ncoef(order) + 3) & ~3) : 24 + 8 * (size_t)E::NQ;
-      const size_t per_node = 48 + mom + 8 * (size_t)tstride;
-      queue = (double)per_node * nn <= 0.75 * (double)l2;
-    }
+  // schedule (walk mode 1; bitwise the same results): 1 one launch per
+  // depth; 2 readiness queue of nodes; 3 readiness queue of sibling pairs
+  // (each record load serves both children's decisions, at fewer warps per
+  // SM); 0 chooses 2 while the walk's records (geometry, moments,
+  // coefficients, list offsets) fit in three quarters of L2, else 3
+  // (measured: 2 is 3 % faster on the 10^6 Plummer sphere, 3 is 6-10 %
+  // faster than both others on the 2x10^6 binary and the 1.6x10^7 cloud)
+  int sched = SYM ? 1 : c->schedule;
+  if (sched == 0) {
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device) != cudaSuccess) l2 = 0;
+    // geometry and right child (36 B), list offset and count (12 B),
+    // moments, coefficients
+    const size_t mom = F32 ? 4 * (size_t)((ncoef(order) + 3) & ~3) : 24 + 8 * (size_t)E::NQ;
+    const size_t per_node = 48 + mom + 8 * (size_t)tstride;
+    sched = ((double)per_node * nn <= 0.75 * (double)l2) ? 2 : 3;
   }
+  const bool queue = sched >= 2, pairs = sched == 3;
+  const int q_blocks = (pairs ? p_per_sm : q_per_sm) * num_sms(c->device);
   int rc;
   // per-depth launches (and the symmetric walk) run over the per-depth lists
   if (!queue && (rc = ensure_levels(c)))
     return set_error(c, rc, rc == SFMM_ESTACK ? "tree deeper than supported" : "per-depth node lists failed");
   for (int attempt = 0; attempt < SFMM_WALK_ATTEMPTS; ++attempt) {
-    const int nwarps = std::max(max_blocks, q_blocks) * WALK_WARPS;  // one ring per resident warp
-    if ((rc = c->ring.ensure(sizeof(int) * (size_t)nwarps * 2 * c->ring_capacity))) return rc;
+    // one ring per resident warp (the pair walk keeps both children's stacks
+    // and lists and the second child's set-aside batches)
+    const size_t ring_ints = pairs ? (size_t)q_blocks * WALK_WARPS * WALK_PAIR_RING * c->ring_capacity
+                                   : (size_t)(queue ? q_blocks : max_blocks) * WALK_WARPS * 2 * c->ring_capacity;
+    if ((rc = c->ring.ensure(sizeof(int) * ring_ints))) return rc;
     long long arena_cap = c->list_capacity > 0 ? c->list_capacity : (long long)nl * 96 + 1024;
     if ((rc = c->arena.ensure(sizeof(int) * (size_t)arena_cap))) return rc;
     arena_cap = (long long)(c->arena.bytes / sizeof(int));
@@ -729,16 +741,19 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     la.queue = nullptr;
     if (queue) {
       // one launch: a warp takes the next slot of the queue and waits until
-      // the parent of the node there has pushed it; the system roots start it
-      // every walkable node, leaves included: all nodes but the nsys - 1 that
-      // span several systems (the binary tree above the system roots)
-      la.q_total = nn - (c->nsys - 1);
+      // the item there has been pushed.  Node queue: every walkable node,
+      // leaves included (all nodes but the nsys - 1 that span several
+      // systems), the system roots first.  Pair queue: the system roots and
+      // the children of every walkable internal node, nsys + (nn - nsys + 1 -
+      // nl) = nn + 1 - nl items
+      la.q_total = pairs ? nn + 1 - nl : nn - (c->nsys - 1);
       if ((rc = c->wqueue.ensure(sizeof(int) * (size_t)(la.q_total + 1)))) return rc;
       la.queue = c->wqueue.as<int>();
       la.q_head = reinterpret_cast<int*>(ctr + 14);
       la.q_tail = reinterpret_cast<int*>(ctr + 15);
       SFMM_CUDA_TRY(cudaMemsetAsync(la.queue, 0xff, sizeof(int) * (size_t)la.q_total, c->stream));
-      k_queue_seed<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), la.queue, la.q_tail);
+      if (pairs) k_queue_seed_pairs<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), la.queue, la.q_tail);
+      else k_queue_seed<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), la.queue, la.q_tail);
       la.level = 0;
       la.level_nodes = nullptr;
       la.level_begin = 0;
@@ -747,7 +762,8 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
         // one block per resident slot (the queue needs none resident: a warp
         // only takes a slot while it runs, and a node's parent always holds
         // an earlier slot)
-        k_walk_level<P, F32, false, true><<<q_blocks, WALK_NT, 0, c->stream>>>(la);
+        if (pairs) k_walk_pair<P, F32><<<q_blocks, WALK_NT, 0, c->stream>>>(la);
+        else k_walk_level<P, F32, false, true><<<q_blocks, WALK_NT, 0, c->stream>>>(la);
         ++c->nlaunch;
       }
       ++c->nlaunch;

@@ -27,8 +27,10 @@ def momentum_residual(m, acc):
 
 # walk forms under test: 0 per-leaf replay (Algorithm 1), 1 per-node shared
 # pairs with one launch per depth, 2 one-sided symmetric pairs, 3 per-node
-# shared pairs taken from the readiness queue
-WALKS = {0: {"walk": 0}, 1: {"walk": 1, "schedule": 1}, 2: {"walk": 2}, 3: {"walk": 1, "schedule": 2}}
+# shared pairs taken from the readiness queue of nodes, 4 the same from the
+# readiness queue of sibling pairs
+WALKS = {0: {"walk": 0}, 1: {"walk": 1, "schedule": 1}, 2: {"walk": 2}, 3: {"walk": 1, "schedule": 2},
+         4: {"walk": 1, "schedule": 3}}
 
 
 def solver(prec, walk=None, **opts):

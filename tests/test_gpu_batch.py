@@ -28,7 +28,7 @@ def _batch(seed=5):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("walk", [0, 1, 3])
+@pytest.mark.parametrize("walk", [0, 1, 3, 4])
 def test_batch_matches_oracle_per_system(prec, walk):
     ps, ms, hs, off, lsz = _batch()
     s = solver(prec, walk=walk)

@@ -137,12 +137,12 @@ def test_uniform_sphere_1e4_fp64_matches_oracle_and_direct():
 
 @pytest.mark.parametrize("name", ["plummer_1e6", "clustered_1.6e7"])
 def test_full_size_schedules_agree_bitwise(name):
-    """One launch per depth and the readiness queue give bitwise the same
-    result at full size (the automatic choice takes the queue for the first
-    tree and per-depth launches for the second)."""
+    """One launch per depth and both readiness queues give bitwise the same
+    result at full size (the automatic choice takes the queue of nodes for
+    the first tree and the queue of sibling pairs for the second)."""
     pos, m, h, w, t = _system(name)
     out = []
-    for sched in (1, 2):
+    for sched in (1, 2, 3):
         s = solver("fp32", walk=1, schedule=sched)
         s.build(pos, m, h, w["leaf_size"])
         acc, pot = s.gravity(w["theta"], 2)

@@ -43,7 +43,7 @@ def test_kd_tree_matches_oracle(kind, n, ls):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("walk", [0, 1, 3])
+@pytest.mark.parametrize("walk", [0, 1, 3, 4])
 @pytest.mark.parametrize("theta", [0.3, 0.6])
 def test_sfmm_on_kd_tree_matches_oracle(prec, walk, theta):
     pos, m, h = workloads.plummer(6000, 23)

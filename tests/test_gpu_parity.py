@@ -126,7 +126,7 @@ PARITY = [("uniform", 6000, 10, 0.5, 2), ("plummer", 8001, 16, 0.5, 2), ("plumme
           ("plummer", 2500, 1, 0.5, 2), ("uniform", 1000, 64, 0.9, 2)]
 
 
-@pytest.mark.parametrize("walk", [0, 1, 2, 3])
+@pytest.mark.parametrize("walk", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("kind,n,ls,theta,p", PARITY)
 def test_fp64_form_matches_oracle(kind, n, ls, theta, p, walk):
     pos, m, h = _set(kind, n, 17)
@@ -146,7 +146,7 @@ def test_fp64_form_matches_oracle(kind, n, ls, theta, p, walk):
     assert abs(st["W"] - 0.5 * (m * pot_o).sum()) <= 1e-10 * abs(st["W"])
 
 
-@pytest.mark.parametrize("walk", [0, 1, 2, 3])
+@pytest.mark.parametrize("walk", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("kind,n,ls,theta,p", PARITY)
 def test_fp32_form_matches_oracle(kind, n, ls, theta, p, walk):
     pos, m, h = _set(kind, n, 17)
@@ -296,7 +296,7 @@ def test_shared_walk_equals_replay(prec, tol):
     assert pot_rel(p1, p0).max() <= tol
 
 
-@pytest.mark.parametrize("walk", [1, 3])
+@pytest.mark.parametrize("walk", [1, 3, 4])
 def test_shared_walk_capacity_regrow(walk):
     pos, m, h = workloads.plummer(6000, 12)
     acc_o, pot_o, _ = oracle.sfmm(pos, m, h, theta=0.3, p=2, leaf_size=16)
@@ -307,7 +307,7 @@ def test_shared_walk_capacity_regrow(walk):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("walk", [0, 1, 3])
+@pytest.mark.parametrize("walk", [0, 1, 3, 4])
 def test_long_lists_split_into_chunks(prec, walk):
     """Neighbour lists longer than one chunk are evaluated as several work
     items and recombined in chunk order: the result still matches the
@@ -356,7 +356,7 @@ def test_one_sided_symmetric_pairs_equal_shared_walk(prec, tol):
         assert momentum_residual(m, a2) <= TOL_MOM_FP64
 
 
-@pytest.mark.parametrize("walk", [0, 1, 2, 3])
+@pytest.mark.parametrize("walk", [0, 1, 2, 3, 4])
 def test_small_theta_grows_buffers_and_matches_oracle(walk):
     """theta = 0.1: almost every pair is done pairwise, lists are long and
     several work buffers must grow (regrow and retry inside the call)."""
@@ -374,14 +374,14 @@ def test_small_theta_grows_buffers_and_matches_oracle(walk):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("kind,n,theta", [("plummer", 40000, 0.5), ("binary", 30000, 0.3)])
 def test_queue_walk_equals_level_walk(prec, kind, n, theta):
-    """The readiness queue runs the per-node shared walk as one launch over
-    nodes whose parents are done, instead of one launch per depth: every
-    node does the same arithmetic on the same inherited list, so the
-    results are bitwise the same, and so are those of the automatic
-    choice."""
+    """The readiness queues run the per-node shared walk as one launch over
+    nodes (or sibling pairs) whose parents are done, instead of one launch
+    per depth: every node does the same arithmetic on the same inherited
+    list in the same order, so the results are bitwise the same, and so are
+    those of the automatic choice."""
     pos, m, h = _set(kind, n, 47)
     out = []
-    for walk in (1, 3):
+    for walk in (1, 3, 4):
         s = solver(prec, walk=walk)
         s.build(pos, m, h, 16)
         acc, pot = s.gravity(theta, 2)
@@ -402,7 +402,7 @@ def test_schedule_option_is_checked():
     from paper_2602_05804_gb300 import sfmm
 
     s = solver("fp32")
-    for bad in (-1, 3, 0.5):
+    for bad in (-1, 4, 0.5):
         with pytest.raises(sfmm.SFMMError) as e:
             s.set_option("schedule", bad)
         assert e.value.code == sfmm.SFMM_EINVAL
