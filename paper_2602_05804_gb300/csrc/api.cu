@@ -45,14 +45,22 @@ int set_error(sfmm_ctx* c, int code, const char* msg) {
 }
 
 // Read (and clear) the device status word: one stream synchronisation.
-int sync_status(sfmm_ctx* c, int* bits) {
+// With `counts`, the build's node and leaf counts come back in the same
+// synchronisation (into c->nnodes, c->nleaves).
+int sync_status(sfmm_ctx* c, int* bits, bool counts) {
   cudaError_t e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && counts)
+    e = cudaMemcpyAsync(c->h_status + 1, c->d_counts, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     c->last_error = cudaGetErrorString(e);
     return (e == cudaErrorMemoryAllocation) ? SFMM_ENOMEM : SFMM_ECUDA;
   }
   *bits = *c->h_status;
+  if (counts) {
+    c->nnodes = c->h_status[1];
+    c->nleaves = c->h_status[2];
+  }
   if (*bits) {
     e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return SFMM_ECUDA;
@@ -140,7 +148,7 @@ int sfmm_create(sfmm_ctx** out, int device, int precision, void* stream) {
     c->owns_stream = true;
   }
   bool ok = cudaMalloc(&c->d_status, sizeof(int)) == cudaSuccess &&
-            cudaMallocHost(&c->h_status, sizeof(int)) == cudaSuccess &&
+            cudaMallocHost(&c->h_status, 4 * sizeof(int)) == cudaSuccess &&
             cudaMallocHost(&c->h_scalars, 64 * sizeof(double)) == cudaSuccess &&
             cudaMemset(c->d_status, 0, sizeof(int)) == cudaSuccess;
   for (int i = 0; ok && i < 8; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
@@ -294,7 +302,7 @@ int build_common(sfmm_ctx* c, const double* pos, const double* mass, const doubl
   if (rc) return set_error(c, rc, "tree build failed");
   if (c->profile) cudaEventRecord(c->ev[1], c->stream);
   int bits = 0;
-  if ((rc = sync_status(c, &bits))) return rc;
+  if ((rc = sync_status(c, &bits, true))) return rc;
   if (bits & (SFMM_ST_NONFINITE | SFMM_ST_NONPOSITIVE))
     return set_error(c, SFMM_ENONFINITE, "non-finite position/mass/h or non-positive mass/h");
   if (bits) return set_error(c, SFMM_ECUDA, "internal consistency check of the tree failed");
@@ -396,30 +404,55 @@ int sfmm_gravity(sfmm_ctx* c, double theta, int order, double* acc, double* pot)
   if (c->moments_order != order) {
     if ((rc = compute_moments(c, order))) return set_error(c, rc, "moment pass failed");
   }
-  if (c->profile) cudaEventRecord(c->ev[3], st);
-  if ((rc = (c->walk_mode >= 1) ? run_walk_shared(c, theta, order) : run_walk(c, theta, order, false, 0, 0))) return rc;
-  if (c->profile) cudaEventRecord(c->ev[4], st);
-  if ((rc = run_p2p(c, acc, pot))) return set_error(c, rc, "near-field pass failed");
-  if (c->profile) cudaEventRecord(c->ev[5], st);
-  double* red = nullptr;
-  if ((rc = run_reduce(c, &red))) return set_error(c, rc, "reduction failed");
-  if (c->nsys > 1 && (rc = run_reduce_systems(c))) return set_error(c, rc, "reduction failed");
-  if (c->profile) cudaEventRecord(c->ev[6], st);
-  cudaError_t e = cudaMemcpyAsync(c->h_scalars + 16, red, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess)  // pair evaluations, counted by the near-field pass
-    e = cudaMemcpyAsync(c->h_scalars + 24, c->counters.as<unsigned long long>() + 3, sizeof(unsigned long long),
-                        cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return set_error(c, SFMM_ECUDA, cudaGetErrorString(e));
-  int bits = 0;
-  if ((rc = sync_status(c, &bits))) return rc;
-  if (bits) return set_error(c, SFMM_ECUDA, "device status error after the near-field pass");
+  // walk, near field and sums are issued without a host wait; one
+  // synchronisation at the end reads the status word, the sums and the
+  // walk's counters.  A walk buffer that ran out sets a status bit: grow it
+  // and run again (the partial results are overwritten)
+  unsigned long long* hs = reinterpret_cast<unsigned long long*>(c->h_scalars + 32);
+  for (int attempt = 0;; ++attempt) {
+    if (c->profile) cudaEventRecord(c->ev[3], st);
+    if ((rc = (c->walk_mode >= 1) ? run_walk_shared(c, theta, order) : run_walk(c, theta, order, false, 0, 0)))
+      return rc;
+    if (c->profile) cudaEventRecord(c->ev[4], st);
+    if ((rc = run_p2p(c, acc, pot))) return set_error(c, rc, "near-field pass failed");
+    if (c->profile) cudaEventRecord(c->ev[5], st);
+    double* red = nullptr;
+    if ((rc = run_reduce(c, &red))) return set_error(c, rc, "reduction failed");
+    if (c->nsys > 1 && (rc = run_reduce_systems(c))) return set_error(c, rc, "reduction failed");
+    if (c->profile) cudaEventRecord(c->ev[6], st);
+    cudaError_t e = cudaMemcpyAsync(c->h_scalars + 16, red, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)  // walk counters (statistics, buffer needs) and pair evaluations
+      e = cudaMemcpyAsync(hs, c->counters.p, 20 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return set_error(c, SFMM_ECUDA, cudaGetErrorString(e));
+    int bits = 0;
+    if ((rc = sync_status(c, &bits))) return rc;
+    if (bits & SFMM_ST_DEPTH) return set_error(c, SFMM_ESTACK, "tree deeper than supported");
+    if (c->walk_mode >= 1 && (bits & (SFMM_ST_RING | SFMM_ST_ARENA | SFMM_ST_CHILDLIST)) &&
+        !(bits & ~(SFMM_ST_RING | SFMM_ST_ARENA | SFMM_ST_CHILDLIST | SFMM_ST_INTERNAL))) {
+      // (an overflowing walk can leave the long-list split inconsistent:
+      // SFMM_ST_INTERNAL then comes with a capacity bit and goes with it)
+      if (attempt == SFMM_WALK_ATTEMPTS - 1)
+        return set_error(c, SFMM_ECAPACITY, "walk buffers too small after the last regrow");
+      walk_shared_regrow(c, bits, hs);
+      continue;
+    }
+    if (bits & SFMM_ST_INTERNAL) return set_error(c, SFMM_ECUDA, "walk: internal consistency check failed");
+    if (bits) return set_error(c, SFMM_ECUDA, "device status error after the near-field pass");
+    break;
+  }
+  if (c->walk_mode >= 1) {
+    c->stats.m2l = (int64_t)hs[0];
+    c->stats.m2l_unique = (int64_t)hs[1];
+    c->stats.p2p_leaves = (int64_t)hs[2];
+    c->stats.mac_fallbacks = (int64_t)hs[4];
+  }
   const double* r = c->h_scalars + 16;
   c->stats.momentum[0] = r[0];
   c->stats.momentum[1] = r[1];
   c->stats.momentum[2] = r[2];
   c->stats.abs_momentum = r[3];
   c->stats.W = 0.5 * r[4];
-  c->stats.p2p_pairs = (int64_t) * reinterpret_cast<const unsigned long long*>(c->h_scalars + 24);
+  c->stats.p2p_pairs = (int64_t)hs[3];
   if (c->profile) {
     c->stats.ms_moments = elapsed(c->ev[2], c->ev[3]);
     c->stats.ms_walk = elapsed(c->ev[3], c->ev[4]);

@@ -8,6 +8,7 @@
 // all lanes work for any leaf size; sources are staged per warp in shared
 // memory, converted once to coordinates relative to the target leaf's
 // centre (FP32 form).
+#include <algorithm>
 #include <type_traits>
 
 #include "sfmm_internal.cuh"
@@ -48,8 +49,10 @@ struct P2PArgs {
   double* pot;
   // long lists: work items [0, nextra) are the further chunks (leaf, chunk)
   // of split lists, items [nextra, nextra + nleaves) the first chunk of every
-  // leaf; a split leaf's chunk k writes its sums to partial slot split[leaf] + k
-  int nextra;
+  // leaf; a split leaf's chunk k writes its sums to partial slot split[leaf] + k.
+  // The counts come from the split pass on the device: d_split[0] extra
+  // items, [1] partial slots, [2] split leaves
+  const unsigned long long* d_split;
   const int2* extra;
   const int* split;   // per leaf: first partial slot, -1 (or NULL array) if unsplit
   const int* slist;   // the split leaves
@@ -198,7 +201,8 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
-  const int nitems = a.nextra + a.nleaves;
+  const int nextra = (int)a.d_split[0];
+  const int nitems = nextra + a.nleaves;
   unsigned long long pairs = 0;  // this lane's share of the pair evaluations
   while (true) {
     int item = 0;
@@ -206,12 +210,12 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
     item = __shfl_sync(SFMM_FULL, item, 0);
     if (item >= nitems) break;
     int leaf, chunk = 0;
-    if (item < a.nextra) {
+    if (item < nextra) {
       const int2 x = a.extra[item];
       leaf = x.x;
       chunk = x.y;
     } else {
-      leaf = item - a.nextra;
+      leaf = item - nextra;
     }
     const int pslot = a.split ? a.split[leaf] : -1;
     const int L = a.leaf_node[leaf];
@@ -660,7 +664,8 @@ __global__ void k_p2p_split(int nleaves, const int* __restrict__ p2p_cnt, int* _
 // Split leaves: one warp per leaf sums the chunks' partial sums in chunk
 // order (so reruns are bitwise identical) and finishes as an unsplit leaf.
 template <bool F32>
-__global__ void k_p2p_combine(const P2PArgs a, int nsplit) {
+__global__ void k_p2p_combine(const P2PArgs a) {
+  const int nsplit = (int)a.d_split[2];
   using R = typename std::conditional<F32, float, double>::type;
   const int lane = threadIdx.x & 31;
   const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -796,23 +801,25 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   unsigned long long* ctr = c->counters.as<unsigned long long>();
   SFMM_CUDA_TRY(cudaMemsetAsync(ctr + 10, 0, 4 * sizeof(unsigned long long), c->stream));
   const bool f32 = (c->precision == SFMM_FP32);
-  // long lists (counted exactly by the walk): slots, extra items, split leaves
-  const int nsplit = (int)c->split_lists;
-  const int nslots = (int)c->split_chunks;
-  const int nextra = nslots - nsplit;
+  // long lists: slots, extra items and split leaves are counted by the split
+  // pass on the device; the buffers are sized from bounds on the host (a list
+  // of cnt > chunk entries takes ceil(cnt / chunk) <= 2 cnt / chunk slots, so
+  // all of them fit 2 arena / chunk), with no wait for the walk
+  const int64_t arena_cap = (int64_t)(c->arena.bytes / sizeof(int));
+  const int nslots = (int)std::min<int64_t>(2 * arena_cap / c->p2p_chunk + 2, INT32_MAX / 2);
+  const int nsplit = (int)std::min<int64_t>(std::min<int64_t>(nl, arena_cap / (c->p2p_chunk + 1) + 1), nslots);
+  const int nextra = nslots;
   int lmax = c->leaf_size;
   for (int v : c->h_sys_lsz) lmax = v > lmax ? v : lmax;
-  if (nsplit > 0) {
-    if ((rc = c->p2p_split.ensure(sizeof(int) * (size_t)nl))) return rc;
-    if ((rc = c->p2p_extra.ensure(sizeof(int2) * (size_t)nextra))) return rc;
-    if ((rc = c->p2p_slist.ensure(sizeof(int) * (size_t)nsplit))) return rc;
-    if ((rc = c->p2p_part.ensure((f32 ? sizeof(float) : sizeof(double)) * 4 * (size_t)lmax * nslots))) return rc;
-    k_p2p_split<<<(nl + 255) / 256, 256, 0, c->stream>>>(nl, c->p2p_cnt.as<int>(), c->p2p_split.as<int>(),
-                                                       c->p2p_extra.as<int2>(), c->p2p_slist.as<int>(), ctr + 11,
-                                                       nextra, nslots, nsplit, c->p2p_chunk, c->d_status);
-    ++c->nlaunch;
-    SFMM_CUDA_TRY(cudaGetLastError());
-  }
+  if ((rc = c->p2p_split.ensure(sizeof(int) * (size_t)nl))) return rc;
+  if ((rc = c->p2p_extra.ensure(sizeof(int2) * (size_t)nextra))) return rc;
+  if ((rc = c->p2p_slist.ensure(sizeof(int) * (size_t)nsplit))) return rc;
+  if ((rc = c->p2p_part.ensure((f32 ? sizeof(float) : sizeof(double)) * 4 * (size_t)lmax * nslots))) return rc;
+  k_p2p_split<<<(nl + 255) / 256, 256, 0, c->stream>>>(nl, c->p2p_cnt.as<int>(), c->p2p_split.as<int>(),
+                                                     c->p2p_extra.as<int2>(), c->p2p_slist.as<int>(), ctr + 11,
+                                                     nextra, nslots, nsplit, c->p2p_chunk, c->d_status);
+  ++c->nlaunch;
+  SFMM_CUDA_TRY(cudaGetLastError());
   P2PArgs a{};
   a.nleaves = nl;
   a.leaf_node = c->leaf_node.as<int>();
@@ -841,11 +848,11 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   a.leaf_counter = reinterpret_cast<int*>(ctr + 10);
   a.acc = acc;
   a.pot = pot;
-  a.nextra = nsplit > 0 ? nextra : 0;
-  a.extra = nsplit > 0 ? c->p2p_extra.as<int2>() : nullptr;
-  a.split = nsplit > 0 ? c->p2p_split.as<int>() : nullptr;
-  a.slist = nsplit > 0 ? c->p2p_slist.as<int>() : nullptr;
-  a.part = nsplit > 0 ? c->p2p_part.p : nullptr;
+  a.d_split = ctr + 11;
+  a.extra = c->p2p_extra.as<int2>();
+  a.split = c->p2p_split.as<int>();
+  a.slist = c->p2p_slist.as<int>();
+  a.part = c->p2p_part.p;
   a.lmax = lmax;
   a.chunk = c->p2p_chunk;
   a.pair_counter = ctr + 3;
@@ -860,10 +867,11 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   else k_p2p<false><<<nblocks, nt, 0, c->stream>>>(a);
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
-  if (nsplit > 0) {
-    const int cblocks = (nsplit + 7) / 8;
-    if (f32) k_p2p_combine<true><<<cblocks, 256, 0, c->stream>>>(a, nsplit);
-    else k_p2p_combine<false><<<cblocks, 256, 0, c->stream>>>(a, nsplit);
+  {
+    // split leaves (their count is on the device): a persistent grid
+    const int cblocks = std::min(2 * num_sms(c->device), (nsplit + 7) / 8 + 1);
+    if (f32) k_p2p_combine<true><<<cblocks, 256, 0, c->stream>>>(a);
+    else k_p2p_combine<false><<<cblocks, 256, 0, c->stream>>>(a);
     ++c->nlaunch;
     SFMM_CUDA_TRY(cudaGetLastError());
   }

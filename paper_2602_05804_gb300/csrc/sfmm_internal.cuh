@@ -45,7 +45,8 @@ struct sfmm_ctx {
   std::vector<int64_t> h_sys_off;
   std::vector<int> h_sys_lsz;
   DevBuf sys_off, sys_lsz, psys, sys_root, wparent, sys_sums;
-  int32_t nnodes = 0, nleaves = 0;
+  int32_t nnodes = 0, nleaves = 0;  // host copies, valid once a build has returned
+  uint32_t* d_counts = nullptr;      // device: node count, leaf count of the current build
   int moments_order = -1;  // order of the cached moments (-1: none)
   bool moments_fp64 = false;  // the cached moments include the FP64 rows (else FP32 only)
   int pref_order = 2;      // order the build computes moments for (the last gravity call's)
@@ -108,6 +109,7 @@ struct sfmm_ctx {
   const double* red_pot = nullptr;
   int64_t arena_used = 0;
   int64_t split_chunks = 0, split_lists = 0;  // from the walk: chunks of split lists, split lists
+  int64_t walk_arena_cap = 0, walk_cf_cap = 0;  // list and child-list capacities of the last walk
 
   // status word (device) + pinned host mirror
   int* d_status = nullptr;
@@ -145,8 +147,10 @@ int exclusive_scan_u32(sfmm_ctx* c, uint32_t* data, int64_t n, uint32_t* total_d
 // moments.cu
 int compute_moments(sfmm_ctx* c, int order);
 
-// walk_shared.cu
+// walk_shared.cu: launches only (no host wait); the caller checks the status
+// word and calls walk_shared_regrow on capacity bits
 int run_walk_shared(sfmm_ctx* c, double theta, int order);
+int walk_shared_regrow(sfmm_ctx* c, int bits, const unsigned long long* hs);
 
 // walk.cu
 int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, int64_t cap_p2p);
@@ -165,7 +169,7 @@ int tuned_knobs(sfmm_ctx* c, double theta, int order, double* acc, bool run_tria
 int p2p_blocks_fit(sfmm_ctx* c);  // near-field blocks per SM that fit (p2p.cu)
 
 int check_status(sfmm_ctx* c);
-int sync_status(sfmm_ctx* c, int* bits);
+int sync_status(sfmm_ctx* c, int* bits, bool counts = false);
 
 inline int num_sms(int device) {
   int v = 0;

@@ -658,7 +658,7 @@ __global__ void k_fill_nodes(int n, const LeafRule lr, const int* __restrict__ k
                              const int* __restrict__ par_int, const int* __restrict__ par_leaf,
                              const int* __restrict__ pre_int, const int* __restrict__ pre_leaf,
                              int* __restrict__ nfirst, int* __restrict__ ncount, int* __restrict__ nright,
-                             int* __restrict__ nparent, uint32_t* __restrict__ isleaf, int* __restrict__ status) {
+                             int* __restrict__ nparent, uint32_t* __restrict__ lstart, int* __restrict__ status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n - 1) {
     int v = pre_int[i];
@@ -669,14 +669,13 @@ __global__ void k_fill_nodes(int n, const LeafRule lr, const int* __restrict__ k
       nparent[v] = (i == 0) ? -1 : pre_int[par_int[i]];
       if (!lr.splits(kf[i], kla[i])) {
         nright[v] = -1;
-        isleaf[v] = 1u;
+        lstart[kf[i]] = 1u;
       } else {
         int L = kl[i], R = kr[i];
         int pl = (L >= 0) ? pre_int[L] : pre_leaf[~L];
         int pr = (R >= 0) ? pre_int[R] : pre_leaf[~R];
         if (pl != v + 1) atomicOr(status, SFMM_ST_INTERNAL);
         nright[v] = pr;
-        isleaf[v] = 0u;
       }
     }
   }
@@ -687,41 +686,53 @@ __global__ void k_fill_nodes(int n, const LeafRule lr, const int* __restrict__ k
       ncount[v] = 1;
       nright[v] = -1;
       nparent[v] = pre_int[par_leaf[i]];
-      isleaf[v] = 1u;
+      lstart[i] = 1u;
     }
   }
 }
 
 // Walk parent of every node: the parent, -1 at a system's root, -2 for nodes
 // spanning several systems (never walked); the root node of each system.
-__global__ void k_sysroots(int nn, const int* __restrict__ psys, const int* __restrict__ nfirst,
+__global__ void k_sysroots(const uint32_t* __restrict__ counts, const int* __restrict__ psys, const int* __restrict__ nfirst,
                            const int* __restrict__ ncount, const int* __restrict__ nparent, int* __restrict__ wparent,
                            int* __restrict__ sys_root) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nn) return;
-  const int f = nfirst[v], l = f + ncount[v] - 1;
-  const int p = nparent[v];
-  if (!psys) {
-    wparent[v] = p;
-    if (p < 0) sys_root[0] = v;
-    return;
+  const int nn = (int)counts[0];
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+    const int f = nfirst[v], l = f + ncount[v] - 1;
+    const int p = nparent[v];
+    if (!psys) {
+      wparent[v] = p;
+      if (p < 0) sys_root[0] = v;
+      continue;
+    }
+    const int sv = psys[f];
+    if (sv != psys[l]) {
+      wparent[v] = -2;
+      continue;
+    }
+    const bool root = (p < 0) || (psys[nfirst[p]] != psys[nfirst[p] + ncount[p] - 1]);
+    wparent[v] = root ? -1 : p;
+    if (root) sys_root[sv] = v;
   }
-  const int sv = psys[f];
-  if (sv != psys[l]) {
-    wparent[v] = -2;
-    return;
-  }
-  const bool root = (p < 0) || (psys[nfirst[p]] != psys[nfirst[p] + ncount[p] - 1]);
-  wparent[v] = root ? -1 : p;
-  if (root) sys_root[sv] = v;
 }
 
-// isleaf has been exclusive-scanned into leaf indices; record the leaves.
-__global__ void k_leaf_list(int nn, const int* __restrict__ nright, const uint32_t* __restrict__ lidx,
-                            int* __restrict__ leaf_node) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nn) return;
-  if (nright[v] < 0) leaf_node[lidx[v]] = v;
+// Leaf numbers: lstart holds the exclusive scan over particles of the
+// leaf-start flags, so the leaves before node v in pre-order are those that
+// start before its first particle: leaf_index[v] = lstart[first[v]] (a
+// leaf's own number).  Records the leaves, and clears each node's arrival
+// flag and size bits for the passes that follow.
+__global__ void k_leaf_list(const uint32_t* __restrict__ counts, const int* __restrict__ nfirst,
+                            const int* __restrict__ nright, const uint32_t* __restrict__ lstart,
+                            uint32_t* __restrict__ leaf_index, int* __restrict__ leaf_node, int* __restrict__ flags,
+                            unsigned long long* __restrict__ l2bits) {
+  const int nn = (int)counts[0];
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+    const uint32_t q = lstart[nfirst[v]];
+    leaf_index[v] = q;
+    if (nright[v] < 0) leaf_node[q] = v;
+    flags[v] = 0;
+    l2bits[v] = 0ull;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -782,7 +793,7 @@ __device__ __forceinline__ void load_moments(int u, QT (&q)[NQ], const double* Q
 // P >= 0: also the leaf's scaled moments of order P about its centre of mass
 // (P2M, Eq. massmom) in FP64 and their FP32 copy; P < 0: geometry only.
 template <int P, typename QT>
-__global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
+__global__ void k_leaf_geom(const uint32_t* __restrict__ counts, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
                             const int* __restrict__ ncount, const double* __restrict__ px,
                             const double* __restrict__ py, const double* __restrict__ pz,
                             const double* __restrict__ pm, const double* __restrict__ ph,
@@ -790,58 +801,59 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
                             double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ pnode,
                             int* __restrict__ nlu, double* __restrict__ extv, int* __restrict__ exti,
                             double* __restrict__ Qd, float* __restrict__ Qf, int nqs) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nleaves) return;
-  const int v = leaf_node[q];
-  const int f = nfirst[v], cnt = ncount[v];
-  double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, hm = 0.0;
-  // extreme particles per axis (min x, y, z, max x, y, z; first one on ties)
-  double ev[6] = {px[f], py[f], pz[f], px[f], py[f], pz[f]};
-  long long ek[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) ek[c] = dkey(ev[c]);
-  int ei[6] = {f, f, f, f, f, f};
-  for (int i = f; i < f + cnt; ++i) {
-    const double m = pm[i];
-    M = dadd(M, m);
-    sx = dadd(sx, dmul(m, px[i]));
-    sy = dadd(sy, dmul(m, py[i]));
-    sz = dadd(sz, dmul(m, pz[i]));
-    hm = dmax_pos(hm, ph[i]);
-    pnode[i] = v;
-    const double xc[3] = {px[i], py[i], pz[i]};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const long long k = dkey(xc[c]);
-      if (k < ek[c]) { ek[c] = k; ev[c] = xc[c]; ei[c] = i; }
-      if (k > ek[3 + c]) { ek[3 + c] = k; ev[3 + c] = xc[c]; ei[3 + c] = i; }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    extv[6 * (size_t)v + c] = ev[c];
-    exti[6 * (size_t)v + c] = ei[c];
-  }
-  nmass[v] = M;
-  const double cx = __ddiv_rn(sx, M), cy = __ddiv_rn(sy, M), cz = __ddiv_rn(sz, M);
-  ncx[v] = cx;
-  ncy[v] = cy;
-  ncz[v] = cz;
-  nhmax[v] = hm;
-  nlu[v] = 1;
-  if constexpr (P >= 0) {
-    constexpr int NQ = MomOps<P>::NQ;
-    QT acc[NQ];
-#pragma unroll
-    for (int k = 0; k < NQ; ++k) acc[k] = QT(0);
+  const int nleaves = (int)counts[1];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
+    const int v = leaf_node[q];
+    const int f = nfirst[v], cnt = ncount[v];
+    double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, hm = 0.0;
+    // extreme particles per axis (min x, y, z, max x, y, z; first one on ties)
+    double ev[6] = {px[f], py[f], pz[f], px[f], py[f], pz[f]};
+    long long ek[6];
+  #pragma unroll
+    for (int c = 0; c < 6; ++c) ek[c] = dkey(ev[c]);
+    int ei[6] = {f, f, f, f, f, f};
     for (int i = f; i < f + cnt; ++i) {
-      QT mono[NQ];
-      MomOps<P>::mono((QT)(px[i] - cx), (QT)(py[i] - cy), (QT)(pz[i] - cz), mono);
-      const QT m = (QT)pm[i];
-#pragma unroll
-      for (int k = 0; k < NQ; ++k) acc[k] = fma(m, mono[k], acc[k]);
+      const double m = pm[i];
+      M = dadd(M, m);
+      sx = dadd(sx, dmul(m, px[i]));
+      sy = dadd(sy, dmul(m, py[i]));
+      sz = dadd(sz, dmul(m, pz[i]));
+      hm = dmax_pos(hm, ph[i]);
+      pnode[i] = v;
+      const double xc[3] = {px[i], py[i], pz[i]};
+  #pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const long long k = dkey(xc[c]);
+        if (k < ek[c]) { ek[c] = k; ev[c] = xc[c]; ei[c] = i; }
+        if (k > ek[3 + c]) { ek[3 + c] = k; ev[3 + c] = xc[c]; ei[3 + c] = i; }
+      }
     }
-    store_moments<NQ>(v, acc, M, Qd, Qf);
+  #pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      extv[6 * (size_t)v + c] = ev[c];
+      exti[6 * (size_t)v + c] = ei[c];
+    }
+    nmass[v] = M;
+    const double cx = __ddiv_rn(sx, M), cy = __ddiv_rn(sy, M), cz = __ddiv_rn(sz, M);
+    ncx[v] = cx;
+    ncy[v] = cy;
+    ncz[v] = cz;
+    nhmax[v] = hm;
+    nlu[v] = 1;
+    if constexpr (P >= 0) {
+      constexpr int NQ = MomOps<P>::NQ;
+      QT acc[NQ];
+  #pragma unroll
+      for (int k = 0; k < NQ; ++k) acc[k] = QT(0);
+      for (int i = f; i < f + cnt; ++i) {
+        QT mono[NQ];
+        MomOps<P>::mono((QT)(px[i] - cx), (QT)(py[i] - cy), (QT)(pz[i] - cz), mono);
+        const QT m = (QT)pm[i];
+  #pragma unroll
+        for (int k = 0; k < NQ; ++k) acc[k] = fma(m, mono[k], acc[k]);
+      }
+      store_moments<NQ>(v, acc, M, Qd, Qf);
+    }
   }
 }
 
@@ -849,61 +861,62 @@ __global__ void k_leaf_geom(int nleaves, const int* __restrict__ leaf_node, cons
 // the parent's moments, both children's translated to its centre, Eq.
 // massmomtrans).
 template <int P, typename QT>
-__global__ void k_upward(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nparent,
+__global__ void k_upward(const uint32_t* __restrict__ counts, const int* __restrict__ leaf_node, const int* __restrict__ nparent,
                          const int* __restrict__ nright, double* ncx, double* ncy, double* ncz, double* nmass,
                          double* nhmax, int* nlu, int* flags, double* extv, int* exti, double* Qd, float* Qf,
                          int nqs) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nleaves) return;
-  int v = nparent[leaf_node[q]];
-  while (v >= 0) {
-    {
-      // release this child's records, acquire the sibling's
-      cuda::atomic_ref<int, cuda::thread_scope_device> arrive(flags[v]);
-      if (arrive.fetch_add(1, cuda::memory_order_acq_rel) == 0) return;
-    }
-    int L = v + 1, R = nright[v];
-    double mL = __ldcg(&nmass[L]), mR = __ldcg(&nmass[R]);
-    double M = dadd(mL, mR);
-    const double cLx = __ldcg(&ncx[L]), cLy = __ldcg(&ncy[L]), cLz = __ldcg(&ncz[L]);
-    const double cRx = __ldcg(&ncx[R]), cRy = __ldcg(&ncy[R]), cRz = __ldcg(&ncz[R]);
-    // one division per node (GB300's FP64 pipe is narrow): the centre is
-    // within rounding of the quotient, like the oracle's own sum
-    const double iM = 1.0 / M;
-    const double cx = dmul(dadd(dmul(mL, cLx), dmul(mR, cRx)), iM);
-    const double cy = dmul(dadd(dmul(mL, cLy), dmul(mR, cRy)), iM);
-    const double cz = dmul(dadd(dmul(mL, cLz), dmul(mR, cRz)), iM);
-    ncx[v] = cx;
-    ncy[v] = cy;
-    ncz[v] = cz;
-    if constexpr (P >= 0) {
-      constexpr int NQ = MomOps<P>::NQ;
-      QT qp[NQ];
-#pragma unroll
-      for (int k = 0; k < NQ; ++k) qp[k] = QT(0);
-      const int kids[2] = {L, R};
-      const double kx[2] = {cLx, cRx}, ky[2] = {cLy, cRy}, kz[2] = {cLz, cRz};
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        QT g[NQ], qc[NQ];
-        MomOps<P>::mono((QT)(kx[c] - cx), (QT)(ky[c] - cy), (QT)(kz[c] - cz), g);
-        load_moments<NQ>(kids[c], qc, Qd, Qf);
-        MomOps<P>::m2m(g, qc, qp);
+  const int nleaves = (int)counts[1];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
+    int v = nparent[leaf_node[q]];
+    while (v >= 0) {
+      {
+        // release this child's records, acquire the sibling's
+        cuda::atomic_ref<int, cuda::thread_scope_device> arrive(flags[v]);
+        if (arrive.fetch_add(1, cuda::memory_order_acq_rel) == 0) break;
       }
-      store_moments<NQ>(v, qp, M, Qd, Qf);
+      int L = v + 1, R = nright[v];
+      double mL = __ldcg(&nmass[L]), mR = __ldcg(&nmass[R]);
+      double M = dadd(mL, mR);
+      const double cLx = __ldcg(&ncx[L]), cLy = __ldcg(&ncy[L]), cLz = __ldcg(&ncz[L]);
+      const double cRx = __ldcg(&ncx[R]), cRy = __ldcg(&ncy[R]), cRz = __ldcg(&ncz[R]);
+      // one division per node (GB300's FP64 pipe is narrow): the centre is
+      // within rounding of the quotient, like the oracle's own sum
+      const double iM = 1.0 / M;
+      const double cx = dmul(dadd(dmul(mL, cLx), dmul(mR, cRx)), iM);
+      const double cy = dmul(dadd(dmul(mL, cLy), dmul(mR, cRy)), iM);
+      const double cz = dmul(dadd(dmul(mL, cLz), dmul(mR, cRz)), iM);
+      ncx[v] = cx;
+      ncy[v] = cy;
+      ncz[v] = cz;
+      if constexpr (P >= 0) {
+        constexpr int NQ = MomOps<P>::NQ;
+        QT qp[NQ];
+  #pragma unroll
+        for (int k = 0; k < NQ; ++k) qp[k] = QT(0);
+        const int kids[2] = {L, R};
+        const double kx[2] = {cLx, cRx}, ky[2] = {cLy, cRy}, kz[2] = {cLz, cRz};
+  #pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          QT g[NQ], qc[NQ];
+          MomOps<P>::mono((QT)(kx[c] - cx), (QT)(ky[c] - cy), (QT)(kz[c] - cz), g);
+          load_moments<NQ>(kids[c], qc, Qd, Qf);
+          MomOps<P>::m2m(g, qc, qp);
+        }
+        store_moments<NQ>(v, qp, M, Qd, Qf);
+      }
+      nmass[v] = M;
+      nhmax[v] = dmax_pos(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
+      nlu[v] = __ldcg(&nlu[L]) + __ldcg(&nlu[R]);
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const double a = __ldcg(&extv[6 * (size_t)L + c]), b = __ldcg(&extv[6 * (size_t)R + c]);
+        const long long ka = dkey(a), kb = dkey(b);
+        const bool right = (c < 3) ? (kb < ka) : (kb > ka);
+        extv[6 * (size_t)v + c] = right ? b : a;
+        exti[6 * (size_t)v + c] = __ldcg(&exti[6 * (size_t)(right ? R : L) + c]);
+      }
+      v = nparent[v];
     }
-    nmass[v] = M;
-    nhmax[v] = dmax_pos(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
-    nlu[v] = __ldcg(&nlu[L]) + __ldcg(&nlu[R]);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      const double a = __ldcg(&extv[6 * (size_t)L + c]), b = __ldcg(&extv[6 * (size_t)R + c]);
-      const long long ka = dkey(a), kb = dkey(b);
-      const bool right = (c < 3) ? (kb < ka) : (kb > ka);
-      extv[6 * (size_t)v + c] = right ? b : a;
-      exti[6 * (size_t)v + c] = __ldcg(&exti[6 * (size_t)(right ? R : L) + c]);
-    }
-    v = nparent[v];
   }
 }
 
@@ -924,32 +937,33 @@ __device__ __forceinline__ double exact_d2(double x, double y, double z, double 
   return dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
 }
 
-__global__ void k_node_lb(int nn, const int* __restrict__ wparent, const int* __restrict__ exti,
+__global__ void k_node_lb(const uint32_t* __restrict__ counts, const int* __restrict__ wparent, const int* __restrict__ exti,
                           const double* __restrict__ px, const double* __restrict__ py,
                           const double* __restrict__ pz, const double* __restrict__ ncx,
                           const double* __restrict__ ncy, const double* __restrict__ ncz, double* __restrict__ lb,
                           float4* __restrict__ geo_hi, float4* __restrict__ geo_lo) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nn) return;
-  double m = 0.0;
-  const double cx = ncx[v], cy = ncy[v], cz = ncz[v];
-  if (wparent[v] != -2) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      const int e = exti[6 * (size_t)v + c];
-      m = fmax(m, exact_d2(px[e], py[e], pz[e], cx, cy, cz));
+  const int nn = (int)counts[0];
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+    double m = 0.0;
+    const double cx = ncx[v], cy = ncy[v], cz = ncz[v];
+    if (wparent[v] != -2) {
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const int e = exti[6 * (size_t)v + c];
+        m = fmax(m, exact_d2(px[e], py[e], pz[e], cx, cy, cz));
+      }
     }
+    const double l = __dsqrt_rn(m);
+    lb[v] = l;
+    // the centre as double-float (final records; w: the size, written last)
+    // and, until then, LB rounded down for the FP32 candidate tests
+    float xh, xl, yh, yl, zh, zl;
+    split_double(cx, xh, xl);
+    split_double(cy, yh, yl);
+    split_double(cz, zh, zl);
+    geo_hi[v] = make_float4(xh, yh, zh, __double2float_rd(l));
+    geo_lo[v] = make_float4(xl, yl, zl, 0.0f);
   }
-  const double l = __dsqrt_rn(m);
-  lb[v] = l;
-  // the centre as double-float (final records; w: the size, written last)
-  // and, until then, LB rounded down for the FP32 candidate tests
-  float xh, xl, yh, yl, zh, zl;
-  split_double(cx, xh, xl);
-  split_double(cy, yh, yl);
-  split_double(cz, zh, zl);
-  geo_hi[v] = make_float4(xh, yh, zh, __double2float_rd(l));
-  geo_lo[v] = make_float4(xl, yl, zl, 0.0f);
 }
 
 // Upper bound on the error of an FP32 distance assembled from double-float
@@ -963,42 +977,43 @@ __device__ __forceinline__ float df_dist_err(float ox, float oy, float oz, float
 // Thread per leaf: the leaf's exact size, and which ancestors it is a
 // candidate for (bit k: the ancestor k levels up; beyond 127 levels every
 // ancestor counts as a candidate).
-__global__ void k_size_leaf(int nleaves, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
+__global__ void k_size_leaf(const uint32_t* __restrict__ counts, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
                             const int* __restrict__ ncount, const int* __restrict__ wparent,
                             const double* __restrict__ px, const double* __restrict__ py,
                             const double* __restrict__ pz, const double* __restrict__ ncx,
                             const double* __restrict__ ncy, const double* __restrict__ ncz,
                             const float4* __restrict__ geo_hi, const float4* __restrict__ geo_lo,
                             unsigned long long* __restrict__ l2bits, unsigned long long* __restrict__ cand) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nleaves) return;
-  const int L = leaf_node[q];
-  const int f = nfirst[L], cnt = ncount[L];
-  const double cx = ncx[L], cy = ncy[L], cz = ncz[L];
-  double l2 = 0.0;
-  for (int i = f; i < f + cnt; ++i) l2 = fmax(l2, exact_d2(px[i], py[i], pz[i], cx, cy, cz));
-  l2bits[L] = (unsigned long long)__double_as_longlong(l2);
-  const float lL = __double2float_ru(__dsqrt_rn(l2));
-  const float4 hL = geo_hi[L], oL = geo_lo[L];
-  // an ancestor v is skipped when every particle of the leaf is certainly
-  // closer to s_v than LB(v) (a real particle's distance): |s_L - s_v| + l_L,
-  // with its error bound and one more relative margin for the FP32 sums,
-  // below LB(v) rounded down
-  unsigned long long m0 = 0ull, m1 = 0ull;
-  int k = 1;
-  for (int v = (wparent[L] >= 0) ? wparent[L] : -1; v >= 0; v = wparent[v], ++k) {
-    const float4 hv = geo_hi[v], ov = geo_lo[v];
-    const float dx = df_diff(hL.x, oL.x, hv.x, ov.x), dy = df_diff(hL.y, oL.y, hv.y, ov.y),
-                dz = df_diff(hL.z, oL.z, hv.z, ov.z);
-    const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    const float reach = (d + df_dist_err(dx, dy, dz, hL, hv) + lL) * (1.0f + 1e-6f);
-    if (!(reach < hv.w)) {
-      if (k < 64) m0 |= 1ull << k;
-      else if (k < 128) m1 |= 1ull << (k - 64);
+  const int nleaves = (int)counts[1];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
+    const int L = leaf_node[q];
+    const int f = nfirst[L], cnt = ncount[L];
+    const double cx = ncx[L], cy = ncy[L], cz = ncz[L];
+    double l2 = 0.0;
+    for (int i = f; i < f + cnt; ++i) l2 = fmax(l2, exact_d2(px[i], py[i], pz[i], cx, cy, cz));
+    l2bits[L] = (unsigned long long)__double_as_longlong(l2);
+    const float lL = __double2float_ru(__dsqrt_rn(l2));
+    const float4 hL = geo_hi[L], oL = geo_lo[L];
+    // an ancestor v is skipped when every particle of the leaf is certainly
+    // closer to s_v than LB(v) (a real particle's distance): |s_L - s_v| + l_L,
+    // with its error bound and one more relative margin for the FP32 sums,
+    // below LB(v) rounded down
+    unsigned long long m0 = 0ull, m1 = 0ull;
+    int k = 1;
+    for (int v = (wparent[L] >= 0) ? wparent[L] : -1; v >= 0; v = wparent[v], ++k) {
+      const float4 hv = geo_hi[v], ov = geo_lo[v];
+      const float dx = df_diff(hL.x, oL.x, hv.x, ov.x), dy = df_diff(hL.y, oL.y, hv.y, ov.y),
+                  dz = df_diff(hL.z, oL.z, hv.z, ov.z);
+      const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      const float reach = (d + df_dist_err(dx, dy, dz, hL, hv) + lL) * (1.0f + 1e-6f);
+      if (!(reach < hv.w)) {
+        if (k < 64) m0 |= 1ull << k;
+        else if (k < 128) m1 |= 1ull << (k - 64);
+      }
     }
+    cand[2 * (size_t)q] = m0;
+    cand[2 * (size_t)q + 1] = m1;
   }
-  cand[2 * (size_t)q] = m0;
-  cand[2 * (size_t)q + 1] = m1;
 }
 
 // Thread per particle: candidate ancestors only; lanes at the same node
@@ -1060,21 +1075,22 @@ __global__ void k_size(int n, const double* __restrict__ px, const double* __res
 }
 
 // Final node records and float32 particle data.
-__global__ void k_finalize_nodes(int nn, const unsigned long long* __restrict__ l2bits,
+__global__ void k_finalize_nodes(const uint32_t* __restrict__ counts, const unsigned long long* __restrict__ l2bits,
                                  const double* __restrict__ ncx, const double* __restrict__ ncy,
                                  const double* __restrict__ ncz, const double* __restrict__ nhmax,
                                  double* __restrict__ nsize, float4* __restrict__ geo_hi,
                                  float4* __restrict__ geo_lo) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nn) return;
-  double l = __dsqrt_rn(__longlong_as_double((long long)l2bits[v]));
-  nsize[v] = l;
-  float xh, xl, yh, yl, zh, zl;
-  split_double(ncx[v], xh, xl);
-  split_double(ncy[v], yh, yl);
-  split_double(ncz[v], zh, zl);
-  geo_hi[v] = make_float4(xh, yh, zh, __double2float_rn(l));
-  geo_lo[v] = make_float4(xl, yl, zl, __double2float_rn(nhmax[v]));
+  const int nn = (int)counts[0];
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+    double l = __dsqrt_rn(__longlong_as_double((long long)l2bits[v]));
+    nsize[v] = l;
+    float xh, xl, yh, yl, zh, zl;
+    split_double(ncx[v], xh, xl);
+    split_double(ncy[v], yh, yl);
+    split_double(ncz[v], zh, zl);
+    geo_hi[v] = make_float4(xh, yh, zh, __double2float_rn(l));
+    geo_lo[v] = make_float4(xl, yl, zl, __double2float_rn(nhmax[v]));
+  }
 }
 
 __global__ void k_particles_f32(int n, const double* __restrict__ px, const double* __restrict__ py,
@@ -1092,15 +1108,16 @@ __global__ void k_particles_f32(int n, const double* __restrict__ px, const doub
   phh[i] = make_float4(__double2float_rn(1.0 / h), __double2float_rn(4.0 * h * h), __double2float_ru(2.0 * h), 0.0f);
 }
 
-__global__ void k_depth(int nn, const int* __restrict__ nparent, int* __restrict__ depth) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nn) return;
-  int d = 0, u = nparent[v];
-  while (u >= 0) {
-    ++d;
-    u = nparent[u];
+__global__ void k_depth(const uint32_t* __restrict__ counts, const int* __restrict__ nparent, int* __restrict__ depth) {
+  const int nn = (int)counts[0];
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+    int d = 0, u = nparent[v];
+    while (u >= 0) {
+      ++d;
+      u = nparent[u];
+    }
+    depth[v] = d;
   }
-  depth[v] = d;
 }
 
 // Internal nodes grouped by depth (level lists for the per-node walk), and
@@ -1164,10 +1181,19 @@ int build_levels(sfmm_ctx* c) {
   return SFMM_OK;
 }
 
+// Grids of the node- and leaf-indexed passes: their counts stay on the
+// device (read by the kernels), so the grids cover the bound and stride.
+static inline unsigned node_grid(const sfmm_ctx* c) {
+  return std::min<unsigned>(nblk(2 * c->n, 256), 16u * num_sms(c->device));
+}
+static inline unsigned leaf_grid(const sfmm_ctx* c) {
+  return std::min<unsigned>(nblk(c->n, 128), 32u * num_sms(c->device));
+}
+
 int compute_depth(sfmm_ctx* c) {
-  int rc = c->ndepth.ensure(sizeof(int) * (size_t)c->nnodes);
+  int rc = c->ndepth.ensure(sizeof(int) * 2 * (size_t)c->n);
   if (rc) return rc;
-  k_depth<<<nblk(c->nnodes, 256), 256, 0, c->stream>>>(c->nnodes, c->nparent.as<int>(), c->ndepth.as<int>());
+  k_depth<<<node_grid(c), 256, 0, c->stream>>>(c->d_counts, c->nparent.as<int>(), c->ndepth.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   return SFMM_OK;
@@ -1183,16 +1209,15 @@ int compute_depth(sfmm_ctx* c) {
 template <int P, typename QT>
 static int geom_upward_t(sfmm_ctx* c, int nqs) {
   cudaStream_t st = c->stream;
-  const int nl = c->nleaves;
-  k_leaf_geom<P, QT><<<nblk(nl, 128), 128, 0, st>>>(
-      nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
+  k_leaf_geom<P, QT><<<leaf_grid(c), 128, 0, st>>>(
+      c->d_counts, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
       c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
       c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),
       c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->Qd.as<double>(), c->Qf.as<float>(), nqs);
   ++c->nlaunch;
-  // the second child to finish climbs on
-  SFMM_CUDA_TRY(cudaMemsetAsync(c->flags.p, 0, sizeof(int) * (size_t)c->nnodes, st));
-  k_upward<P, QT><<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
+  // the second child to finish climbs on (arrival flags cleared by the leaf
+  // numbering pass)
+  k_upward<P, QT><<<leaf_grid(c), 128, 0, st>>>(c->d_counts, c->leaf_node.as<int>(), c->nparent.as<int>(), c->nright.as<int>(),
                                                  c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
                                                  c->nmass.as<double>(), c->nhmax.as<double>(), c->nlu.as<int>(),
                                                  c->flags.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(),
@@ -1303,7 +1328,10 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
 #undef ENS
   const int nsys = c->nsys;
   double* bbox = c->misc.as<double>();             // 8 doubles per system
-  uint32_t* totals = (uint32_t*)(bbox + 8 * nsys);  // scan totals
+  // scan totals: [0] node count, [1] leaf count (read on the device by every
+  // node- and leaf-indexed pass, and by the host with the closing status)
+  uint32_t* totals = (uint32_t*)(bbox + 8 * nsys);
+  c->d_counts = totals;
   const int* psys = nullptr;                       // system of each particle (batches only)
   if (nsys > 1) {
     if ((rc = c->psys.ensure(sizeof(int) * (size_t)n))) return rc;
@@ -1324,12 +1352,15 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     k_bbox_seg<<<nsys, BB_NT, 0, st>>>(pos, mass, h, c->sys_off.as<int>(), bbox, c->d_status);
     ++c->nlaunch;
   }
-  int nnodes = 1;
   uint64_t* ka_final = c->keys_a.as<uint64_t>();  // where the sorted keys end up
   if (c->tree_kind == 1) {
-    // centre-of-mass-pivot kd tree: topology, sorted particles, pre-order nodes
+    // centre-of-mass-pivot kd tree: topology, sorted particles, pre-order
+    // nodes (level-synchronous on the host, so its counts are known here)
     if ((rc = build_kd_topology(c, pos, mass, h))) return rc;
-    nnodes = c->nnodes;
+    const uint32_t hc[2] = {(uint32_t)c->nnodes, (uint32_t)c->nleaves};
+    SFMM_CUDA_TRY(cudaMemcpyAsync(totals, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+    SFMM_CUDA_TRY(cudaMemsetAsync(c->flags.p, 0, sizeof(int) * (size_t)c->nnodes, st));
+    SFMM_CUDA_TRY(cudaMemsetAsync(c->l2bits.p, 0, sizeof(unsigned long long) * (size_t)c->nnodes, st));
   } else {
     k_morton<<<nblk(n, 256), 256, 0, st>>>(pos, n, bbox, psys, c->keys_a.as<uint64_t>(), c->idx_a.as<uint32_t>());
     ++c->nlaunch;
@@ -1397,12 +1428,10 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
       SFMM_CUDA_TRY(cudaMemcpyAsync(c->ncount.as<int>(), &one, sizeof(int), cudaMemcpyHostToDevice, st));
       SFMM_CUDA_TRY(cudaMemcpyAsync(c->nright.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
       SFMM_CUDA_TRY(cudaMemcpyAsync(c->nparent.as<int>(), &minus, sizeof(int), cudaMemcpyHostToDevice, st));
-      SFMM_CUDA_TRY(cudaMemcpyAsync(c->leaf_node.as<int>(), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-      // leaf numbers of the nodes (exclusive scan of the leaf flags): node 0 is leaf 0
-      static const uint32_t leaf_scan[2] = {0u, 1u};
-      SFMM_CUDA_TRY(cudaMemcpyAsync(c->isleaf.p, leaf_scan, sizeof(leaf_scan), cudaMemcpyHostToDevice, st));
-      c->nnodes = 1;
-      c->nleaves = 1;
+      // one leaf, starting at particle 0: its number is 0
+      SFMM_CUDA_TRY(cudaMemsetAsync(c->chain.p, 0, sizeof(uint32_t), st));
+      static const uint32_t one_node[2] = {1u, 1u};
+      SFMM_CUDA_TRY(cudaMemcpyAsync(totals, one_node, sizeof(one_node), cudaMemcpyHostToDevice, st));
     } else {
       const SysView sv{psys, c->sys_off.as<int>()};
       const LeafRule lr{psys, c->sys_lsz.as<int>(), c->leaf_size};
@@ -1415,36 +1444,36 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
                                            c->par_int.as<int>(), c->par_leaf.as<int>(), c->chain.as<uint32_t>());
       ++c->nlaunch;
       SFMM_CUDA_TRY(cudaGetLastError());
+      // the node count (totals[0]) stays on the device: every node-indexed
+      // pass reads it there, and the host learns it with the status word
       if ((rc = exclusive_scan_u32(c, c->chain.as<uint32_t>(), n, totals))) return rc;
       k_preorder<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_first.as<int>(), c->k_last.as<int>(),
                                                c->par_int.as<int>(), c->par_leaf.as<int>(),
                                                c->chain.as<uint32_t>(), c->pre_int.as<int>(), c->pre_leaf.as<int>());
       ++c->nlaunch;
       SFMM_CUDA_TRY(cudaGetLastError());
-      uint32_t h_tot = 0;
-      SFMM_CUDA_TRY(cudaMemcpyAsync(&h_tot, totals, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-      SFMM_CUDA_TRY(cudaStreamSynchronize(st));
-      nnodes = (int)h_tot;
-      c->nnodes = nnodes;
+      // leaf-start flags per particle (chain is free again), scanned into
+      // leaf numbers; their total is the leaf count (totals[1])
+      SFMM_CUDA_TRY(cudaMemsetAsync(c->chain.p, 0, sizeof(uint32_t) * (n + 1), st));
       k_fill_nodes<<<nblk(n, 256), 256, 0, st>>>(n, lr, c->k_left.as<int>(), c->k_right.as<int>(),
                                                  c->k_first.as<int>(), c->k_last.as<int>(), c->par_int.as<int>(),
                                                  c->par_leaf.as<int>(), c->pre_int.as<int>(), c->pre_leaf.as<int>(),
                                                  c->nfirst.as<int>(), c->ncount.as<int>(), c->nright.as<int>(),
-                                                 c->nparent.as<int>(), c->isleaf.as<uint32_t>(), c->d_status);
+                                                 c->nparent.as<int>(), c->chain.as<uint32_t>(), c->d_status);
       ++c->nlaunch;
       SFMM_CUDA_TRY(cudaGetLastError());
-      if ((rc = exclusive_scan_u32(c, c->isleaf.as<uint32_t>(), nnodes, totals + 1))) return rc;
-      k_leaf_list<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->nright.as<int>(), c->isleaf.as<uint32_t>(),
-                                                     c->leaf_node.as<int>());
-      ++c->nlaunch;
-      SFMM_CUDA_TRY(cudaGetLastError());
-      c->nleaves = (nnodes + 1) / 2;  // full binary tree
+      if ((rc = exclusive_scan_u32(c, c->chain.as<uint32_t>(), n, totals + 1))) return rc;
     }
+    k_leaf_list<<<node_grid(c), 256, 0, st>>>(c->d_counts, c->nfirst.as<int>(), c->nright.as<int>(),
+                                              c->chain.as<uint32_t>(), c->isleaf.as<uint32_t>(),
+                                              c->leaf_node.as<int>(), c->flags.as<int>(),
+                                              c->l2bits.as<unsigned long long>());
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
   }
-  const int nl = c->nleaves;
   // walk parents and system roots
-  k_sysroots<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, psys, c->nfirst.as<int>(), c->ncount.as<int>(),
-                                                c->nparent.as<int>(), c->wparent.as<int>(), c->sys_root.as<int>());
+  k_sysroots<<<node_grid(c), 256, 0, st>>>(c->d_counts, psys, c->nfirst.as<int>(), c->ncount.as<int>(),
+                                           c->nparent.as<int>(), c->wparent.as<int>(), c->sys_root.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
 
@@ -1452,8 +1481,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   // (P2M at the leaves, M2M on the way up: the same passes)
   const int P = c->pref_order;
   const int NQ = (int)ncoef(P), nqs = (NQ + 3) & ~3;
-  if ((rc = c->Qd.ensure(sizeof(double) * (size_t)nnodes * NQ)) ||
-      (rc = c->Qf.ensure(sizeof(float) * (size_t)nnodes * nqs)))
+  if ((rc = c->Qd.ensure(sizeof(double) * nn_max * NQ)) || (rc = c->Qf.ensure(sizeof(float) * nn_max * nqs)))
     return rc;
   // node depths (exported, and ranks of the one-sided symmetric walk); the
   // per-depth lists are built when a walk first needs them
@@ -1467,23 +1495,22 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     default: rc = geom_upward<4>(c, nqs); break;
   }
   if (rc) return rc;
-  SFMM_CUDA_TRY(cudaMemsetAsync(c->l2bits.p, 0, sizeof(unsigned long long) * nnodes, st));
-  k_node_lb<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->wparent.as<int>(), c->n_exti.as<int>(),
-                                               c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
-                                               c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                               c->n_lb.as<double>(), c->geo_hi.as<float4>(), c->geo_lo.as<float4>());
+  k_node_lb<<<node_grid(c), 256, 0, st>>>(c->d_counts, c->wparent.as<int>(), c->n_exti.as<int>(),
+                                          c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
+                                          c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
+                                          c->n_lb.as<double>(), c->geo_hi.as<float4>(), c->geo_lo.as<float4>());
   // FP32 particle records (offsets from the leaf centre) first: the size
   // tests use them
   k_particles_f32<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
                                                 c->pm.as<double>(), c->ph.as<double>(), c->pnode.as<int>(),
                                                 c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
                                                 c->prel.as<float4>(), c->phh.as<float4>());
-  k_size_leaf<<<nblk(nl, 128), 128, 0, st>>>(nl, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(),
-                                             c->wparent.as<int>(), c->px.as<double>(), c->py.as<double>(),
-                                             c->pz.as<double>(), c->ncx.as<double>(), c->ncy.as<double>(),
-                                             c->ncz.as<double>(), c->geo_hi.as<float4>(), c->geo_lo.as<float4>(),
-                                             c->l2bits.as<unsigned long long>(),
-                                             c->size_cand.as<unsigned long long>());
+  k_size_leaf<<<leaf_grid(c), 128, 0, st>>>(c->d_counts, c->leaf_node.as<int>(), c->nfirst.as<int>(),
+                                            c->ncount.as<int>(), c->wparent.as<int>(), c->px.as<double>(),
+                                            c->py.as<double>(), c->pz.as<double>(), c->ncx.as<double>(),
+                                            c->ncy.as<double>(), c->ncz.as<double>(), c->geo_hi.as<float4>(),
+                                            c->geo_lo.as<float4>(), c->l2bits.as<unsigned long long>(),
+                                            c->size_cand.as<unsigned long long>());
   k_size<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
                                        c->pnode.as<int>(), c->isleaf.as<uint32_t>(),
                                        c->size_cand.as<unsigned long long>(), c->wparent.as<int>(),
@@ -1491,10 +1518,10 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
                                        c->geo_hi.as<float4>(), c->geo_lo.as<float4>(), c->prel.as<float4>(),
                                        c->l2bits.as<unsigned long long>());
   c->nlaunch += 4;
-  k_finalize_nodes<<<nblk(nnodes, 256), 256, 0, st>>>(nnodes, c->l2bits.as<unsigned long long>(), c->ncx.as<double>(),
-                                                      c->ncy.as<double>(), c->ncz.as<double>(), c->nhmax.as<double>(),
-                                                      c->nsize.as<double>(), c->geo_hi.as<float4>(),
-                                                      c->geo_lo.as<float4>());
+  k_finalize_nodes<<<node_grid(c), 256, 0, st>>>(c->d_counts, c->l2bits.as<unsigned long long>(),
+                                                 c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
+                                                 c->nhmax.as<double>(), c->nsize.as<double>(), c->geo_hi.as<float4>(),
+                                                 c->geo_lo.as<float4>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   c->moments_order = P;

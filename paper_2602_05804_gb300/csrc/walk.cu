@@ -400,7 +400,7 @@ int run_walk(sfmm_ctx* c, double theta, int order, bool dump, int64_t cap_m2l, i
     arena_cap = (long long)(c->arena.bytes / sizeof(int));
     if ((rc = c->p2p_off.ensure(sizeof(long long) * (size_t)nl))) return rc;
     if ((rc = c->p2p_cnt.ensure(sizeof(int) * (size_t)nl))) return rc;
-    if ((rc = c->counters.ensure(sizeof(unsigned long long) * 16))) return rc;
+    if ((rc = c->counters.ensure(sizeof(unsigned long long) * 20))) return rc;
     if ((rc = c->far.ensure((f32 ? sizeof(float4) : 4 * sizeof(double)) * (size_t)c->n))) return rc;
     unsigned long long* ctr = c->counters.as<unsigned long long>();
     SFMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 16, c->stream));

@@ -654,7 +654,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
   // per-depth launches (and the symmetric walk) run over the per-depth lists
   if (!queue && (rc = ensure_levels(c)))
     return set_error(c, rc, rc == SFMM_ESTACK ? "tree deeper than supported" : "per-depth node lists failed");
-  for (int attempt = 0; attempt < SFMM_WALK_ATTEMPTS; ++attempt) {
+  {
     // one ring per resident warp (the pair walk keeps both children's stacks
     // and lists and the second child's set-aside batches)
     const size_t ring_ints = pairs ? (size_t)q_blocks * WALK_WARPS * WALK_PAIR_RING * c->ring_capacity
@@ -678,6 +678,9 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     }
     if ((rc = c->p2p_off.ensure(sizeof(long long) * (size_t)nl))) return rc;
     if ((rc = c->p2p_cnt.ensure(sizeof(int) * (size_t)nl))) return rc;
+    // empty lists until a leaf writes its own: the near field runs before the
+    // status is read, and a walk cut short must leave no stale list behind
+    SFMM_CUDA_TRY(cudaMemsetAsync(c->p2p_cnt.p, 0, sizeof(int) * (size_t)nl, c->stream));
     const int nlev = queue ? 0 : c->max_depth + 1;  // levels holding internal nodes
     if ((rc = c->counters.ensure(sizeof(unsigned long long) * (20 + 2 * (size_t)nlev)))) return rc;
     if ((rc = c->far.ensure((F32 ? sizeof(float4) : 4 * sizeof(double)) * (size_t)c->n))) return rc;
@@ -794,43 +797,31 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
       }
       SFMM_CUDA_TRY(cudaGetLastError());
     }
-    int bits = 0;
-    if ((rc = sync_status(c, &bits))) return rc;
-    if (bits & SFMM_ST_DEPTH) return set_error(c, SFMM_ESTACK, "tree deeper than supported");
-    if (bits & SFMM_ST_INTERNAL) return set_error(c, SFMM_ECUDA, "walk: a queued node was not handed on in time");
-    if (bits & (SFMM_ST_RING | SFMM_ST_ARENA | SFMM_ST_CHILDLIST)) {
-      if (attempt == SFMM_WALK_ATTEMPTS - 1)
-        return set_error(c, SFMM_ECAPACITY, "walk buffers too small after the last regrow");
-      if (bits & SFMM_ST_RING) c->ring_capacity = c->ring_capacity < (1 << 20) ? c->ring_capacity * 16 : (1 << 24);
-      if (bits & SFMM_ST_ARENA) {
-        unsigned long long need = 0;
-        SFMM_CUDA_TRY(cudaMemcpy(&need, ctr + 9, sizeof(need), cudaMemcpyDeviceToHost));
-        int64_t grown = 2 * (int64_t)arena_cap, want = (int64_t)(need + need / 4 + 1024);
-        c->list_capacity = want > grown ? want : grown;
-      }
-      if (bits & SFMM_ST_CHILDLIST) {
-        // the count undercounts: a node that could not reserve skipped its
-        // children's lists, so their descendants reserved less
-        unsigned long long need = 0;
-        SFMM_CUDA_TRY(cudaMemcpy(&need, ctr + 16, sizeof(need), cudaMemcpyDeviceToHost));
-        const int64_t grown = 4 * (int64_t)cf_cap, want = 2 * (int64_t)need + 4096;
-        c->cf_capacity = want > grown ? want : grown;
-      }
-      continue;
-    }
-    SFMM_CUDA_TRY(cudaMemcpy(c->h_scalars, ctr, sizeof(unsigned long long) * 10, cudaMemcpyDeviceToHost));
-    const unsigned long long* hs = reinterpret_cast<const unsigned long long*>(c->h_scalars);
-    c->arena_used = (int64_t)hs[9];
-    c->split_chunks = (int64_t)hs[5];
-    c->split_lists = (int64_t)hs[6];
-    c->stats.m2l = (int64_t)hs[0];
-    c->stats.m2l_unique = (int64_t)hs[1];
-    c->stats.p2p_leaves = (int64_t)hs[2];
-    c->stats.p2p_pairs = (int64_t)hs[3];
-    c->stats.mac_fallbacks = (int64_t)hs[4];
-    return SFMM_OK;
+    // no host wait here: the gravity call checks the status word once, after
+    // the near field and the sums, and regrows and reruns on overflow
+    c->walk_arena_cap = arena_cap;
+    c->walk_cf_cap = cf_cap;
   }
-  return SFMM_ECAPACITY;
+  return SFMM_OK;
+}
+
+// Capacity overflow of the shared walk (status bits of the last run, its
+// counters in hs): grow what ran out before the rerun.
+int walk_shared_regrow(sfmm_ctx* c, int bits, const unsigned long long* hs) {
+  if (bits & SFMM_ST_RING) c->ring_capacity = c->ring_capacity < (1 << 20) ? c->ring_capacity * 16 : (1 << 24);
+  if (bits & SFMM_ST_ARENA) {
+    const unsigned long long need = hs[9];
+    const int64_t grown = 2 * c->walk_arena_cap, want = (int64_t)(need + need / 4 + 1024);
+    c->list_capacity = want > grown ? want : grown;
+  }
+  if (bits & SFMM_ST_CHILDLIST) {
+    // the count undercounts: a node that could not reserve skipped its
+    // children's lists, so their descendants reserved less
+    const unsigned long long need = hs[16];
+    const int64_t grown = 4 * c->walk_cf_cap, want = 2 * (int64_t)need + 4096;
+    c->cf_capacity = want > grown ? want : grown;
+  }
+  return SFMM_OK;
 }
 
 int run_walk_shared(sfmm_ctx* c, double theta, int order) {
