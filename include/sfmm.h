@@ -83,6 +83,7 @@ typedef struct sfmm_stats {
   double ms_reduce;     /* device time of the reductions */
   double ms_gravity;    /* device time of the whole last sfmm_gravity */
   int64_t kernel_launches; /* CUDA kernels this context has launched so far */
+  int64_t graph_replays;   /* steps sfmm_solve_graph ran as a replayed graph */
 } sfmm_stats;
 
 /* Create a context on CUDA device `device` in arithmetic form `precision`
@@ -210,6 +211,31 @@ int sfmm_build_batch(sfmm_ctx* ctx, int nsys, const int64_t* offsets, const doub
  * theta/order.  Errors: as sfmm_build_batch and sfmm_gravity. */
 int sfmm_autotune_batch(sfmm_ctx* ctx, int nsys, const int64_t* offsets, const double* pos, const double* mass,
                         const double* h, double theta, int order, int* leaf_size_out);
+
+/* Build + gravity of one particle set or batch as ONE CUDA graph per shape
+ * class (an ensemble service; the paper has no counterpart): the same
+ * results as sfmm_build_batch + sfmm_gravity_batch (bitwise), issued as a
+ * single graph launch followed by one synchronisation.
+ *   Arguments as sfmm_build_batch (nsys = 1 for a single set; leaf_size
+ *   HOST nsys ints, or NULL for autotuned sizes) and sfmm_gravity (theta,
+ *   order, acc, pot).  The shape class is (offsets, leaf sizes, theta, order,
+ *   the five array addresses); the particle values may change freely between
+ *   calls (positions of a time step, say): the graph's kernels take the node
+ *   and leaf counts of each replay's own build from the device.
+ *   The first call of a shape class runs the ordinary calls (sizing every
+ *   node- and leaf-indexed buffer for the bounds: 2n nodes, n leaves) and
+ *   then captures the step on the context's stream; later calls replay it.
+ *   A walk buffer that runs out during a replay (status bit) is grown and
+ *   the step rerun the ordinary way, then captured again.  Changing an
+ *   option, an ordinary build on the context, or any reallocation of the
+ *   context's buffers invalidates the graph (the next call recaptures).
+ *   sfmm_get_stats counts replays in graph_replays.
+ * Needs the Morton tree (option "tree" 0), walk 1 and at least two
+ * particles; the walk runs on a readiness queue (schedule 2 or 3, the
+ * automatic choice otherwise).  Errors: as sfmm_build_batch and
+ * sfmm_gravity; ENOTIMPL for another tree or walk. */
+int sfmm_solve_graph(sfmm_ctx* ctx, int nsys, const int64_t* offsets, const double* pos, const double* mass,
+                     const double* h, const int* leaf_size, double theta, int order, double* acc, double* pot);
 
 /* Cache file of the context's autotuner table (JSON): entries in the file
  * are loaded now (a missing file is an empty table) and the file is

@@ -162,11 +162,13 @@ int sfmm_create(sfmm_ctx** out, int device, int precision, void* stream) {
   return SFMM_OK;
 }
 
-void sfmm_destroy(sfmm_ctx* c) {
-  if (!c) return;
-  DeviceGuard g(c->device);
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  DevBuf* bufs[] = {&c->in_pos, &c->in_mass, &c->in_h, &c->out_acc, &c->out_pot, &c->keys_a, &c->keys_b,
+}  // extern "C"
+
+namespace sfmm {
+
+// Every device buffer of a context.
+std::vector<DevBuf*> ctx_buffers(sfmm_ctx* c) {
+  return {&c->in_pos, &c->in_mass, &c->in_h, &c->out_acc, &c->out_pot, &c->keys_a, &c->keys_b,
                     &c->idx_a, &c->idx_b, &c->sort_counts, &c->scan_tmp, &c->bbox_part, &c->k_left,
                     &c->k_right, &c->k_first, &c->k_last, &c->par_int, &c->par_leaf, &c->chain,
                     &c->pre_int, &c->pre_leaf, &c->misc, &c->px, &c->py, &c->pz, &c->pm, &c->ph,
@@ -180,7 +182,28 @@ void sfmm_destroy(sfmm_ctx* c) {
                     &c->p2p_extra, &c->p2p_split, &c->p2p_slist, &c->p2p_part, &c->lf_acc, &c->lf_part,
                     &c->kd_ord, &c->kd_node, &c->kd_act, &c->kd_work, &c->kd_chunk, &c->kd_part, &c->kd_split,
                     &c->sym_own, &c->sym_recv, &c->wqueue, &c->sort_aux, &c->n_extv, &c->n_exti, &c->n_lb, &c->size_cand};
-  for (DevBuf* b : bufs) b->release();
+}
+
+// Addresses and sizes of a context's buffers, folded into one number: a
+// captured graph holds the addresses it was captured with.
+unsigned long long buffers_fingerprint(sfmm_ctx* c) {
+  unsigned long long f = 1469598103934665603ull;
+  for (DevBuf* b : ctx_buffers(c)) {
+    f = (f ^ (unsigned long long)(uintptr_t)b->p) * 1099511628211ull;
+    f = (f ^ (unsigned long long)b->bytes) * 1099511628211ull;
+  }
+  return f;
+}
+
+}  // namespace sfmm
+
+extern "C" {
+
+void sfmm_destroy(sfmm_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (DevBuf* b : ctx_buffers(c)) b->release();
   for (int i = 0; i < 8; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->ev_stage) cudaEventDestroy(c->ev_stage);
@@ -189,6 +212,7 @@ void sfmm_destroy(sfmm_ctx* c) {
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
   if (c->h_level_pin) cudaFreeHost(c->h_level_pin);
   if (c->h_sys_pin) cudaFreeHost(c->h_sys_pin);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
   tune_table_free(c);
   delete c;
@@ -214,6 +238,7 @@ int sfmm_set_stream(sfmm_ctx* c, void* stream) {
 
 int sfmm_set_option(sfmm_ctx* c, const char* key, double v) {
   if (check_ctx(c) || !key) return SFMM_EINVAL;
+  c->graph_valid = false;
   if (!std::isfinite(v)) return set_error(c, SFMM_EINVAL, "option value must be finite");
   if (!strcmp(key, "G")) {
     c->G = v;
@@ -266,6 +291,7 @@ namespace {
 // Build for nsys >= 1 systems packed back to back (h_sys_off / h_sys_lsz set).
 int build_common(sfmm_ctx* c, const double* pos, const double* mass, const double* h) {
   c->built = false;
+  c->graph_valid = false;
   c->moments_order = -1;
   int rc;
   if ((rc = c->sys_off.ensure(sizeof(int) * ((size_t)c->nsys + 1))) ||
@@ -487,6 +513,155 @@ int sfmm_batch_sums(const sfmm_ctx* cc, int nsys, double* out) {
   return SFMM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One step, build and gravity, issued on the context's stream with no host
+// wait: what sfmm_solve_graph captures.  It ends with the copies the host
+// reads after a replay: sums, walk counters, status word, node and leaf
+// counts (pinned buffers).
+int issue_step(sfmm_ctx* c, const double* pos, const double* mass, const double* h, double theta, int order,
+               double* acc, double* pot) {
+  cudaStream_t st = c->stream;
+  int rc;
+  SFMM_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
+  if ((rc = build_tree(c, pos, mass, h))) return rc;
+  if ((rc = run_walk_shared(c, theta, order))) return rc;
+  if ((rc = run_p2p(c, acc, pot))) return rc;
+  double* red = nullptr;
+  if ((rc = run_reduce(c, &red))) return rc;
+  if (c->nsys > 1 && (rc = run_reduce_systems(c))) return rc;
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_scalars + 16, red, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_scalars + 32, c->counters.p, 20 * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, st));
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SFMM_CUDA_TRY(cudaMemcpyAsync(c->h_status + 1, c->d_counts, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  return SFMM_OK;
+}
+
+// Captures issue_step into c->graph_exec.  False (and no graph) if the
+// capture failed or a device buffer moved while it ran.
+bool capture_step(sfmm_ctx* c, const double* pos, const double* mass, const double* h, double theta, int order,
+                  double* acc, double* pot) {
+  const unsigned long long mark = buffers_fingerprint(c);
+  const int prof = c->profile;
+  c->profile = 0;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->profile = prof;
+    return false;
+  }
+  const int rc = issue_step(c, pos, mass, h, theta, order, acc, pot);
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  c->profile = prof;
+  bool ok = rc == SFMM_OK && e == cudaSuccess && g && buffers_fingerprint(c) == mark;
+  cudaGraphExec_t ex = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    if (ex) cudaGraphExecDestroy(ex);
+    return false;
+  }
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = ex;
+  c->g_mark = mark;
+  return true;
+}
+
+// Counts, sums and statistics of a replayed step, from the copies it made.
+void replay_stats(sfmm_ctx* c, int order) {
+  c->nnodes = c->h_status[1];
+  c->nleaves = c->h_status[2];
+  c->built = true;
+  c->levels_ready = false;
+  c->moments_order = order;
+  c->pref_order = order;
+  const unsigned long long* hs = reinterpret_cast<const unsigned long long*>(c->h_scalars + 32);
+  const double* r = c->h_scalars + 16;
+  c->stats = sfmm_stats{};
+  c->stats.n = c->n;
+  c->stats.nnodes = c->nnodes;
+  c->stats.nleaves = c->nleaves;
+  c->stats.m2l = (int64_t)hs[0];
+  c->stats.m2l_unique = (int64_t)hs[1];
+  c->stats.p2p_leaves = (int64_t)hs[2];
+  c->stats.p2p_pairs = (int64_t)hs[3];
+  c->stats.mac_fallbacks = (int64_t)hs[4];
+  c->stats.momentum[0] = r[0];
+  c->stats.momentum[1] = r[1];
+  c->stats.momentum[2] = r[2];
+  c->stats.abs_momentum = r[3];
+  c->stats.W = 0.5 * r[4];
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfmm_solve_graph(sfmm_ctx* c, int nsys, const int64_t* offsets, const double* pos, const double* mass,
+                     const double* h, const int* leaf_size, double theta, int order, double* acc, double* pot) {
+  if (check_ctx(c)) return SFMM_EINVAL;
+  if (nsys < 1 || nsys > 65536 || !offsets) return set_error(c, SFMM_EINVAL, "nsys must be in [1, 65536]");
+  if (!pos || !mass || !h || !acc) return set_error(c, SFMM_EINVAL, "NULL pointer");
+  if (!(theta >= 0.0 && theta < 1.0)) return set_error(c, SFMM_EINVAL, "theta must be in [0, 1)");
+  if (order < 0 || order > SFMM_PMAX) return set_error(c, SFMM_EINVAL, "order must be in [0, 4]");
+  if (c->tree_kind != 0 || c->walk_mode != 1)
+    return set_error(c, SFMM_ENOTIMPL, "captured steps run the Morton tree and the shared walk (walk 1)");
+  if (offsets[nsys] < 2) return set_error(c, SFMM_EINVAL, "a captured step needs at least two particles");
+  DeviceGuard g(c->device);
+  std::vector<int64_t> off(offsets, offsets + nsys + 1);
+  std::vector<int> lsz;
+  if (leaf_size) lsz.assign(leaf_size, leaf_size + nsys);
+  const void* ptr[5] = {pos, mass, h, acc, pot};
+  bool same = c->graph_exec && c->graph_valid && buffers_fingerprint(c) == c->g_mark && c->g_off == off &&
+              c->g_auto_leaf == !leaf_size && c->g_lsz == lsz && c->g_theta == theta && c->g_order == order;
+  for (int k = 0; same && k < 5; ++k) same = c->g_ptr[k] == ptr[k];
+  if (same) {
+    cudaError_t e = cudaGraphLaunch(c->graph_exec, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return set_error(c, SFMM_ECUDA, cudaGetErrorString(e));
+    const int bits = c->h_status[0];
+    if (bits == 0) {
+      replay_stats(c, order);
+      ++c->graph_replays;
+      c->nlaunch += c->g_launches;
+      return SFMM_OK;
+    }
+    // a walk buffer ran out, or the inputs are bad: the ordinary path below
+    // regrows and reruns, or reports the inputs
+    if (bits & (SFMM_ST_RING | SFMM_ST_ARENA | SFMM_ST_CHILDLIST))
+      walk_shared_regrow(c, bits, reinterpret_cast<const unsigned long long*>(c->h_scalars + 32));
+    SFMM_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    c->graph_valid = false;
+  }
+  // the ordinary build and gravity with buffers sized for any tree of these
+  // particles, then the capture that the next calls replay
+  c->graph_mode = true;
+  int rc = sfmm_build_batch(c, nsys, offsets, pos, mass, h, leaf_size);
+  if (rc == SFMM_OK) rc = sfmm_gravity(c, theta, order, acc, pot);
+  if (rc == SFMM_OK) {
+    const int64_t l0 = c->nlaunch;
+    const sfmm_stats keep = c->stats;
+    if (capture_step(c, pos, mass, h, theta, order, acc, pot)) {
+      c->graph_valid = true;
+      c->g_off = off;
+      c->g_lsz = lsz;
+      c->g_auto_leaf = !leaf_size;
+      c->g_theta = theta;
+      c->g_order = order;
+      for (int k = 0; k < 5; ++k) c->g_ptr[k] = ptr[k];
+      c->g_launches = c->nlaunch - l0;
+    }
+    c->nlaunch = l0;  // captured, not run
+    c->stats = keep;
+  }
+  c->graph_mode = false;
+  return rc;
+}
+
 int sfmm_solve_host(sfmm_ctx* c, int64_t n, const double* pos, const double* mass, const double* h, int leaf_size,
                     double theta, int order, double* acc, double* pot) {
   if (check_ctx(c)) return SFMM_EINVAL;
@@ -519,6 +694,7 @@ int sfmm_get_stats(const sfmm_ctx* c, sfmm_stats* out) {
   if (check_ctx(c) || !out) return SFMM_EINVAL;
   *out = c->stats;
   out->kernel_launches = c->nlaunch;
+  out->graph_replays = c->graph_replays;
   return SFMM_OK;
 }
 

@@ -20,7 +20,7 @@ namespace sfmm {
 #define P2P_SB 128
 
 struct P2PArgs {
-  int nleaves;
+  const uint32_t* counts;  // the build's node and leaf counts (device)
   const int* leaf_node;
   const int* nfirst;
   const int* ncount;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
   const int nextra = (int)a.d_split[0];
-  const int nitems = nextra + a.nleaves;
+  const int nitems = nextra + (int)a.counts[1];
   unsigned long long pairs = 0;  // this lane's share of the pair evaluations
   while (true) {
     int item = 0;
@@ -636,29 +636,31 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
 // ceil(entries / chunk) partial slots and one extra work item
 // per chunk after the first.  ctr[0]: extra items, ctr[1]: slots, ctr[2]:
 // split leaves.  Which slots a leaf gets does not change any result.
-__global__ void k_p2p_split(int nleaves, const int* __restrict__ p2p_cnt, int* __restrict__ split,
-                            int2* __restrict__ extra, int* __restrict__ slist, unsigned long long* __restrict__ ctr,
-                            int max_extra, int max_slots, int max_split, int chunk, int* __restrict__ status) {
-  const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
-  if (leaf >= nleaves) return;
-  const int cnt = p2p_cnt[leaf];
-  if (cnt <= chunk) {
-    split[leaf] = -1;
-    return;
+__global__ void k_p2p_split(const uint32_t* __restrict__ counts, const int* __restrict__ p2p_cnt,
+                            int* __restrict__ split, int2* __restrict__ extra, int* __restrict__ slist,
+                            unsigned long long* __restrict__ ctr, int max_extra, int max_slots, int max_split,
+                            int chunk, int* __restrict__ status) {
+  const int nleaves = (int)counts[1];
+  for (int leaf = blockIdx.x * blockDim.x + threadIdx.x; leaf < nleaves; leaf += gridDim.x * blockDim.x) {
+    const int cnt = p2p_cnt[leaf];
+    if (cnt <= chunk) {
+      split[leaf] = -1;
+      continue;
+    }
+    const int nch = (cnt + chunk - 1) / chunk;
+    const int x = (int)atomicAdd(ctr, (unsigned long long)(nch - 1));
+    const int base = (int)atomicAdd(ctr + 1, (unsigned long long)nch);
+    const int q = (int)atomicAdd(ctr + 2, 1ull);
+    if (x + nch - 1 > max_extra || base + nch > max_slots || q >= max_split) {
+      // the walk counted these exactly: more means an internal inconsistency
+      split[leaf] = -1;
+      set_status(status, SFMM_ST_INTERNAL);
+      continue;
+    }
+    split[leaf] = base;
+    for (int k = 1; k < nch; ++k) extra[x + k - 1] = make_int2(leaf, k);
+    slist[q] = leaf;
   }
-  const int nch = (cnt + chunk - 1) / chunk;
-  const int x = (int)atomicAdd(ctr, (unsigned long long)(nch - 1));
-  const int base = (int)atomicAdd(ctr + 1, (unsigned long long)nch);
-  const int q = (int)atomicAdd(ctr + 2, 1ull);
-  if (x + nch - 1 > max_extra || base + nch > max_slots || q >= max_split) {
-    // the walk counted these exactly: more means an internal inconsistency
-    split[leaf] = -1;
-    set_status(status, SFMM_ST_INTERNAL);
-    return;
-  }
-  split[leaf] = base;
-  for (int k = 1; k < nch; ++k) extra[x + k - 1] = make_int2(leaf, k);
-  slist[q] = leaf;
 }
 
 // Split leaves: one warp per leaf sums the chunks' partial sums in chunk
@@ -807,21 +809,24 @@ int run_p2p(sfmm_ctx* c, double* acc, double* pot) {
   // all of them fit 2 arena / chunk), with no wait for the walk
   const int64_t arena_cap = (int64_t)(c->arena.bytes / sizeof(int));
   const int nslots = (int)std::min<int64_t>(2 * arena_cap / c->p2p_chunk + 2, INT32_MAX / 2);
-  const int nsplit = (int)std::min<int64_t>(std::min<int64_t>(nl, arena_cap / (c->p2p_chunk + 1) + 1), nslots);
+  const int nsplit =
+      (int)std::min<int64_t>(std::min<int64_t>(c->graph_mode ? c->n : nl, arena_cap / (c->p2p_chunk + 1) + 1), nslots);
   const int nextra = nslots;
   int lmax = c->leaf_size;
   for (int v : c->h_sys_lsz) lmax = v > lmax ? v : lmax;
-  if ((rc = c->p2p_split.ensure(sizeof(int) * (size_t)nl))) return rc;
+  const int nl_b = c->graph_mode ? (int)c->n : nl;  // leaf-indexed: the bound for a captured step
+  if ((rc = c->p2p_split.ensure(sizeof(int) * (size_t)nl_b))) return rc;
   if ((rc = c->p2p_extra.ensure(sizeof(int2) * (size_t)nextra))) return rc;
   if ((rc = c->p2p_slist.ensure(sizeof(int) * (size_t)nsplit))) return rc;
   if ((rc = c->p2p_part.ensure((f32 ? sizeof(float) : sizeof(double)) * 4 * (size_t)lmax * nslots))) return rc;
-  k_p2p_split<<<(nl + 255) / 256, 256, 0, c->stream>>>(nl, c->p2p_cnt.as<int>(), c->p2p_split.as<int>(),
+  const int sblocks = std::max(1, std::min((nl_b + 255) / 256, 8 * num_sms(c->device)));
+  k_p2p_split<<<sblocks, 256, 0, c->stream>>>(c->d_counts, c->p2p_cnt.as<int>(), c->p2p_split.as<int>(),
                                                      c->p2p_extra.as<int2>(), c->p2p_slist.as<int>(), ctr + 11,
                                                      nextra, nslots, nsplit, c->p2p_chunk, c->d_status);
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   P2PArgs a{};
-  a.nleaves = nl;
+  a.counts = c->d_counts;
   a.leaf_node = c->leaf_node.as<int>();
   a.nfirst = c->nfirst.as<int>();
   a.ncount = c->ncount.as<int>();

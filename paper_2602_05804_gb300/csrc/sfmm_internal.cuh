@@ -47,6 +47,21 @@ struct sfmm_ctx {
   DevBuf sys_off, sys_lsz, psys, sys_root, wparent, sys_sums;
   int32_t nnodes = 0, nleaves = 0;  // host copies, valid once a build has returned
   uint32_t* d_counts = nullptr;      // device: node count, leaf count of the current build
+  bool graph_mode = false;           // buffers sized for a captured step (bounds, device counts)
+  // captured step (sfmm_solve_graph): one graph per shape class, with the
+  // class it was captured for and the fingerprint of the buffers it uses;
+  // a reallocated buffer, an option change or an ordinary build invalidates it
+  cudaGraphExec_t graph_exec = nullptr;
+  bool graph_valid = false;
+  std::vector<int64_t> g_off;
+  std::vector<int> g_lsz;
+  double g_theta = -1.0;
+  int g_order = -1;
+  const void* g_ptr[5] = {};
+  unsigned long long g_mark = 0;
+  int64_t graph_replays = 0;
+  int64_t g_launches = 0;  // kernels in the captured step
+  bool g_auto_leaf = false;  // captured with autotuned (NULL) leaf sizes
   int moments_order = -1;  // order of the cached moments (-1: none)
   bool moments_fp64 = false;  // the cached moments include the FP64 rows (else FP32 only)
   int pref_order = 2;      // order the build computes moments for (the last gravity call's)
@@ -167,6 +182,9 @@ int tuned_leaf_sizes(sfmm_ctx* c, int nsys, const int64_t* offsets, const double
                      const double* h, double theta, int order, std::vector<int>& lsz);
 int tuned_knobs(sfmm_ctx* c, double theta, int order, double* acc, bool run_trials);
 int p2p_blocks_fit(sfmm_ctx* c);  // near-field blocks per SM that fit (p2p.cu)
+
+std::vector<DevBuf*> ctx_buffers(sfmm_ctx* c);        // every device buffer of a context
+unsigned long long buffers_fingerprint(sfmm_ctx* c);  // their addresses and sizes, folded
 
 int check_status(sfmm_ctx* c);
 int sync_status(sfmm_ctx* c, int* bits, bool counts = false);

@@ -178,13 +178,15 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? 4 : 1) k_walk_pair(
     return true;
   };
 
+  // items: the system roots and the children of every walkable internal node
+  const int q_total = (int)la.counts[0] + 1 - (int)la.counts[1];
   while (true) {
     // next item: a warp only takes a slot while it runs, and an item's slot
     // comes after its parent's, so the wait ends (bounded all the same)
     int slot = 0;
     if (lane == 0) slot = atomicAdd(la.q_head, 1);
     slot = __shfl_sync(SFMM_FULL, slot, 0);
-    if (slot >= la.q_total) break;
+    if (slot >= q_total) break;
     int got = -1;
     if (lane == 0) {
       for (int it = 0; it < SFMM_QUEUE_SPIN; ++it) {

@@ -47,6 +47,10 @@ struct LevelArgs {
   int* q_head;
   int* q_tail;
   int q_total;
+  // the build's node and leaf counts on the device (the queue walks size
+  // their work from them, so a captured graph follows every rebuild)
+  const uint32_t* counts;
+  int nsys;
 };
 
 // Data a parent's warp wrote earlier in the same launch (the queue walk) is
@@ -247,13 +251,15 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
       }
     }
   };
+  // queue walk: every walkable node (all but the nsys - 1 spanning systems)
+  const int q_total = queue ? (int)la.counts[0] - (la.nsys - 1) : 0;
   while (true) {
     int A;
     if constexpr (queue) {
       int slot = 0;
       if (lane == 0) slot = atomicAdd(la.q_head, 1);
       slot = __shfl_sync(SFMM_FULL, slot, 0);
-      if (slot >= la.q_total) break;
+      if (slot >= q_total) break;
       int got = -1;
       if (lane == 0) {
         for (int it = 0; it < SFMM_QUEUE_SPIN; ++it) {
@@ -648,6 +654,12 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     const size_t per_node = 48 + mom + 8 * (size_t)tstride;
     sched = ((double)per_node * nn <= 0.75 * (double)l2) ? 2 : 3;
   }
+  // a captured step runs on the counts of each replay's own build: node- and
+  // leaf-indexed buffers are sized for the bounds (2n nodes, n leaves), and
+  // only the queue schedules (which need no host-side level lists) run
+  if (c->graph_mode && sched == 1) sched = 2;
+  const int nn_b = c->graph_mode ? (int)std::min<int64_t>(2 * c->n, INT32_MAX) : nn;
+  const int nl_b = c->graph_mode ? (int)c->n : nl;
   const bool queue = sched >= 2, pairs = sched == 3;
   const int q_blocks = (pairs ? p_per_sm : q_per_sm) * num_sms(c->device);
   int rc;
@@ -667,20 +679,20 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     long long cf_cap = c->cf_capacity > 0 ? c->cf_capacity : (long long)nn * 256 + 4096;
     if ((rc = c->cf_arena.ensure(sizeof(int) * (size_t)cf_cap))) return rc;
     cf_cap = (long long)(c->cf_arena.bytes / sizeof(int));
-    if ((rc = c->cf_off.ensure(sizeof(long long) * (size_t)nn))) return rc;
-    if ((rc = c->cf_cnt.ensure(sizeof(int) * (size_t)nn))) return rc;
-    if ((rc = c->Tnode.ensure((F32 ? 2 * sizeof(float) : sizeof(double)) * (size_t)nn * tstride))) return rc;
+    if ((rc = c->cf_off.ensure(sizeof(long long) * (size_t)nn_b))) return rc;
+    if ((rc = c->cf_cnt.ensure(sizeof(int) * (size_t)nn_b))) return rc;
+    if ((rc = c->Tnode.ensure((F32 ? 2 * sizeof(float) : sizeof(double)) * (size_t)nn_b * tstride))) return rc;
     if (SYM) {
       if ((rc = c->sym_own.ensure(sizeof(double) * (size_t)nn * tstride)) ||
           (rc = c->sym_recv.ensure(sizeof(double) * (size_t)nn * tstride)))
         return rc;
       SFMM_CUDA_TRY(cudaMemsetAsync(c->sym_recv.p, 0, sizeof(double) * (size_t)nn * tstride, c->stream));
     }
-    if ((rc = c->p2p_off.ensure(sizeof(long long) * (size_t)nl))) return rc;
-    if ((rc = c->p2p_cnt.ensure(sizeof(int) * (size_t)nl))) return rc;
+    if ((rc = c->p2p_off.ensure(sizeof(long long) * (size_t)nl_b))) return rc;
+    if ((rc = c->p2p_cnt.ensure(sizeof(int) * (size_t)nl_b))) return rc;
     // empty lists until a leaf writes its own: the near field runs before the
     // status is read, and a walk cut short must leave no stale list behind
-    SFMM_CUDA_TRY(cudaMemsetAsync(c->p2p_cnt.p, 0, sizeof(int) * (size_t)nl, c->stream));
+    SFMM_CUDA_TRY(cudaMemsetAsync(c->p2p_cnt.p, 0, sizeof(int) * (size_t)nl_b, c->stream));
     const int nlev = queue ? 0 : c->max_depth + 1;  // levels holding internal nodes
     if ((rc = c->counters.ensure(sizeof(unsigned long long) * (20 + 2 * (size_t)nlev)))) return rc;
     if ((rc = c->far.ensure((F32 ? sizeof(float4) : 4 * sizeof(double)) * (size_t)c->n))) return rc;
@@ -749,19 +761,22 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
       // systems), the system roots first.  Pair queue: the system roots and
       // the children of every walkable internal node, nsys + (nn - nsys + 1 -
       // nl) = nn + 1 - nl items
-      la.q_total = pairs ? nn + 1 - nl : nn - (c->nsys - 1);
-      if ((rc = c->wqueue.ensure(sizeof(int) * (size_t)(la.q_total + 1)))) return rc;
+      la.q_total = pairs ? nn + 1 - nl : nn - (c->nsys - 1);  // (the kernels take it from the counts)
+      const int q_bound = c->graph_mode ? nn_b : la.q_total;
+      if ((rc = c->wqueue.ensure(sizeof(int) * (size_t)(q_bound + 1)))) return rc;
       la.queue = c->wqueue.as<int>();
       la.q_head = reinterpret_cast<int*>(ctr + 14);
       la.q_tail = reinterpret_cast<int*>(ctr + 15);
-      SFMM_CUDA_TRY(cudaMemsetAsync(la.queue, 0xff, sizeof(int) * (size_t)la.q_total, c->stream));
+      la.counts = c->d_counts;
+      la.nsys = c->nsys;
+      SFMM_CUDA_TRY(cudaMemsetAsync(la.queue, 0xff, sizeof(int) * (size_t)q_bound, c->stream));
       if (pairs) k_queue_seed_pairs<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), la.queue, la.q_tail);
       else k_queue_seed<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), la.queue, la.q_tail);
       la.level = 0;
       la.level_nodes = nullptr;
       la.level_begin = 0;
       la.level_count = la.q_total;
-      if (la.q_total > 0) {
+      if (la.q_total > 0 || c->graph_mode) {
         // one block per resident slot (the queue needs none resident: a warp
         // only takes a slot while it runs, and a node's parent always holds
         // an earlier slot)

@@ -24,7 +24,7 @@ EXPORTS = ("sfmm_create", "sfmm_destroy", "sfmm_set_stream", "sfmm_set_option", 
            "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
            "sfmm_lists", "sfmm_strerror", "sfmm_last_error", "sfmm_version", "sfmm_reduce_noalloc",
            "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums", "sfmm_leapfrog", "sfmm_fma_peak",
-           "sfmm_autotune_batch", "sfmm_autotune_cache")
+           "sfmm_autotune_batch", "sfmm_autotune_cache", "sfmm_solve_graph")
 SFMM_NOALLOC_MAX_N = 67108864
 
 
@@ -35,7 +35,7 @@ class sfmm_stats(ctypes.Structure):
                 ("momentum", ctypes.c_double * 3), ("abs_momentum", ctypes.c_double), ("W", ctypes.c_double),
                 ("ms_build", ctypes.c_double), ("ms_moments", ctypes.c_double), ("ms_walk", ctypes.c_double),
                 ("ms_p2p", ctypes.c_double), ("ms_reduce", ctypes.c_double), ("ms_gravity", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,10 +89,11 @@ def load(path: str = LIB_PATH):
     lib.sfmm_fma_peak.restype = i32
     lib.sfmm_autotune_batch.argtypes = [P, i32, P, P, P, P, dbl, i32, P]
     lib.sfmm_autotune_cache.argtypes = [P, ctypes.c_char_p]
+    lib.sfmm_solve_graph.argtypes = [P, i32, P, P, P, P, P, dbl, i32, P, P]
     for name in ("sfmm_create", "sfmm_set_stream", "sfmm_set_option", "sfmm_build", "sfmm_gravity",
                  "sfmm_solve_host", "sfmm_get_stats", "sfmm_tree_size", "sfmm_tree_export", "sfmm_moments_export",
                  "sfmm_lists", "sfmm_build_batch", "sfmm_gravity_batch", "sfmm_batch_sums", "sfmm_leapfrog", "sfmm_fma_peak",
-           "sfmm_autotune_batch", "sfmm_autotune_cache"):
+           "sfmm_autotune_batch", "sfmm_autotune_cache", "sfmm_solve_graph"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -216,6 +217,15 @@ def sfmm_autotune_batch(ctx, offsets, pos, mass, h, theta, order):
 
 def sfmm_autotune_cache(ctx, path):
     _check(load().sfmm_autotune_cache(ctx, path.encode() if path else None), ctx)
+
+
+def sfmm_solve_graph(ctx, offsets, pos, mass, h, leaf_size, theta, order, acc, pot):
+    """Build + gravity as one captured CUDA graph per shape class (see
+    include/sfmm.h); offsets (nsys + 1) host, leaf sizes per system or None."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    ls = None if leaf_size is None else np.ascontiguousarray(leaf_size, dtype=np.int32)
+    _check(load().sfmm_solve_graph(ctx, len(off) - 1, _ptr(off), _ptr(pos), _ptr(mass), _ptr(h), _ptr(ls),
+                                   float(theta), int(order), _ptr(acc), _ptr(pot)), ctx)
 
 
 def sfmm_gravity_batch(ctx, theta, order, acc, pot):
