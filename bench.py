@@ -410,40 +410,80 @@ def _err_stats(e):
 
 
 def oracle_error_block(pos, m, h, w, results, nleaf=96, ntarget=4096):
-    """Error of each form against the FP64 oracle, per result: accelerations
-    and potentials on a seeded sample of leaves (the oracle runs Algorithms
-    1-2 for those leaves only: exact, since a leaf's result depends on the
-    read-only tree alone), plus the momentum residual over all particles.
-    Also each form's, and the oracle's, force error against the softened
-    direct sum on seeded targets: the truncation error both forms share,
-    which is what "equal force accuracy" compares."""
+    """Error of each result against the FP64 oracle: accelerations and
+    potentials on a seeded sample of leaves of the oracle's tree of the
+    result's leaf size (the oracle runs Algorithms 1-2 for those leaves only:
+    exact, since a leaf's result depends on the read-only tree alone), plus
+    the momentum residual over all particles.  Also each result's, and the
+    oracle's, force error against the softened direct sum on seeded targets:
+    the truncation error, which is what "equal force accuracy" compares.
+    results: name -> (acc, pot, stats, leaf size)."""
     import oracle
 
     t0 = time.perf_counter()
-    t = oracle.Tree(pos, m, h, w["leaf_size"], p=w["order"])
     rng = np.random.default_rng(11)
-    sel = np.unique(np.concatenate([rng.choice(t.nleaves, min(nleaf, t.nleaves), replace=False),
-                                    [0, t.nleaves - 1]])).astype(np.int32)
-    a_o, p_o, _ = t.sfmm(w["theta"], leaf_sample=sel)
-    idx = np.concatenate([t.perm[t.first[L]:t.first[L] + t.count[L]] for L in t.leaves[sel]])
     tg = np.sort(rng.choice(len(m), min(ntarget, len(m)), replace=False))
     a_d, _ = oracle.direct(pos, m, h, targets=tg)
-    leaf_of = np.empty(len(m), np.int64)
-    for q, L in enumerate(t.leaves):
-        leaf_of[t.perm[t.first[L]:t.first[L] + t.count[L]]] = q
-    a_ot, _, _ = t.sfmm(w["theta"], leaf_sample=np.unique(leaf_of[tg]).astype(np.int32))
     an = np.linalg.norm(a_d, axis=1)
-    out = {"sample": "%d leaves (%d particles) vs the oracle; %d seeded targets vs the direct sum"
-                     % (len(sel), len(idx), len(tg)),
-           "oracle_vs_direct": _err_stats(np.linalg.norm(a_ot[tg] - a_d, axis=1) / an)}
-    for form, (acc, pot, st) in results.items():
+    out = {}
+    trees = {}
+    for name, (acc, pot, st, leaf) in results.items():
+        if leaf not in trees:
+            t = oracle.Tree(pos, m, h, leaf, p=w["order"])
+            r = np.random.default_rng(11 + leaf)
+            sel = np.unique(np.concatenate([r.choice(t.nleaves, min(nleaf, t.nleaves), replace=False),
+                                            [0, t.nleaves - 1]])).astype(np.int32)
+            a_o, p_o, _ = t.sfmm(w["theta"], leaf_sample=sel)
+            idx = np.concatenate([t.perm[t.first[L]:t.first[L] + t.count[L]] for L in t.leaves[sel]])
+            leaf_of = np.empty(len(m), np.int64)
+            for q, L in enumerate(t.leaves):
+                leaf_of[t.perm[t.first[L]:t.first[L] + t.count[L]]] = q
+            a_ot, _, _ = t.sfmm(w["theta"], leaf_sample=np.unique(leaf_of[tg]).astype(np.int32))
+            trees[leaf] = (a_o, p_o, idx)
+            out["oracle_leaf%d_vs_direct" % leaf] = _err_stats(np.linalg.norm(a_ot[tg] - a_d, axis=1) / an)
+            out["sample_leaf%d" % leaf] = ("%d leaves (%d particles) vs the oracle; %d seeded targets vs the direct "
+                                          "sum" % (len(sel), len(idx), len(tg)))
+        a_o, p_o, idx = trees[leaf]
         ep = np.abs(pot[idx] - p_o[idx]) / np.abs(p_o[idx])
-        out[form] = {"acc_rel_vs_oracle": _err_stats(_acc_rel(acc[idx], a_o[idx])),
+        out[name] = {"leaf_size": leaf, "acc_rel_vs_oracle": _err_stats(_acc_rel(acc[idx], a_o[idx])),
                      "pot_rel_vs_oracle": _err_stats(ep),
                      "momentum_residual": float(np.linalg.norm(st["momentum"]) / st["abs_momentum"]),
                      "acc_rel_vs_direct": _err_stats(np.linalg.norm(acc[tg] - a_d, axis=1) / an)}
     out["seconds"] = time.perf_counter() - t0
     return out
+
+
+def fp64_tuned_block(torch, local, pos_d, m_d, h_d, acc, pot, w, steps, flush):
+    """The FP64 form at the leaf size the library's autotuner picks for this
+    particle set (sfmm_autotune_batch over the one system: timed trials of
+    leaf 8, 16, 32, 64), through the captured graph.  The FP64 near field
+    costs 64x the FP32 one per pair, so smaller leaves (more M2L, fewer pairs)
+    pay off in this form."""
+    from paper_2602_05804_gb300 import sfmm
+
+    n = m_d.shape[0]
+    off = np.array([0, n], np.int64)
+    s = sfmm.Solver(local, "fp64")
+    t0 = time.perf_counter()
+    leaf = int(sfmm.sfmm_autotune_batch(s.ctx, off, pos_d, m_d, h_d, w["theta"], w["order"])[0])
+    t_tune = time.perf_counter() - t0
+    ls = np.array([leaf], np.int32)
+    for _ in range(2):
+        sfmm.sfmm_solve_graph(s.ctx, off, pos_d, m_d, h_d, ls, w["theta"], w["order"], acc, pot)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        _flush(flush)
+        ev[k][0].record(s.stream)
+        sfmm.sfmm_solve_graph(s.ctx, off, pos_d, m_d, h_d, ls, w["theta"], w["order"], acc, pot)
+        ev[k][1].record(s.stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    st = s.stats()
+    s.close()
+    return ({"leaf_size": leaf, "ms_per_step": ms, "particles_per_s": n / (ms * 1e-3), "steps": steps,
+             "autotune_seconds": t_tune,
+             "how": "sfmm_autotune_batch (one system), then sfmm_solve_graph at the chosen leaf size"},
+            (acc.cpu().numpy(), pot.cpu().numpy(), st, leaf))
 
 
 def uniform_1e4_block(torch, local, flush, steps):
@@ -773,8 +813,13 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
 
-    oracle_err = None if args.no_oracle_error else oracle_error_block(pos, m, h, w, {"fp32": res_fp32,
-                                                                                      "fp64": res_fp64})
+    fp64_tuned, res_fp64t = fp64_tuned_block(torch, local, pos_d, m_d, h_d, acc, pot, w, max(1, min(args.steps, 3)),
+                                             flush)
+    oracle_err = None
+    if not args.no_oracle_error:
+        oracle_err = oracle_error_block(pos, m, h, w, {"fp32": res_fp32 + (w["leaf_size"],),
+                                                       "fp64": res_fp64 + (w["leaf_size"],),
+                                                       "fp64_tuned_leaf": res_fp64t})
     small = None if args.no_configs else uniform_1e4_block(torch, local, flush, max(3, min(args.steps, 10)))
 
     # roofline of the dominant kernel
@@ -828,6 +873,10 @@ def run_gpu(args):
                       "speedup_fp32_over_fp64": fp64_ms / step_ms,
                       "speedup_at": ("same theta, p and tree: equal force accuracy, since both forms share the "
                                      "truncation error against the direct sum (oracle_error.*.acc_rel_vs_direct)"),
+                      "tuned_leaf": dict(fp64_tuned, speedup_fp32_over_fp64=fp64_tuned["ms_per_step"] / step_ms,
+                                         acc_rel_vs_direct_mean=(None if oracle_err is None else
+                                                                 oracle_err["fp64_tuned_leaf"]["acc_rel_vs_direct"][
+                                                                     "mean"])),
                       "acc_rel_vs_direct_mean": (None if oracle_err is None else
                                                  {f: oracle_err[f]["acc_rel_vs_direct"]["mean"]
                                                   for f in ("fp32", "fp64")}),
