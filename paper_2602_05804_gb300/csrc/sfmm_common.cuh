@@ -72,18 +72,28 @@ __device__ __forceinline__ float df_diff(float ahi, float alo, float bhi, float 
 // ---------------------------------------------------------------------------
 // Compensated FP64 sums (Neumaier's variant of Kahan summation, 1974): a sum
 // is carried as the rounded running sum s plus the accumulated rounding
-// errors c of every addition, each error taken exactly with Knuth's TwoSum,
-// so the order of the operands' magnitudes does not matter.  Two partial sums
-// merge by adding one's s to the other and both c's: the total error is
-// about eps |sum| + O(n eps^2) sum |x|, instead of O(n eps) sum |x| for a
-// plain sum.  Every operation is rounded as written.
+// errors c of every addition, each error taken exactly, so the order of the
+// operands' magnitudes does not matter.  Two partial sums merge by adding
+// one's s to the other and both c's: the total error is about eps |sum| +
+// O(n eps^2) sum |x|, instead of O(n eps) sum |x| for a plain sum.  Every
+// operation is rounded as written.
+//
+// The error of t = fl(a + b) is taken as (big - t) + small, with big the
+// operand of larger magnitude (Dekker's Fast2Sum, exact under that ordering:
+// the same value as Knuth's branch-free TwoSum, in three FP64 operations
+// instead of six).  The magnitudes are compared on the bit patterns (for
+// finite doubles |a| >= |b| iff the sign-cleared patterns compare so as
+// unsigned integers), on the integer pipe: GB300's FP64 pipe is the narrow one.
 // ---------------------------------------------------------------------------
 struct csum { double s, c; };
 
 __device__ __forceinline__ void cs_add(csum& a, double x) {
   const double t = __dadd_rn(a.s, x);
-  const double bb = __dsub_rn(t, a.s);
-  const double e = __dadd_rn(__dsub_rn(a.s, __dsub_rn(t, bb)), __dsub_rn(x, bb));
+  const unsigned long long ma = (unsigned long long)__double_as_longlong(a.s) & 0x7fffffffffffffffull;
+  const unsigned long long mx = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const bool a_big = ma >= mx;
+  const double big = a_big ? a.s : x, small = a_big ? x : a.s;
+  const double e = __dadd_rn(__dsub_rn(big, t), small);
   a.s = t;
   a.c = __dadd_rn(a.c, e);
 }

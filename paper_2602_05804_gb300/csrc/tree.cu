@@ -857,9 +857,94 @@ __global__ void k_leaf_geom(const uint32_t* __restrict__ counts, const int* __re
   }
 }
 
-// Bottom-up: the second child to finish computes its parent (P >= 0: also
-// the parent's moments, both children's translated to its centre, Eq.
-// massmomtrans).
+// 1 / M for M > 0, within about one unit in the last place: Newton's
+// iteration for the reciprocal, r <- r + r (1 - M r), twice from the FP32
+// reciprocal of M rounded to FP32 (relative error below 2^-22, so below
+// 2^-44 after one step and at FP64 rounding after the second).  Four FP64
+// operations in a dependent chain instead of a correctly rounded division;
+// magnitudes outside FP32's normal range take the division.
+__device__ __forceinline__ double recip_pos(double M) {
+  const float mf = __double2float_rn(M);
+  if (!(mf > 1e-36f && mf < 1e36f)) return 1.0 / M;
+  double r = (double)__frcp_rn(mf);
+  r = fma(r, fma(-M, r, 1.0), r);
+  r = fma(r, fma(-M, r, 1.0), r);
+  return r;
+}
+
+// Node v from its children L = v + 1 and R: centre of mass, moments (P >= 0:
+// both children's translated to v's centre, Eq. massmomtrans), h_max, leaf
+// count and the axis-extreme particles (the left child's on ties).  The
+// children's records are read through L2: another thread of this launch may
+// have written them.
+template <int P, typename QT>
+__device__ __forceinline__ void upward_node(int v, int R, double* ncx, double* ncy, double* ncz, double* nmass,
+                                            double* nhmax, int* nlu, double* extv, int* exti, double* Qd,
+                                            float* Qf) {
+  const int L = v + 1;
+  // every load first: the stores below may alias them as far as the
+  // compiler knows, and loads left after a store would wait for the work
+  // before it, one L2 round trip per group
+  const double mL = __ldcg(&nmass[L]), mR = __ldcg(&nmass[R]);
+  const double cLx = __ldcg(&ncx[L]), cLy = __ldcg(&ncy[L]), cLz = __ldcg(&ncz[L]);
+  const double cRx = __ldcg(&ncx[R]), cRy = __ldcg(&ncy[R]), cRz = __ldcg(&ncz[R]);
+  const double hL = __ldcg(&nhmax[L]), hR = __ldcg(&nhmax[R]);
+  const int uL = __ldcg(&nlu[L]), uR = __ldcg(&nlu[R]);
+  double ea[6], eb[6];
+  int ia[6], ib[6];
+  #pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    ea[c] = __ldcg(&extv[6 * (size_t)L + c]);
+    eb[c] = __ldcg(&extv[6 * (size_t)R + c]);
+    ia[c] = __ldcg(&exti[6 * (size_t)L + c]);
+    ib[c] = __ldcg(&exti[6 * (size_t)R + c]);
+  }
+  constexpr int NQ = (P >= 0) ? MomOps<(P >= 0 ? P : 0)>::NQ : 1;
+  QT qL[NQ], qR[NQ];
+  if constexpr (P >= 0) {
+    load_moments<NQ>(L, qL, Qd, Qf);
+    load_moments<NQ>(R, qR, Qd, Qf);
+  }
+  const double M = dadd(mL, mR);
+  // one reciprocal per node (GB300's FP64 pipe is narrow): the centre is
+  // within rounding of the quotient, like the oracle's own sum
+  const double iM = recip_pos(M);
+  const double cx = dmul(dadd(dmul(mL, cLx), dmul(mR, cRx)), iM);
+  const double cy = dmul(dadd(dmul(mL, cLy), dmul(mR, cRy)), iM);
+  const double cz = dmul(dadd(dmul(mL, cLz), dmul(mR, cRz)), iM);
+  ncx[v] = cx;
+  ncy[v] = cy;
+  ncz[v] = cz;
+  if constexpr (P >= 0) {
+    QT qp[NQ];
+  #pragma unroll
+    for (int k = 0; k < NQ; ++k) qp[k] = QT(0);
+    QT g[NQ];
+    MomOps<P>::mono((QT)(cLx - cx), (QT)(cLy - cy), (QT)(cLz - cz), g);
+    MomOps<P>::m2m(g, qL, qp);
+    MomOps<P>::mono((QT)(cRx - cx), (QT)(cRy - cy), (QT)(cRz - cz), g);
+    MomOps<P>::m2m(g, qR, qp);
+    store_moments<NQ>(v, qp, M, Qd, Qf);
+  }
+  nmass[v] = M;
+  nhmax[v] = dmax_pos(hL, hR);
+  nlu[v] = uL + uR;
+  #pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const long long ka = dkey(ea[c]), kb = dkey(eb[c]);
+    const bool right = (c < 3) ? (kb < ka) : (kb > ka);
+    extv[6 * (size_t)v + c] = right ? eb[c] : ea[c];
+    exti[6 * (size_t)v + c] = right ? ib[c] : ia[c];
+  }
+}
+
+// Bottom-up: the second child to finish computes its parent.  The climb's
+// cost is its longest chain of dependent arrivals (one device-scope fence,
+// atomic and round of loads per level: about 30 levels on a Plummer sphere
+// of 10^6), so the node body issues all its loads at once.  (Measured on
+// GB300: computing the top of the tree -- the ~1500 nodes of more than 10^3
+// particles, 23 levels deep -- level by level in one block after a climb
+// that stops below it was slower, 0.18 against 0.13 ms.)
 template <int P, typename QT>
 __global__ void k_upward(const uint32_t* __restrict__ counts, const int* __restrict__ leaf_node, const int* __restrict__ nparent,
                          const int* __restrict__ nright, double* ncx, double* ncy, double* ncz, double* nmass,
@@ -869,53 +954,15 @@ __global__ void k_upward(const uint32_t* __restrict__ counts, const int* __restr
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
     int v = nparent[leaf_node[q]];
     while (v >= 0) {
+      // the tree's links (written by earlier launches) load ahead of the arrival
+      const int R = nright[v], up = nparent[v];
       {
         // release this child's records, acquire the sibling's
         cuda::atomic_ref<int, cuda::thread_scope_device> arrive(flags[v]);
         if (arrive.fetch_add(1, cuda::memory_order_acq_rel) == 0) break;
       }
-      int L = v + 1, R = nright[v];
-      double mL = __ldcg(&nmass[L]), mR = __ldcg(&nmass[R]);
-      double M = dadd(mL, mR);
-      const double cLx = __ldcg(&ncx[L]), cLy = __ldcg(&ncy[L]), cLz = __ldcg(&ncz[L]);
-      const double cRx = __ldcg(&ncx[R]), cRy = __ldcg(&ncy[R]), cRz = __ldcg(&ncz[R]);
-      // one division per node (GB300's FP64 pipe is narrow): the centre is
-      // within rounding of the quotient, like the oracle's own sum
-      const double iM = 1.0 / M;
-      const double cx = dmul(dadd(dmul(mL, cLx), dmul(mR, cRx)), iM);
-      const double cy = dmul(dadd(dmul(mL, cLy), dmul(mR, cRy)), iM);
-      const double cz = dmul(dadd(dmul(mL, cLz), dmul(mR, cRz)), iM);
-      ncx[v] = cx;
-      ncy[v] = cy;
-      ncz[v] = cz;
-      if constexpr (P >= 0) {
-        constexpr int NQ = MomOps<P>::NQ;
-        QT qp[NQ];
-  #pragma unroll
-        for (int k = 0; k < NQ; ++k) qp[k] = QT(0);
-        const int kids[2] = {L, R};
-        const double kx[2] = {cLx, cRx}, ky[2] = {cLy, cRy}, kz[2] = {cLz, cRz};
-  #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          QT g[NQ], qc[NQ];
-          MomOps<P>::mono((QT)(kx[c] - cx), (QT)(ky[c] - cy), (QT)(kz[c] - cz), g);
-          load_moments<NQ>(kids[c], qc, Qd, Qf);
-          MomOps<P>::m2m(g, qc, qp);
-        }
-        store_moments<NQ>(v, qp, M, Qd, Qf);
-      }
-      nmass[v] = M;
-      nhmax[v] = dmax_pos(__ldcg(&nhmax[L]), __ldcg(&nhmax[R]));
-      nlu[v] = __ldcg(&nlu[L]) + __ldcg(&nlu[R]);
-  #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const double a = __ldcg(&extv[6 * (size_t)L + c]), b = __ldcg(&extv[6 * (size_t)R + c]);
-        const long long ka = dkey(a), kb = dkey(b);
-        const bool right = (c < 3) ? (kb < ka) : (kb > ka);
-        extv[6 * (size_t)v + c] = right ? b : a;
-        exti[6 * (size_t)v + c] = __ldcg(&exti[6 * (size_t)(right ? R : L) + c]);
-      }
-      v = nparent[v];
+      upward_node<P, QT>(v, R, ncx, ncy, ncz, nmass, nhmax, nlu, extv, exti, Qd, Qf);
+      v = up;
     }
   }
 }
