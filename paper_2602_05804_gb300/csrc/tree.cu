@@ -3,6 +3,7 @@
 // pre-order node layout, node centres of mass, maximum smoothing lengths and
 // exact sizes l = max_j |x_j - s| over each node's particles.
 #include <cfloat>
+#include <climits>
 #include <cuda/atomic>
 
 #include "mom_ops.cuh"
@@ -112,39 +113,84 @@ int exclusive_scan_u32(sfmm_ctx* c, uint32_t* data, int64_t n, uint32_t* total_d
 // ---------------------------------------------------------------------------
 #define BB_NT 256
 
-__global__ void k_bbox_partial(const double* __restrict__ pos, const double* __restrict__ mass,
-                               const double* __restrict__ h, int n, double* __restrict__ part,
-                               int* __restrict__ status) {
-  double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-  int bad = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+// Order-preserving integer key of a finite double and its inverse (signed
+// comparison of keys orders the values; -0 sorts just below +0): extrema and
+// checks on the integer pipe instead of GB300's narrow FP64 pipe.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dkey_inv(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
+// 1 / M for M > 0, within about one unit in the last place: Newton's
+// iteration for the reciprocal, r <- r + r (1 - M r), twice from the FP32
+// reciprocal of M rounded to FP32 (relative error below 2^-22, so below
+// 2^-44 after one step and at FP64 rounding after the second).  Four FP64
+// operations in a dependent chain instead of a correctly rounded division;
+// magnitudes outside FP32's normal range take the division.
+__device__ __forceinline__ double recip_pos(double M) {
+  const float mf = __double2float_rn(M);
+  if (!(mf > 1e-36f && mf < 1e36f)) return 1.0 / M;
+  double r = (double)__frcp_rn(mf);
+  r = fma(r, fma(-M, r, 1.0), r);
+  r = fma(r, fma(-M, r, 1.0), r);
+  return r;
+}
+
+// One particle into a thread's box (as keys) and validity bits: positions,
+// masses and h finite (exponent field not all ones), masses and h > 0 (a
+// positive double's bit pattern is a positive integer; zero, -0 and
+// negatives are not, and NaN fails the test as it fails m > 0).
+__device__ __forceinline__ void bbox_take(const double* __restrict__ pos, const double* __restrict__ mass,
+                                          const double* __restrict__ h, int i, long long (&mn)[3],
+                                          long long (&mx)[3], int& bad) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double v = pos[3 * (int64_t)i + c];
-      if (!isfinite(v)) bad |= SFMM_ST_NONFINITE;
-      mn[c] = fmin(mn[c], v);
-      mx[c] = fmax(mx[c], v);
-    }
-    double m = mass[i], hh = h[i];
-    if (!isfinite(m) || !isfinite(hh)) bad |= SFMM_ST_NONFINITE;
-    if (!(m > 0.0) || !(hh > 0.0)) bad |= SFMM_ST_NONPOSITIVE;
+  for (int c = 0; c < 3; ++c) {
+    const long long b = __double_as_longlong(pos[3 * (int64_t)i + c]);
+    if (((b >> 52) & 0x7ff) == 0x7ff) bad |= SFMM_ST_NONFINITE;
+    const long long k = b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+    mn[c] = min(mn[c], k);
+    mx[c] = max(mx[c], k);
   }
-  __shared__ double s[6][BB_NT / 32];
+  const long long bm = __double_as_longlong(mass[i]), bh = __double_as_longlong(h[i]);
+  if (((bm >> 52) & 0x7ff) == 0x7ff || ((bh >> 52) & 0x7ff) == 0x7ff) bad |= SFMM_ST_NONFINITE;
+  const long long inf = 0x7ff0000000000000LL, mag = 0x7fffffffffffffffLL;
+  if (bm <= 0 || bh <= 0 || (bm & mag) > inf || (bh & mag) > inf) bad |= SFMM_ST_NONPOSITIVE;
+}
+
+// Block-wide extrema of the keys: s[c][w] per warp (min c < 3, max c >= 3).
+__device__ __forceinline__ void bbox_block(long long (&mn)[3], long long (&mx)[3], long long (&s)[6][BB_NT / 32]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     for (int o = 16; o > 0; o >>= 1) {
-      mn[c] = fmin(mn[c], __shfl_xor_sync(SFMM_FULL, mn[c], o));
-      mx[c] = fmax(mx[c], __shfl_xor_sync(SFMM_FULL, mx[c], o));
+      mn[c] = min(mn[c], __shfl_xor_sync(SFMM_FULL, mn[c], o));
+      mx[c] = max(mx[c], __shfl_xor_sync(SFMM_FULL, mx[c], o));
     }
-    if (lane == 0) { s[c][warp] = mn[c]; s[3 + c][warp] = mx[c]; }
+    if (lane == 0) {
+      s[c][warp] = mn[c];
+      s[3 + c][warp] = mx[c];
+    }
   }
   __syncthreads();
+}
+
+__global__ void k_bbox_partial(const double* __restrict__ pos, const double* __restrict__ mass,
+                               const double* __restrict__ h, int n, double* __restrict__ part,
+                               int* __restrict__ status) {
+  long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    bbox_take(pos, mass, h, i, mn, mx, bad);
+  __shared__ long long s[6][BB_NT / 32];
+  bbox_block(mn, mx, s);
   if (threadIdx.x < 6) {
-    int c = threadIdx.x;
-    double v = s[c][0];
-    for (int w = 1; w < BB_NT / 32; ++w) v = (c < 3) ? fmin(v, s[c][w]) : fmax(v, s[c][w]);
-    part[6 * blockIdx.x + c] = v;
+    const int c = threadIdx.x;
+    long long v = s[c][0];
+    for (int w = 1; w < BB_NT / 32; ++w) v = (c < 3) ? min(v, s[c][w]) : max(v, s[c][w]);
+    part[6 * blockIdx.x + c] = dkey_inv(v);
   }
   if (bad) atomicOr(status, bad);
 }
@@ -155,45 +201,23 @@ __global__ void k_bbox_seg(const double* __restrict__ pos, const double* __restr
                            int* __restrict__ status) {
   const int sys = blockIdx.x;
   const int lo = off[sys], hi = off[sys + 1];
-  double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
   int bad = 0;
-  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double v = pos[3 * (int64_t)i + c];
-      if (!isfinite(v)) bad |= SFMM_ST_NONFINITE;
-      mn[c] = fmin(mn[c], v);
-      mx[c] = fmax(mx[c], v);
-    }
-    double m = mass[i], hh = h[i];
-    if (!isfinite(m) || !isfinite(hh)) bad |= SFMM_ST_NONFINITE;
-    if (!(m > 0.0) || !(hh > 0.0)) bad |= SFMM_ST_NONPOSITIVE;
-  }
-  __shared__ double s[6][BB_NT / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    for (int o = 16; o > 0; o >>= 1) {
-      mn[c] = fmin(mn[c], __shfl_xor_sync(SFMM_FULL, mn[c], o));
-      mx[c] = fmax(mx[c], __shfl_xor_sync(SFMM_FULL, mx[c], o));
-    }
-    if (lane == 0) {
-      s[c][warp] = mn[c];
-      s[3 + c][warp] = mx[c];
-    }
-  }
-  __syncthreads();
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) bbox_take(pos, mass, h, i, mn, mx, bad);
+  __shared__ long long s[6][BB_NT / 32];
+  bbox_block(mn, mx, s);
   if (threadIdx.x == 0) {
     double E = 0.0;
     for (int c = 0; c < 3; ++c) {
-      double a = s[c][0], b = s[3 + c][0];
+      long long a = s[c][0], b = s[3 + c][0];
       for (int w = 1; w < BB_NT / 32; ++w) {
-        a = fmin(a, s[c][w]);
-        b = fmax(b, s[3 + c][w]);
+        a = min(a, s[c][w]);
+        b = max(b, s[3 + c][w]);
       }
-      bbox[8 * sys + c] = a;
-      bbox[8 * sys + 3 + c] = b;
-      double e = dsub(b, a);
+      const double da = dkey_inv(a), db = dkey_inv(b);
+      bbox[8 * sys + c] = da;
+      bbox[8 * sys + 3 + c] = db;
+      double e = dsub(db, da);
       if (e > E) E = e;
     }
     bbox[8 * sys + 6] = E;
@@ -745,14 +769,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Order-preserving integer key of a finite double (signed comparison of keys
-// orders the values; -0 sorts just below +0): the axis-extreme comparisons
-// run on the integer pipe instead of GB300's narrow FP64 pipe.
-__device__ __forceinline__ long long dkey(double x) {
-  const long long b = __double_as_longlong(x);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-
 // The larger of two non-negative doubles, compared as bit patterns (exact).
 __device__ __forceinline__ double dmax_pos(double a, double b) {
   const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
@@ -800,7 +816,8 @@ __global__ void k_leaf_geom(const uint32_t* __restrict__ counts, const int* __re
                             double* __restrict__ ncx, double* __restrict__ ncy, double* __restrict__ ncz,
                             double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ pnode,
                             int* __restrict__ nlu, double* __restrict__ extv, int* __restrict__ exti,
-                            double* __restrict__ Qd, float* __restrict__ Qf, int nqs) {
+                            float4* __restrict__ prel, double* __restrict__ Qd, float* __restrict__ Qf,
+                            int nqs) {
   const int nleaves = (int)counts[1];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
     const int v = leaf_node[q];
@@ -834,42 +851,37 @@ __global__ void k_leaf_geom(const uint32_t* __restrict__ counts, const int* __re
       exti[6 * (size_t)v + c] = ei[c];
     }
     nmass[v] = M;
+    // the leaf centre as the oracle forms it (sums of rounded products, one
+    // correctly rounded division per axis): degenerate leaves (coincident
+    // particles) then have exactly its zero offsets
     const double cx = __ddiv_rn(sx, M), cy = __ddiv_rn(sy, M), cz = __ddiv_rn(sz, M);
     ncx[v] = cx;
     ncy[v] = cy;
     ncz[v] = cz;
     nhmax[v] = hm;
     nlu[v] = 1;
-    if constexpr (P >= 0) {
-      constexpr int NQ = MomOps<P>::NQ;
-      QT acc[NQ];
+    // the particles' FP32 records (offsets from the leaf centre, mass) and,
+    // P >= 0, the leaf's moments from the same offsets
+    constexpr int NQ = (P >= 0) ? MomOps<(P >= 0 ? P : 0)>::NQ : 1;
+    QT acc[NQ];
   #pragma unroll
-      for (int k = 0; k < NQ; ++k) acc[k] = QT(0);
-      for (int i = f; i < f + cnt; ++i) {
+    for (int k = 0; k < NQ; ++k) acc[k] = QT(0);
+    for (int i = f; i < f + cnt; ++i) {
+      const double dx = dsub(px[i], cx), dy = dsub(py[i], cy), dz = dsub(pz[i], cz);
+      const float fx = __double2float_rn(dx), fy = __double2float_rn(dy), fz = __double2float_rn(dz);
+      const float fm = __double2float_rn(pm[i]);
+      prel[i] = make_float4(fx, fy, fz, fm);
+      if constexpr (P >= 0) {
         QT mono[NQ];
-        MomOps<P>::mono((QT)(px[i] - cx), (QT)(py[i] - cy), (QT)(pz[i] - cz), mono);
-        const QT m = (QT)pm[i];
+        if constexpr (std::is_same<QT, float>::value) MomOps<P>::mono(fx, fy, fz, mono);
+        else MomOps<P>::mono(dx, dy, dz, mono);
+        const QT m = std::is_same<QT, float>::value ? (QT)fm : (QT)pm[i];
   #pragma unroll
         for (int k = 0; k < NQ; ++k) acc[k] = fma(m, mono[k], acc[k]);
       }
-      store_moments<NQ>(v, acc, M, Qd, Qf);
     }
+    if constexpr (P >= 0) store_moments<NQ>(v, acc, M, Qd, Qf);
   }
-}
-
-// 1 / M for M > 0, within about one unit in the last place: Newton's
-// iteration for the reciprocal, r <- r + r (1 - M r), twice from the FP32
-// reciprocal of M rounded to FP32 (relative error below 2^-22, so below
-// 2^-44 after one step and at FP64 rounding after the second).  Four FP64
-// operations in a dependent chain instead of a correctly rounded division;
-// magnitudes outside FP32's normal range take the division.
-__device__ __forceinline__ double recip_pos(double M) {
-  const float mf = __double2float_rn(M);
-  if (!(mf > 1e-36f && mf < 1e36f)) return 1.0 / M;
-  double r = (double)__frcp_rn(mf);
-  r = fma(r, fma(-M, r, 1.0), r);
-  r = fma(r, fma(-M, r, 1.0), r);
-  return r;
 }
 
 // Node v from its children L = v + 1 and R: centre of mass, moments (P >= 0:
@@ -1030,14 +1042,34 @@ __global__ void k_size_leaf(const uint32_t* __restrict__ counts, const int* __re
                             const double* __restrict__ pz, const double* __restrict__ ncx,
                             const double* __restrict__ ncy, const double* __restrict__ ncz,
                             const float4* __restrict__ geo_hi, const float4* __restrict__ geo_lo,
-                            unsigned long long* __restrict__ l2bits, unsigned long long* __restrict__ cand) {
+                            const float4* __restrict__ prel, unsigned long long* __restrict__ l2bits,
+                            unsigned long long* __restrict__ cand) {
   const int nleaves = (int)counts[1];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
     const int L = leaf_node[q];
     const int f = nfirst[L], cnt = ncount[L];
     const double cx = ncx[L], cy = ncy[L], cz = ncz[L];
-    double l2 = 0.0;
-    for (int i = f; i < f + cnt; ++i) l2 = fmax(l2, exact_d2(px[i], py[i], pz[i], cx, cy, cz));
+    // the particles' FP32 offsets give their squared distances within 2^-21
+    // (relative): only those within 4e-6 of the FP32 maximum can hold the
+    // exact maximum, and only they are evaluated in FP64 (one, as a rule);
+    // offsets too small or too large for that bound take every particle
+    float best = -1.0f;
+    int bi = f;
+    for (int i = f; i < f + cnt; ++i) {
+      const float4 r = prel[i];
+      const float d2 = fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z));
+      if (d2 > best) {
+        best = d2;
+        bi = i;
+      }
+    }
+    double l2 = exact_d2(px[bi], py[bi], pz[bi], cx, cy, cz);
+    const float thr = (best > 1e-30f && best < 1e30f) ? best * (1.0f - 4e-6f) : -1.0f;
+    for (int i = f; i < f + cnt; ++i) {
+      const float4 r = prel[i];
+      if (i != bi && fmaf(r.x, r.x, fmaf(r.y, r.y, r.z * r.z)) >= thr)
+        l2 = fmax(l2, exact_d2(px[i], py[i], pz[i], cx, cy, cz));
+    }
     l2bits[L] = (unsigned long long)__double_as_longlong(l2);
     const float lL = __double2float_ru(__dsqrt_rn(l2));
     const float4 hL = geo_hi[L], oL = geo_lo[L];
@@ -1063,30 +1095,53 @@ __global__ void k_size_leaf(const uint32_t* __restrict__ counts, const int* __re
   }
 }
 
-// Thread per particle: candidate ancestors only; lanes at the same node
+// Thread per particle: candidate ancestors only.  A (particle, ancestor)
+// pair that passes the FP32 test goes to its warp's queue; every 32 queued
+// pairs are evaluated exactly, one per lane (FP64 work costs per warp
+// instruction, whatever the active lanes), and lanes at the same node
 // combine their squared distances, one atomic max per group.
-__global__ void k_size(int n, const double* __restrict__ px, const double* __restrict__ py,
+#define SIZE_NT 256
+__device__ __forceinline__ void size_flush(const int2* q, int cnt, const double* __restrict__ px,
+                                           const double* __restrict__ py, const double* __restrict__ pz,
+                                           const double* __restrict__ ncx, const double* __restrict__ ncy,
+                                           const double* __restrict__ ncz, unsigned long long* __restrict__ l2bits) {
+  const int lane = threadIdx.x & 31;
+  const bool on = lane < cnt;
+  const int2 e = on ? q[lane] : make_int2(0, -1);
+  const unsigned act = __ballot_sync(SFMM_FULL, on);
+  if (on) {
+    const int i = e.x, v = e.y;
+    const double d2 = exact_d2(px[i], py[i], pz[i], ncx[v], ncy[v], ncz[v]);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(d2);
+    const unsigned grp = __match_any_sync(act, v);
+    const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+    const unsigned mhi = __reduce_max_sync(grp, hi);
+    const unsigned mlo = __reduce_max_sync(grp, hi == mhi ? lo : 0u);
+    if ((__ffs(grp) - 1) == lane) atomicMax(&l2bits[v], ((unsigned long long)mhi << 32) | mlo);
+  }
+}
+
+__global__ void __launch_bounds__(SIZE_NT) k_size(int n, const double* __restrict__ px, const double* __restrict__ py,
                        const double* __restrict__ pz, const int* __restrict__ pnode,
                        const uint32_t* __restrict__ leaf_index, const unsigned long long* __restrict__ cand,
                        const int* __restrict__ wparent, const double* __restrict__ ncx,
                        const double* __restrict__ ncy, const double* __restrict__ ncz,
                        const float4* __restrict__ geo_hi, const float4* __restrict__ geo_lo,
                        const float4* __restrict__ prel, unsigned long long* __restrict__ l2bits) {
+  __shared__ int2 s_q[SIZE_NT / 32][64];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int2* const q = s_q[warp];
+  int nq = 0;
   int v = -1;
   unsigned long long m0 = 0ull, m1 = 0ull;
-  double x = 0.0, y = 0.0, z = 0.0;
   float4 hL = make_float4(0.f, 0.f, 0.f, 0.f), oL = hL, r = hL;
   if (i < n) {
     const int L = pnode[i];
     v = wparent[L];  // the leaf itself was done by k_size_leaf
-    const uint32_t q = leaf_index[L];
-    m0 = cand[2 * (size_t)q];
-    m1 = cand[2 * (size_t)q + 1];
-    x = px[i];
-    y = py[i];
-    z = pz[i];
+    const uint32_t ql = leaf_index[L];
+    m0 = cand[2 * (size_t)ql];
+    m1 = cand[2 * (size_t)ql + 1];
     hL = geo_hi[L];
     oL = geo_lo[L];
     r = prel[i];  // x - s_L in FP32
@@ -1106,19 +1161,24 @@ __global__ void k_size(int n, const double* __restrict__ px, const double* __res
       const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
       want = !((d + er + df_dist_err(ox, oy, oz, hL, hv)) * (1.0f + 1e-6f) < hv.w);
     }
-    const unsigned actw = __ballot_sync(SFMM_FULL, want);
-    if (want) {
-      const double d2 = exact_d2(x, y, z, ncx[v], ncy[v], ncz[v]);
-      unsigned long long bits = (unsigned long long)__double_as_longlong(d2);
-      unsigned grp = __match_any_sync(actw, v);
-      unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
-      unsigned mhi = __reduce_max_sync(grp, hi);
-      unsigned mlo = __reduce_max_sync(grp, hi == mhi ? lo : 0u);
-      if ((__ffs(grp) - 1) == lane) atomicMax(&l2bits[v], ((unsigned long long)mhi << 32) | mlo);
+    const unsigned bw = __ballot_sync(SFMM_FULL, want);
+    if (want) q[nq + __popc(bw & lanemask_lt())] = make_int2(i, v);
+    nq += __popc(bw);
+    __syncwarp();
+    if (nq >= 32) {
+      size_flush(q, 32, px, py, pz, ncx, ncy, ncz, l2bits);
+      __syncwarp();
+      const int rest = nq - 32;  // carry the pairs beyond the batch to the front
+      const int2 c = (lane < rest) ? q[32 + lane] : make_int2(0, 0);
+      __syncwarp();
+      if (lane < rest) q[lane] = c;
+      __syncwarp();
+      nq = rest;
     }
     if (v >= 0) v = wparent[v];  // stops after the system root (-1)
     ++k;
   }
+  if (nq > 0) size_flush(q, nq, px, py, pz, ncx, ncy, ncz, l2bits);
 }
 
 // Final node records and float32 particle data.
@@ -1140,19 +1200,14 @@ __global__ void k_finalize_nodes(const uint32_t* __restrict__ counts, const unsi
   }
 }
 
-__global__ void k_particles_f32(int n, const double* __restrict__ px, const double* __restrict__ py,
-                                const double* __restrict__ pz, const double* __restrict__ pm,
-                                const double* __restrict__ ph, const int* __restrict__ pnode,
-                                const double* __restrict__ ncx, const double* __restrict__ ncy,
-                                const double* __restrict__ ncz, float4* __restrict__ prel,
-                                float4* __restrict__ phh) {
+// FP32 softening records of every particle: {1/h, (2h)^2, 2h rounded up}
+// (the offsets and masses come from the leaf pass).
+__global__ void k_particles_hh(int n, const double* __restrict__ ph, float4* __restrict__ phh) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int v = pnode[i];
-  prel[i] = make_float4(__double2float_rn(dsub(px[i], ncx[v])), __double2float_rn(dsub(py[i], ncy[v])),
-                        __double2float_rn(dsub(pz[i], ncz[v])), __double2float_rn(pm[i]));
   const double h = ph[i];
-  phh[i] = make_float4(__double2float_rn(1.0 / h), __double2float_rn(4.0 * h * h), __double2float_ru(2.0 * h), 0.0f);
+  phh[i] = make_float4(__double2float_rn(recip_pos(h)), __double2float_rn(4.0 * h * h), __double2float_ru(2.0 * h),
+                       0.0f);
 }
 
 __global__ void k_depth(const uint32_t* __restrict__ counts, const int* __restrict__ nparent, int* __restrict__ depth) {
@@ -1260,7 +1315,8 @@ static int geom_upward_t(sfmm_ctx* c, int nqs) {
       c->d_counts, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
       c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
       c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),
-      c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->Qd.as<double>(), c->Qf.as<float>(), nqs);
+      c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->prel.as<float4>(), c->Qd.as<double>(),
+      c->Qf.as<float>(), nqs);
   ++c->nlaunch;
   // the second child to finish climbs on (arrival flags cleared by the leaf
   // numbering pass)
@@ -1546,19 +1602,14 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
                                           c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
                                           c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
                                           c->n_lb.as<double>(), c->geo_hi.as<float4>(), c->geo_lo.as<float4>());
-  // FP32 particle records (offsets from the leaf centre) first: the size
-  // tests use them
-  k_particles_f32<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
-                                                c->pm.as<double>(), c->ph.as<double>(), c->pnode.as<int>(),
-                                                c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                                c->prel.as<float4>(), c->phh.as<float4>());
+  k_particles_hh<<<nblk(n, 256), 256, 0, st>>>(n, c->ph.as<double>(), c->phh.as<float4>());
   k_size_leaf<<<leaf_grid(c), 128, 0, st>>>(c->d_counts, c->leaf_node.as<int>(), c->nfirst.as<int>(),
                                             c->ncount.as<int>(), c->wparent.as<int>(), c->px.as<double>(),
                                             c->py.as<double>(), c->pz.as<double>(), c->ncx.as<double>(),
                                             c->ncy.as<double>(), c->ncz.as<double>(), c->geo_hi.as<float4>(),
-                                            c->geo_lo.as<float4>(), c->l2bits.as<unsigned long long>(),
-                                            c->size_cand.as<unsigned long long>());
-  k_size<<<nblk(n, 256), 256, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
+                                            c->geo_lo.as<float4>(), c->prel.as<float4>(),
+                                            c->l2bits.as<unsigned long long>(), c->size_cand.as<unsigned long long>());
+  k_size<<<nblk(n, SIZE_NT), SIZE_NT, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
                                        c->pnode.as<int>(), c->isleaf.as<uint32_t>(),
                                        c->size_cand.as<unsigned long long>(), c->wparent.as<int>(),
                                        c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
