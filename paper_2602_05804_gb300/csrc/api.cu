@@ -181,7 +181,7 @@ std::vector<DevBuf*> ctx_buffers(sfmm_ctx* c) {
                     &c->sys_lsz, &c->psys, &c->sys_root, &c->wparent, &c->sys_sums,
                     &c->p2p_extra, &c->p2p_split, &c->p2p_slist, &c->p2p_part, &c->lf_acc, &c->lf_part,
                     &c->kd_ord, &c->kd_node, &c->kd_act, &c->kd_work, &c->kd_chunk, &c->kd_part, &c->kd_split,
-                    &c->sym_own, &c->sym_recv, &c->wqueue, &c->sort_aux, &c->n_extv, &c->n_exti, &c->n_lb, &c->size_cand};
+                    &c->sym_own, &c->sym_recv, &c->wqueue, &c->sort_aux, &c->n_extv, &c->n_exti, &c->size_cand};
 }
 
 // Addresses and sizes of a context's buffers, folded into one number: a

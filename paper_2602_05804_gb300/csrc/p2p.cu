@@ -695,7 +695,7 @@ __global__ void k_p2p_combine(const P2PArgs a) {
 // sum |m a|, as Neumaier-compensated sums.  Every block takes a contiguous range of
 // sorted positions (thread t: positions lo + t, lo + t + RED_NT, ...), merges
 // its threads' sums in a fixed tree and writes one partial (s and c: 10
-// doubles); one block merges the partials.  Accelerations and potentials are
+// doubles); one warp per sum merges the partials.  Accelerations and potentials are
 // read in caller order through the permutation.  A separate pass costs fewer
 // FP64 instructions per particle than sums formed in the near-field kernel,
 // whose warps hold a leaf of ~11 particles.
@@ -753,14 +753,18 @@ __global__ void __launch_bounds__(RED_NT) k_reduce_particles(int64_t n, const do
   if (threadIdx.x < 10) part[10 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// One warp per sum (block c: sum c), on five SMs: lane l merges partials l,
+// l + 32, ... in order, then the lanes merge in a fixed tree.
 __global__ void k_reduce_final(int nparts, const double* __restrict__ part, double* __restrict__ out) {
-  __shared__ double sh[10][RED_NT];
-  csum s[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
-  for (int q = threadIdx.x; q < nparts; q += RED_NT)
+  const int c = blockIdx.x, lane = threadIdx.x;
+  csum s{0.0, 0.0};
+  for (int q = lane; q < nparts; q += 32) cs_merge(s, part[10 * q + c], part[10 * q + 5 + c]);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) cs_merge(s[c], part[10 * q + c], part[10 * q + 5 + c]);
-  block_merge(s, sh);
-  if (threadIdx.x < 5) out[threadIdx.x] = __dadd_rn(sh[threadIdx.x][0], sh[5 + threadIdx.x][0]);
+  for (int o = 16; o > 0; o >>= 1) {
+    const double bs = __shfl_down_sync(SFMM_FULL, s.s, o), bc = __shfl_down_sync(SFMM_FULL, s.c, o);
+    if (lane < o) cs_merge(s, bs, bc);
+  }
+  if (lane == 0) out[c] = __dadd_rn(s.s, s.c);
 }
 
 // Per-system sums of a batch: one block per system over its range of sorted
@@ -898,7 +902,7 @@ int run_reduce(sfmm_ctx* c, double** out_dev) {
   k_reduce_particles<<<RED_BLOCKS, RED_NT, 0, c->stream>>>(c->n, c->pm.as<double>(), c->perm.as<int>(), c->red_acc,
                                                           c->red_pot, part);
   ++c->nlaunch;
-  k_reduce_final<<<1, RED_NT, 0, c->stream>>>(RED_BLOCKS, part, out);
+  k_reduce_final<<<5, 32, 0, c->stream>>>(RED_BLOCKS, part, out);
   ++c->nlaunch;
   *out_dev = out;
   SFMM_CUDA_TRY(cudaGetLastError());

@@ -102,7 +102,7 @@ struct sfmm_ctx {
   DevBuf geo_hi, geo_lo;        // float4 walk records
   DevBuf leaf_node, isleaf;
   DevBuf nlu;                   // leaves under each node
-  DevBuf n_extv, n_exti, n_lb;  // axis-extreme particles (values, positions), size lower bounds
+  DevBuf n_extv, n_exti;        // axis-extreme particles (values, positions)
   DevBuf size_cand;             // per leaf: ancestors its particles may hold the size of
   DevBuf level_nodes, level_off, level_cur;  // internal nodes grouped by depth
   DevBuf leaf_order;            // leaves by depth, shallowest first

@@ -139,6 +139,17 @@ __device__ __forceinline__ double recip_pos(double M) {
   return r;
 }
 
+// A node's centre as double-float walk records (w fields: filled later).
+__device__ __forceinline__ void store_centre_df(int v, double cx, double cy, double cz, float4* __restrict__ geo_hi,
+                                                float4* __restrict__ geo_lo) {
+  float xh, xl, yh, yl, zh, zl;
+  split_double(cx, xh, xl);
+  split_double(cy, yh, yl);
+  split_double(cz, zh, zl);
+  geo_hi[v] = make_float4(xh, yh, zh, 0.0f);
+  geo_lo[v] = make_float4(xl, yl, zl, 0.0f);
+}
+
 // One particle into a thread's box (as keys) and validity bits: positions,
 // masses and h finite (exponent field not all ones), masses and h > 0 (a
 // positive double's bit pattern is a positive integer; zero, -0 and
@@ -279,10 +290,11 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
   return v;
 }
 
+// floor((x - mn) scale) clamped to [0, 2^21 - 1]: the conversion rounds
+// down (exactly floor, saturating out of range), the clamp is on integers.
 __device__ __forceinline__ uint64_t quantise(double x, double mn, double scale) {
-  double v = floor(dmul(dsub(x, mn), scale));
-  uint64_t k = (v > 0.0) ? (uint64_t)v : 0ull;
-  return k > 2097151ull ? 2097151ull : k;
+  const long long v = __double2ll_rd(dmul(dsub(x, mn), scale));
+  return (uint64_t)min(max(v, 0LL), 2097151LL);
 }
 
 __global__ void k_morton(const double* __restrict__ pos, int n, const double* __restrict__ bbox0,
@@ -816,8 +828,8 @@ __global__ void k_leaf_geom(const uint32_t* __restrict__ counts, const int* __re
                             double* __restrict__ ncx, double* __restrict__ ncy, double* __restrict__ ncz,
                             double* __restrict__ nmass, double* __restrict__ nhmax, int* __restrict__ pnode,
                             int* __restrict__ nlu, double* __restrict__ extv, int* __restrict__ exti,
-                            float4* __restrict__ prel, double* __restrict__ Qd, float* __restrict__ Qf,
-                            int nqs) {
+                            float4* __restrict__ prel, float4* __restrict__ geo_hi, float4* __restrict__ geo_lo,
+                            double* __restrict__ Qd, float* __restrict__ Qf, int nqs) {
   const int nleaves = (int)counts[1];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
     const int v = leaf_node[q];
@@ -858,6 +870,7 @@ __global__ void k_leaf_geom(const uint32_t* __restrict__ counts, const int* __re
     ncx[v] = cx;
     ncy[v] = cy;
     ncz[v] = cz;
+    store_centre_df(v, cx, cy, cz, geo_hi, geo_lo);
     nhmax[v] = hm;
     nlu[v] = 1;
     // the particles' FP32 records (offsets from the leaf centre, mass) and,
@@ -996,41 +1009,61 @@ __device__ __forceinline__ double exact_d2(double x, double y, double z, double 
   return dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
 }
 
-__global__ void k_node_lb(const uint32_t* __restrict__ counts, const int* __restrict__ wparent, const int* __restrict__ exti,
-                          const double* __restrict__ px, const double* __restrict__ py,
-                          const double* __restrict__ pz, const double* __restrict__ ncx,
-                          const double* __restrict__ ncy, const double* __restrict__ ncz, double* __restrict__ lb,
-                          float4* __restrict__ geo_hi, float4* __restrict__ geo_lo) {
-  const int nn = (int)counts[0];
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
-    double m = 0.0;
-    const double cx = ncx[v], cy = ncy[v], cz = ncz[v];
-    if (wparent[v] != -2) {
-  #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const int e = exti[6 * (size_t)v + c];
-        m = fmax(m, exact_d2(px[e], py[e], pz[e], cx, cy, cz));
-      }
-    }
-    const double l = __dsqrt_rn(m);
-    lb[v] = l;
-    // the centre as double-float (final records; w: the size, written last)
-    // and, until then, LB rounded down for the FP32 candidate tests
-    float xh, xl, yh, yl, zh, zl;
-    split_double(cx, xh, xl);
-    split_double(cy, yh, yl);
-    split_double(cz, zh, zl);
-    geo_hi[v] = make_float4(xh, yh, zh, __double2float_rd(l));
-    geo_lo[v] = make_float4(xl, yl, zl, 0.0f);
-  }
-}
-
 // Upper bound on the error of an FP32 distance assembled from double-float
 // centre differences (each within a few units of 2^-24 of its value, the
 // centres within 2^-48 of theirs) and FP32 offsets: generous by two orders.
 __device__ __forceinline__ float df_dist_err(float ox, float oy, float oz, float4 a, float4 b) {
   return 2e-6f * (fabsf(ox) + fabsf(oy) + fabsf(oz)) +
          1e-13f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + fabsf(b.x) + fabsf(b.y) + fabsf(b.z));
+}
+
+// An internal node's centre as double-float walk records (the leaf pass
+// wrote the leaves'), and LB(v) in FP32, rounded down: the largest distance
+// from s_v among the node's six axis-extreme particles, each assembled from
+// the particle's FP32 offset in its leaf and the double-float difference of
+// the leaf's and v's centres, less that sum's error bound (so LB(v) never
+// exceeds the real distance, nor, hence, l_v), in the w field of v's record.
+// A thread reads the records of leaves only, besides its own node's.
+__global__ void k_node_lb(const uint32_t* __restrict__ counts, const int* __restrict__ wparent,
+                          const int* __restrict__ nright, const int* __restrict__ exti,
+                          const int* __restrict__ pnode, const double* __restrict__ ncx,
+                          const double* __restrict__ ncy, const double* __restrict__ ncz,
+                          const float4* __restrict__ prel, float4* __restrict__ geo_hi,
+                          float4* __restrict__ geo_lo) {
+  const int nn = (int)counts[0];
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+    float4 hv, ov;
+    if (nright[v] >= 0) {
+      float xh, xl, yh, yl, zh, zl;
+      split_double(ncx[v], xh, xl);
+      split_double(ncy[v], yh, yl);
+      split_double(ncz[v], zh, zl);
+      hv = make_float4(xh, yh, zh, 0.0f);
+      ov = make_float4(xl, yl, zl, 0.0f);
+      geo_lo[v] = ov;
+    } else {
+      hv = geo_hi[v];
+      ov = geo_lo[v];
+    }
+    float lbv = 0.0f;
+    if (wparent[v] != -2) {
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const int e = exti[6 * (size_t)v + c];
+        const int L = pnode[e];
+        const float4 r = prel[e], hL = geo_hi[L], oL = geo_lo[L];
+        const float ox = df_diff(hL.x, oL.x, hv.x, ov.x), oy = df_diff(hL.y, oL.y, hv.y, ov.y),
+                    oz = df_diff(hL.z, oL.z, hv.z, ov.z);
+        const float dx = r.x + ox, dy = r.y + oy, dz = r.z + oz;
+        const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float err = 2e-6f * (fabsf(r.x) + fabsf(r.y) + fabsf(r.z)) + df_dist_err(ox, oy, oz, hL, hv);
+        lbv = fmaxf(lbv, (d - err) * (1.0f - 1e-6f));
+      }
+    }
+    hv.w = lbv;
+    if (nright[v] >= 0) geo_hi[v] = hv;
+    else reinterpret_cast<float*>(&geo_hi[v])[3] = lbv;  // only w: other threads read a leaf's centre
+  }
 }
 
 // Thread per leaf: the leaf's exact size, and which ancestors it is a
@@ -1181,22 +1214,17 @@ __global__ void __launch_bounds__(SIZE_NT) k_size(int n, const double* __restric
   if (nq > 0) size_flush(q, nq, px, py, pz, ncx, ncy, ncz, l2bits);
 }
 
-// Final node records and float32 particle data.
+// Final node records: the sizes and h_max into the w fields (the centres
+// were written with the nodes).
 __global__ void k_finalize_nodes(const uint32_t* __restrict__ counts, const unsigned long long* __restrict__ l2bits,
-                                 const double* __restrict__ ncx, const double* __restrict__ ncy,
-                                 const double* __restrict__ ncz, const double* __restrict__ nhmax,
-                                 double* __restrict__ nsize, float4* __restrict__ geo_hi,
-                                 float4* __restrict__ geo_lo) {
+                                 const double* __restrict__ nhmax, double* __restrict__ nsize,
+                                 float4* __restrict__ geo_hi, float4* __restrict__ geo_lo) {
   const int nn = (int)counts[0];
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
-    double l = __dsqrt_rn(__longlong_as_double((long long)l2bits[v]));
+    const double l = __dsqrt_rn(__longlong_as_double((long long)l2bits[v]));
     nsize[v] = l;
-    float xh, xl, yh, yl, zh, zl;
-    split_double(ncx[v], xh, xl);
-    split_double(ncy[v], yh, yl);
-    split_double(ncz[v], zh, zl);
-    geo_hi[v] = make_float4(xh, yh, zh, __double2float_rn(l));
-    geo_lo[v] = make_float4(xl, yl, zl, __double2float_rn(nhmax[v]));
+    reinterpret_cast<float*>(&geo_hi[v])[3] = __double2float_rn(l);
+    reinterpret_cast<float*>(&geo_lo[v])[3] = __double2float_rn(nhmax[v]);
   }
 }
 
@@ -1315,8 +1343,8 @@ static int geom_upward_t(sfmm_ctx* c, int nqs) {
       c->d_counts, c->leaf_node.as<int>(), c->nfirst.as<int>(), c->ncount.as<int>(), c->px.as<double>(),
       c->py.as<double>(), c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(), c->ncx.as<double>(),
       c->ncy.as<double>(), c->ncz.as<double>(), c->nmass.as<double>(), c->nhmax.as<double>(), c->pnode.as<int>(),
-      c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->prel.as<float4>(), c->Qd.as<double>(),
-      c->Qf.as<float>(), nqs);
+      c->nlu.as<int>(), c->n_extv.as<double>(), c->n_exti.as<int>(), c->prel.as<float4>(), c->geo_hi.as<float4>(),
+      c->geo_lo.as<float4>(), c->Qd.as<double>(), c->Qf.as<float>(), nqs);
   ++c->nlaunch;
   // the second child to finish climbs on (arrival flags cleared by the leaf
   // numbering pass)
@@ -1424,7 +1452,6 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ENS(nlu, sizeof(int) * nn_max);
   ENS(n_extv, sizeof(double) * 6 * nn_max);
   ENS(n_exti, sizeof(int) * 6 * nn_max);
-  ENS(n_lb, sizeof(double) * nn_max);
   ENS(size_cand, sizeof(unsigned long long) * 2 * nn_max);
   const int nbb = 2 * num_sms(c->device);
   ENS(bbox_part, sizeof(double) * 6 * nbb);
@@ -1598,10 +1625,10 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     default: rc = geom_upward<4>(c, nqs); break;
   }
   if (rc) return rc;
-  k_node_lb<<<node_grid(c), 256, 0, st>>>(c->d_counts, c->wparent.as<int>(), c->n_exti.as<int>(),
-                                          c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
-                                          c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
-                                          c->n_lb.as<double>(), c->geo_hi.as<float4>(), c->geo_lo.as<float4>());
+  k_node_lb<<<node_grid(c), 256, 0, st>>>(c->d_counts, c->wparent.as<int>(), c->nright.as<int>(), c->n_exti.as<int>(),
+                                          c->pnode.as<int>(), c->ncx.as<double>(), c->ncy.as<double>(),
+                                          c->ncz.as<double>(), c->prel.as<float4>(), c->geo_hi.as<float4>(),
+                                          c->geo_lo.as<float4>());
   k_particles_hh<<<nblk(n, 256), 256, 0, st>>>(n, c->ph.as<double>(), c->phh.as<float4>());
   k_size_leaf<<<leaf_grid(c), 128, 0, st>>>(c->d_counts, c->leaf_node.as<int>(), c->nfirst.as<int>(),
                                             c->ncount.as<int>(), c->wparent.as<int>(), c->px.as<double>(),
@@ -1617,7 +1644,6 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
                                        c->l2bits.as<unsigned long long>());
   c->nlaunch += 4;
   k_finalize_nodes<<<node_grid(c), 256, 0, st>>>(c->d_counts, c->l2bits.as<unsigned long long>(),
-                                                 c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
                                                  c->nhmax.as<double>(), c->nsize.as<double>(), c->geo_hi.as<float4>(),
                                                  c->geo_lo.as<float4>());
   ++c->nlaunch;
