@@ -44,6 +44,7 @@ struct LevelArgs {
   // filled), slots handed out by q_head, filled through q_tail; q_total
   // walkable nodes in all
   int* queue;
+  long long* queue64;  // node queue: (walk parent + 1) << 32 | node, -1 while unfilled
   int* q_head;
   int* q_tail;
   int q_total;
@@ -245,25 +246,28 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
       __threadfence();
       __syncwarp();
       if (lane == 0) {
+        // each entry carries the parent, so that a child reads the parent's
+        // list without first looking the parent up
         const int t = atomicAdd(la.q_tail, 2);
-        la.queue[t] = node + 1;
-        la.queue[t + 1] = right;
+        const long long up = (long long)(node + 1) << 32;
+        la.queue64[t] = up | (unsigned)(node + 1);
+        la.queue64[t + 1] = up | (unsigned)right;
       }
     }
   };
   // queue walk: every walkable node (all but the nsys - 1 spanning systems)
   const int q_total = queue ? (int)la.counts[0] - (la.nsys - 1) : 0;
   while (true) {
-    int A;
+    int A, par;
     if constexpr (queue) {
       int slot = 0;
       if (lane == 0) slot = atomicAdd(la.q_head, 1);
       slot = __shfl_sync(SFMM_FULL, slot, 0);
       if (slot >= q_total) break;
-      int got = -1;
+      long long got = -1;
       if (lane == 0) {
         for (int it = 0; it < SFMM_QUEUE_SPIN; ++it) {
-          got = *reinterpret_cast<volatile int*>(la.queue + slot);
+          got = *reinterpret_cast<volatile long long*>(la.queue64 + slot);
           if (got >= 0) break;
           __nanosleep(64);
         }
@@ -274,17 +278,18 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
         break;
       }
       __threadfence();
-      A = got;
+      A = (int)(got & 0xffffffffLL);
+      par = (int)(got >> 32) - 1;
     } else {
       int idx = 0;
       if (lane == 0) idx = atomicAdd(a.leaf_counter, 1);
       idx = __shfl_sync(SFMM_FULL, idx, 0);
       if (idx >= la.level_count) break;
       A = la.level_nodes[la.level_begin + idx];
+      par = la.nparent[A];
     }
     const int rA = a.nright[A];
     const bool leafA = rA < 0;
-    const int par = la.nparent[A];
     const float4 hiA = a.geo_hi[A], loA = a.geo_lo[A];
     double cAx = 0.0, cAy = 0.0, cAz = 0.0;
     if (!F32) {
@@ -613,10 +618,10 @@ __global__ void __launch_bounds__(WALK_NT) k_walk_finalize(const LevelArgs la, i
   }
 }
 
-// Queue walk: the system roots fill the first slots.
-__global__ void k_queue_seed(int nsys, const int* __restrict__ sys_root, int* __restrict__ queue,
+// Queue walk: the system roots (no walk parent) fill the first slots.
+__global__ void k_queue_seed(int nsys, const int* __restrict__ sys_root, long long* __restrict__ queue,
                              int* __restrict__ tail) {
-  for (int i = threadIdx.x; i < nsys; i += blockDim.x) queue[i] = sys_root[i];
+  for (int i = threadIdx.x; i < nsys; i += blockDim.x) queue[i] = (long long)(unsigned)sys_root[i];
   if (threadIdx.x == 0) *tail = nsys;
 }
 
@@ -763,15 +768,17 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
       // nl) = nn + 1 - nl items
       la.q_total = pairs ? nn + 1 - nl : nn - (c->nsys - 1);  // (the kernels take it from the counts)
       const int q_bound = c->graph_mode ? nn_b : la.q_total;
-      if ((rc = c->wqueue.ensure(sizeof(int) * (size_t)(q_bound + 1)))) return rc;
+      if ((rc = c->wqueue.ensure(sizeof(long long) * (size_t)(q_bound + 1)))) return rc;
       la.queue = c->wqueue.as<int>();
+      la.queue64 = c->wqueue.as<long long>();
       la.q_head = reinterpret_cast<int*>(ctr + 14);
       la.q_tail = reinterpret_cast<int*>(ctr + 15);
       la.counts = c->d_counts;
       la.nsys = c->nsys;
-      SFMM_CUDA_TRY(cudaMemsetAsync(la.queue, 0xff, sizeof(int) * (size_t)q_bound, c->stream));
+      SFMM_CUDA_TRY(cudaMemsetAsync(la.queue, 0xff, (pairs ? sizeof(int) : sizeof(long long)) * (size_t)q_bound,
+                                    c->stream));
       if (pairs) k_queue_seed_pairs<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), la.queue, la.q_tail);
-      else k_queue_seed<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), la.queue, la.q_tail);
+      else k_queue_seed<<<1, 32, 0, c->stream>>>(c->nsys, c->sys_root.as<int>(), la.queue64, la.q_tail);
       la.level = 0;
       la.level_nodes = nullptr;
       la.level_begin = 0;
