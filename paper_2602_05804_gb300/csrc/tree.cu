@@ -403,6 +403,7 @@ __global__ void __launch_bounds__(RS_NT) k_rs_scatter(const uint64_t* __restrict
 // Bounded wait on an earlier tile's word (it is running, so the wait ends;
 // the limit only turns a fault into an error status)
 #define RS_SPIN (1 << 22)
+#define RS_LOOK 4  // predecessor tiles read per look-back round trip
 #ifndef OS_ITEMS
 #define OS_ITEMS 8  // keys per thread of a onesweep tile (4, 8, 16 measured: 8 best)
 #endif
@@ -469,20 +470,31 @@ __global__ void __launch_bounds__(RS_NT) k_rs_onesweep(const uint64_t* __restric
     for (int w = 0; w < RS_WARPS; ++w) cnt += wc[w][d];
     volatile uint32_t* st = tstat;
     st[(int64_t)tile * 256 + d] = (tile == 0 ? RS_FLAG_INC : RS_FLAG_AGG) | cnt;
+    // look back RS_LOOK tiles per round trip: their words are read at once
+    // and taken in order up to the first inclusive one (done) or the first
+    // not yet published (read again from there); tile 0 is always inclusive
     uint32_t excl = 0;
     int t = tile - 1, spins = 0;
     while (t >= 0) {
-      const uint32_t w = st[(int64_t)t * 256 + d];
-      if ((w & ~RS_COUNT_MASK) == 0u) {
-        if (++spins > RS_SPIN) {
-          set_status(status, SFMM_ST_INTERNAL);
-          break;
+      uint32_t w[RS_LOOK];
+#pragma unroll
+      for (int k = 0; k < RS_LOOK; ++k) w[k] = (t - k >= 0) ? st[(int64_t)(t - k) * 256 + d] : 0u;
+      int k = 0;
+      bool done = false;
+#pragma unroll
+      for (int q = 0; q < RS_LOOK; ++q) {
+        if (k == q && t - q >= 0 && (w[q] & ~RS_COUNT_MASK) != 0u) {
+          excl += w[q] & RS_COUNT_MASK;
+          if ((w[q] & ~RS_COUNT_MASK) == RS_FLAG_INC) done = true;
+          else k = q + 1;
         }
-        continue;
       }
-      excl += w & RS_COUNT_MASK;
-      if ((w & ~RS_COUNT_MASK) == RS_FLAG_INC) break;
-      --t;
+      if (done) break;
+      t -= k;
+      if (k == 0 && ++spins > RS_SPIN) {
+        set_status(status, SFMM_ST_INTERNAL);
+        break;
+      }
     }
     if (tile > 0) st[(int64_t)tile * 256 + d] = RS_FLAG_INC | (excl + cnt);
     s_tot[d] = ghist[d];
