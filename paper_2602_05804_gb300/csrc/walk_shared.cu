@@ -238,28 +238,36 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
   unsigned long long st_m2l_p = 0;  // mode 2: replicated count of the partner sides, per lane
   int st_fb = 0;
 
-  // queue walk: an internal node hands its children on once everything they
-  // read (coefficients, opened list) is written
+  // queue walk: an internal node hands its right child on through the queue
+  // once everything the child reads (coefficients, opened list) is written,
+  // and goes on with its left child itself (no queue round trip, no wait:
+  // the warp wrote what the child reads)
   constexpr bool queue = QUEUE;
+  int next = -1;  // queue walk: the left child this warp takes next
   auto push_children = [&](int node, int right) {
     if constexpr (queue) {
       __threadfence();
       __syncwarp();
       if (lane == 0) {
-        // each entry carries the parent, so that a child reads the parent's
-        // list without first looking the parent up
-        const int t = atomicAdd(la.q_tail, 2);
-        const long long up = (long long)(node + 1) << 32;
-        la.queue64[t] = up | (unsigned)(node + 1);
-        la.queue64[t + 1] = up | (unsigned)right;
+        // the entry carries the parent, so that the child reads the
+        // parent's list without first looking the parent up
+        const int t = atomicAdd(la.q_tail, 1);
+        la.queue64[t] = ((long long)(node + 1) << 32) | (unsigned)right;
       }
+      next = node + 1;
     }
   };
-  // queue walk: every walkable node (all but the nsys - 1 spanning systems)
-  const int q_total = queue ? (int)la.counts[0] - (la.nsys - 1) : 0;
+  // queue walk: the system roots and every walkable internal node's right
+  // child (walkable: all but the nsys - 1 nodes spanning systems; a full
+  // binary tree per system), counts[0] + 1 - counts[1] items
+  const int q_total = queue ? (int)la.counts[0] + 1 - (int)la.counts[1] : 0;
   while (true) {
     int A, par;
-    if constexpr (queue) {
+    if (queue && next >= 0) {
+      par = next - 1;
+      A = next;
+      next = -1;
+    } else if constexpr (queue) {
       int slot = 0;
       if (lane == 0) slot = atomicAdd(la.q_head, 1);
       slot = __shfl_sync(SFMM_FULL, slot, 0);
@@ -761,12 +769,12 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     la.queue = nullptr;
     if (queue) {
       // one launch: a warp takes the next slot of the queue and waits until
-      // the item there has been pushed.  Node queue: every walkable node,
-      // leaves included (all nodes but the nsys - 1 that span several
-      // systems), the system roots first.  Pair queue: the system roots and
-      // the children of every walkable internal node, nsys + (nn - nsys + 1 -
-      // nl) = nn + 1 - nl items
-      la.q_total = pairs ? nn + 1 - nl : nn - (c->nsys - 1);  // (the kernels take it from the counts)
+      // the item there has been pushed.  Node queue: the system roots first,
+      // then the right child of every walkable internal node (its left child
+      // goes on in the parent's warp).  Pair queue: the system roots and the
+      // children of every walkable internal node.  Both: nsys + (nn - nsys +
+      // 1 - nl) = nn + 1 - nl items
+      la.q_total = nn + 1 - nl;  // (the kernels take it from the counts)
       const int q_bound = c->graph_mode ? nn_b : la.q_total;
       if ((rc = c->wqueue.ensure(sizeof(long long) * (size_t)(q_bound + 1)))) return rc;
       la.queue = c->wqueue.as<int>();
