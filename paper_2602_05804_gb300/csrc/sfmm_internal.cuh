@@ -46,7 +46,7 @@ struct sfmm_ctx {
   std::vector<int> h_sys_lsz;
   DevBuf sys_off, sys_lsz, psys, sys_root, wparent, sys_sums;
   int32_t nnodes = 0, nleaves = 0;  // host copies, valid once a build has returned
-  uint32_t* d_counts = nullptr;      // device: node count, leaf count of the current build
+  uint32_t* d_counts = nullptr;      // device: node count, leaf count of the current build, leaf-pair parents
   bool graph_mode = false;           // buffers sized for a captured step (bounds, device counts)
   // captured step (sfmm_solve_graph): one graph per shape class, with the
   // class it was captured for and the fingerprint of the buffers it uses;

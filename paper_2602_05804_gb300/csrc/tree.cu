@@ -1250,15 +1250,29 @@ __global__ void k_particles_hh(int n, const double* __restrict__ ph, float4* __r
                        0.0f);
 }
 
-__global__ void k_depth(const uint32_t* __restrict__ counts, const int* __restrict__ nparent, int* __restrict__ depth) {
+// Node depths, and counts[2]: the walkable internal nodes whose children are
+// both leaves (the node-queue walk takes both in the parent's warp and
+// queues neither, so its queue holds that many items fewer).
+__global__ void k_depth(uint32_t* __restrict__ counts, const int* __restrict__ nparent,
+                        const int* __restrict__ nright, const int* __restrict__ wparent, int* __restrict__ depth) {
   const int nn = (int)counts[0];
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
-    int d = 0, u = nparent[v];
-    while (u >= 0) {
-      ++d;
-      u = nparent[u];
+  const int lane = threadIdx.x & 31;
+  // warp-aligned strides, so that every lane of a warp runs the same trips
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nn; base += gridDim.x * blockDim.x) {
+    const int v = base + lane;
+    bool pair = false;
+    if (v < nn) {
+      int d = 0, u = nparent[v];
+      while (u >= 0) {
+        ++d;
+        u = nparent[u];
+      }
+      depth[v] = d;
+      const int r = nright[v];
+      pair = r >= 0 && wparent[v] != -2 && nright[v + 1] < 0 && nright[r] < 0;
     }
-    depth[v] = d;
+    const unsigned b = __ballot_sync(SFMM_FULL, pair);
+    if (lane == 0 && b) atomicAdd(&counts[2], (unsigned)__popc(b));
   }
 }
 
@@ -1335,7 +1349,9 @@ static inline unsigned leaf_grid(const sfmm_ctx* c) {
 int compute_depth(sfmm_ctx* c) {
   int rc = c->ndepth.ensure(sizeof(int) * 2 * (size_t)c->n);
   if (rc) return rc;
-  k_depth<<<node_grid(c), 256, 0, c->stream>>>(c->d_counts, c->nparent.as<int>(), c->ndepth.as<int>());
+  SFMM_CUDA_TRY(cudaMemsetAsync(c->d_counts + 2, 0, sizeof(uint32_t), c->stream));
+  k_depth<<<node_grid(c), 256, 0, c->stream>>>(c->d_counts, c->nparent.as<int>(), c->nright.as<int>(),
+                                               c->wparent.as<int>(), c->ndepth.as<int>());
   ++c->nlaunch;
   SFMM_CUDA_TRY(cudaGetLastError());
   return SFMM_OK;

@@ -241,32 +241,39 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
   // queue walk: an internal node hands its right child on through the queue
   // once everything the child reads (coefficients, opened list) is written,
   // and goes on with its left child itself (no queue round trip, no wait:
-  // the warp wrote what the child reads)
+  // the warp wrote what the child reads); when both children are leaves it
+  // takes both and queues neither
   constexpr bool queue = QUEUE;
-  int next = -1;  // queue walk: the left child this warp takes next
-  auto push_children = [&](int node, int right) {
+  int next = -1, next2 = -1, next_par = -1;  // queue walk: the children this warp takes next
+  auto push_children = [&](int node, int right, bool two_leaves) {
     if constexpr (queue) {
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) {
-        // the entry carries the parent, so that the child reads the
-        // parent's list without first looking the parent up
-        const int t = atomicAdd(la.q_tail, 1);
-        la.queue64[t] = ((long long)(node + 1) << 32) | (unsigned)right;
+      if (!two_leaves) {
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+          // the entry carries the parent, so that the child reads the
+          // parent's list without first looking the parent up
+          const int t = atomicAdd(la.q_tail, 1);
+          la.queue64[t] = ((long long)(node + 1) << 32) | (unsigned)right;
+        }
       }
       next = node + 1;
+      next2 = two_leaves ? right : -1;
+      next_par = node;
     }
   };
-  // queue walk: the system roots and every walkable internal node's right
-  // child (walkable: all but the nsys - 1 nodes spanning systems; a full
-  // binary tree per system), counts[0] + 1 - counts[1] items
-  const int q_total = queue ? (int)la.counts[0] + 1 - (int)la.counts[1] : 0;
+  // queue walk: the system roots and the right child of every walkable
+  // internal node whose children are not both leaves (walkable: all but the
+  // nsys - 1 nodes spanning systems; a full binary tree per system):
+  // counts[0] + 1 - counts[1] - counts[2] items
+  const int q_total = queue ? (int)la.counts[0] + 1 - (int)la.counts[1] - (int)la.counts[2] : 0;
   while (true) {
     int A, par;
     if (queue && next >= 0) {
-      par = next - 1;
+      par = next_par;
       A = next;
-      next = -1;
+      next = next2;
+      next2 = -1;
     } else if constexpr (queue) {
       int slot = 0;
       if (lane == 0) slot = atomicAdd(la.q_head, 1);
@@ -298,6 +305,9 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
     }
     const int rA = a.nright[A];
     const bool leafA = rA < 0;
+    // (queue walk) whether both children are leaves: loaded now, used at the end
+    bool two_leaves = false;
+    if (queue && !leafA) two_leaves = a.nright[A + 1] < 0 && a.nright[rA] < 0;
     const float4 hiA = a.geo_hi[A], loA = a.geo_lo[A];
     double cAx = 0.0, cAy = 0.0, cAz = 0.0;
     if (!F32) {
@@ -330,7 +340,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
           set_status(a.status, SFMM_ST_CHILDLIST);
           la.cf_cnt_out[A] = 0;
         }
-        push_children(A, rA);
+        push_children(A, rA, two_leaves);
         continue;
       }
       cfw = la.cf_out + cfbase;
@@ -484,7 +494,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
         if (leafA) a.p2p_cnt[la.leaf_index[A]] = 0;
         else la.cf_cnt_out[A] = 0;
       }
-      if (!leafA) push_children(A, rA);
+      if (!leafA) push_children(A, rA, two_leaves);
       continue;
     }
     if (lane == 0) {
@@ -520,7 +530,7 @@ __global__ void __launch_bounds__(WALK_NT, (P <= 2 && F32) ? (QUEUE ? 5 : 4) : 1
         la.cf_cnt_out[A] = nn;
       }
       __syncwarp();
-      push_children(A, rA);
+      push_children(A, rA, two_leaves);
       continue;
     }
 
