@@ -762,8 +762,8 @@ def run_gpu(args):
     # the shared walk under its three node orders (bitwise the same results):
     # one launch per depth, one launch over a queue of nodes whose parent is
     # done, and the same over a queue of sibling pairs; the automatic choice
-    # takes the node queue while the walk's per-node records fit in L2, else
-    # the pair queue
+    # takes the node queue while the walk's per-node records take at most
+    # twice the L2, else the pair queue
     schedules = {}
     for sched, label in ((1, "one launch per depth"), (2, "readiness queue of nodes"),
                          (3, "readiness queue of sibling pairs")):

@@ -119,8 +119,8 @@ int sfmm_set_stream(sfmm_ctx* ctx, void* stream);
  *                    parent is done from a queue; 3 the same with both
  *                    children of a node taken by one warp (their common
  *                    inherited list read once); 0 (default) chooses 2 when
- *                    the walk's per-node records fit in three quarters of the
- *                    L2 cache, else 3; bitwise the same results
+ *                    the walk's per-node records take at most twice the L2
+ *                    cache, else 3; bitwise the same results
  *   "tree"           0 (default): binary radix tree over Morton keys (Sect. 3);
  *                    1: centre-of-mass-pivot kd tree (Sect. 3; single
  *                    systems only, sfmm_build_batch returns ENOTIMPL)

@@ -664,9 +664,10 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
   // depth; 2 readiness queue of nodes; 3 readiness queue of sibling pairs
   // (each record load serves both children's decisions, at fewer warps per
   // SM); 0 chooses 2 while the walk's records (geometry, moments,
-  // coefficients, list offsets) fit in three quarters of L2, else 3
-  // (measured: 2 is 3 % faster on the 10^6 Plummer sphere, 3 is 6-10 %
-  // faster than both others on the 2x10^6 binary and the 1.6x10^7 cloud)
+  // coefficients, list offsets) take at most twice the L2, else 3
+  // (measured on GB300: 2 is faster on the 10^6 Plummer sphere, 1.21 against
+  // 1.32 ms, records 64 MB, and on the 2x10^6 binary, 2.11 against 2.17 ms,
+  // records 127 MB; 3 on the 1.6x10^7 cloud, 16.3 against 17.4 ms, 1 GB)
   int sched = SYM ? 1 : c->schedule;
   if (sched == 0) {
     int l2 = 0;
@@ -675,7 +676,7 @@ static int run_levels(sfmm_ctx* c, double theta, int order) {
     // moments, coefficients
     const size_t mom = F32 ? 4 * (size_t)((ncoef(order) + 3) & ~3) : 24 + 8 * (size_t)E::NQ;
     const size_t per_node = 48 + mom + 8 * (size_t)tstride;
-    sched = ((double)per_node * nn <= 0.75 * (double)l2) ? 2 : 3;
+    sched = ((double)per_node * nn <= 2.0 * (double)l2) ? 2 : 3;
   }
   // a captured step runs on the counts of each replay's own build: node- and
   // leaf-indexed buffers are sized for the bounds (2n nodes, n leaves), and
