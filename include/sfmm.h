@@ -255,7 +255,11 @@ int sfmm_batch_sums(const sfmm_ctx* ctx, int nsys, double* out);
 /* Whole solve from HOST buffers: copies the inputs to the device, builds,
  * runs the gravity and copies the results back, all on the context's stream.
  * Same arguments and errors as sfmm_build + sfmm_gravity, but every pointer
- * is a host pointer (pinned memory gives the fastest copies). */
+ * is a host pointer (pinned memory gives the fastest copies).  With the
+ * Morton tree and the shared walk (the defaults) and n >= 2, build and
+ * gravity run as sfmm_solve_graph's captured step on the context's staging
+ * buffers (bitwise the same results; repeated calls of one shape replay
+ * one graph). */
 int sfmm_solve_host(sfmm_ctx* ctx, int64_t n, const double* pos, const double* mass,
                     const double* h, int leaf_size, double theta, int order, double* acc,
                     double* pot);

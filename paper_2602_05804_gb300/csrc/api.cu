@@ -680,10 +680,21 @@ int sfmm_solve_host(sfmm_ctx* c, int64_t n, const double* pos, const double* mas
   SFMM_CUDA_TRY(cudaMemcpyAsync(c->in_pos.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
   SFMM_CUDA_TRY(cudaMemcpyAsync(c->in_mass.p, mass, sizeof(double) * n, cudaMemcpyHostToDevice, st));
   SFMM_CUDA_TRY(cudaMemcpyAsync(c->in_h.p, h, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  if ((rc = sfmm_build(c, n, c->in_pos.as<double>(), c->in_mass.as<double>(), c->in_h.as<double>(), leaf_size)))
-    return rc;
-  if ((rc = sfmm_gravity(c, theta, order, c->out_acc.as<double>(), pot ? c->out_pot.as<double>() : nullptr)))
-    return rc;
+  if (c->tree_kind == 0 && c->walk_mode == 1 && n >= 2) {
+    // build + gravity as the captured step (one host wait; bitwise the
+    // results of the separate calls): the staging buffers keep their
+    // addresses, so repeated calls of one shape replay one graph
+    const int64_t off[2] = {0, n};
+    const int lsz[1] = {leaf_size};
+    if ((rc = sfmm_solve_graph(c, 1, off, c->in_pos.as<double>(), c->in_mass.as<double>(), c->in_h.as<double>(), lsz,
+                               theta, order, c->out_acc.as<double>(), pot ? c->out_pot.as<double>() : nullptr)))
+      return rc;
+  } else {
+    if ((rc = sfmm_build(c, n, c->in_pos.as<double>(), c->in_mass.as<double>(), c->in_h.as<double>(), leaf_size)))
+      return rc;
+    if ((rc = sfmm_gravity(c, theta, order, c->out_acc.as<double>(), pot ? c->out_pot.as<double>() : nullptr)))
+      return rc;
+  }
   SFMM_CUDA_TRY(cudaMemcpyAsync(acc, c->out_acc.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
   if (pot) SFMM_CUDA_TRY(cudaMemcpyAsync(pot, c->out_pot.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   SFMM_CUDA_TRY(cudaStreamSynchronize(st));
