@@ -188,22 +188,61 @@ __device__ __forceinline__ void bbox_block(long long (&mn)[3], long long (&mx)[3
   __syncthreads();
 }
 
+// Block partials as keys; the last block to finish (a counter the caller
+// zeroes) combines them into bbox: [0..2] min, [3..5] max, [6] cube extent
+// E, [7] key scale 2^21 / E (0 if E == 0).
 __global__ void k_bbox_partial(const double* __restrict__ pos, const double* __restrict__ mass,
-                               const double* __restrict__ h, int n, double* __restrict__ part,
-                               int* __restrict__ status) {
+                               const double* __restrict__ h, int n, long long* __restrict__ part,
+                               unsigned* __restrict__ done, double* __restrict__ bbox, int* __restrict__ status) {
   long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
   int bad = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     bbox_take(pos, mass, h, i, mn, mx, bad);
   __shared__ long long s[6][BB_NT / 32];
+  __shared__ bool s_last;
   bbox_block(mn, mx, s);
   if (threadIdx.x < 6) {
     const int c = threadIdx.x;
     long long v = s[c][0];
     for (int w = 1; w < BB_NT / 32; ++w) v = (c < 3) ? min(v, s[c][w]) : max(v, s[c][w]);
-    part[6 * blockIdx.x + c] = dkey_inv(v);
+    part[6 * blockIdx.x + c] = v;
   }
   if (bad) atomicOr(status, bad);
+  // publish the partial, then count: the last block sees every partial
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    long long a[6] = {LLONG_MAX, LLONG_MAX, LLONG_MAX, LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    for (int b = lane; b < (int)gridDim.x; b += 32)
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const long long v = __ldcg(&part[6 * b + c]);
+        a[c] = (c < 3) ? min(a[c], v) : max(a[c], v);
+      }
+  #pragma unroll
+    for (int c = 0; c < 6; ++c)
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long y = __shfl_xor_sync(SFMM_FULL, a[c], o);
+        a[c] = (c < 3) ? min(a[c], y) : max(a[c], y);
+      }
+    if (lane == 0) {
+      double E = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const double lo = dkey_inv(a[c]), hi = dkey_inv(a[3 + c]);
+        bbox[c] = lo;
+        bbox[3 + c] = hi;
+        const double e = dsub(hi, lo);
+        if (e > E) E = e;
+      }
+      bbox[6] = E;
+      bbox[7] = (E > 0.0) ? __ddiv_rn(2097152.0, E) : 0.0;
+    }
+  }
 }
 
 // Per-system bounding boxes for a batch: one block per system; bbox[8 s ..].
@@ -251,31 +290,6 @@ __global__ void k_fill_psys(int n, int nsys, const int* __restrict__ off, int* _
   psys[i] = lo;
 }
 
-// bbox[0..2] min, [3..5] max, [6] cube extent E, [7] key scale 2^21 / E (0 if E == 0)
-__global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ bbox) {
-  const int lane = threadIdx.x;  // one warp
-  double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-  for (int b = lane; b < nb; b += 32)
-    for (int c = 0; c < 3; ++c) {
-      mn[c] = fmin(mn[c], part[6 * b + c]);
-      mx[c] = fmax(mx[c], part[6 * b + 3 + c]);
-    }
-  for (int c = 0; c < 3; ++c)
-    for (int o = 16; o > 0; o >>= 1) {
-      mn[c] = fmin(mn[c], __shfl_xor_sync(SFMM_FULL, mn[c], o));
-      mx[c] = fmax(mx[c], __shfl_xor_sync(SFMM_FULL, mx[c], o));
-    }
-  if (lane != 0) return;
-  double E = 0.0;
-  for (int c = 0; c < 3; ++c) {
-    bbox[c] = mn[c];
-    bbox[3 + c] = mx[c];
-    double e = dsub(mx[c], mn[c]);
-    if (e > E) E = e;
-  }
-  bbox[6] = E;
-  bbox[7] = (E > 0.0) ? __ddiv_rn(2097152.0, E) : 0.0;
-}
 
 // ---------------------------------------------------------------------------
 // Morton keys: 21 bits per axis, x highest (bit 3b+2 = x_b, 3b+1 = y_b, 3b = z_b)
@@ -554,10 +568,20 @@ __global__ void __launch_bounds__(RS_NT) k_rs_onesweep(const uint64_t* __restric
 // ---------------------------------------------------------------------------
 // Gather the sorted particles (float64 SoA)
 // ---------------------------------------------------------------------------
+// FP32 softening record of a particle: {1/h, (2h)^2, 2h rounded up, 0} (1/h
+// by the Newton reciprocal, within about one unit in the last place).
+__device__ __forceinline__ float4 softening_record(double h) {
+  return make_float4(__double2float_rn(recip_pos(h)), __double2float_rn(4.0 * h * h), __double2float_ru(2.0 * h),
+                     0.0f);
+}
+
+// Sorted particles (and their softening records, formed while the gather
+// waits on its loads).
 __global__ void k_gather(const double* __restrict__ pos, const double* __restrict__ mass,
                          const double* __restrict__ h, const uint32_t* __restrict__ idx, int n,
                          double* __restrict__ px, double* __restrict__ py, double* __restrict__ pz,
-                         double* __restrict__ pm, double* __restrict__ ph, int* __restrict__ perm) {
+                         double* __restrict__ pm, double* __restrict__ ph, int* __restrict__ perm,
+                         float4* __restrict__ phh) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t j = idx[i];
@@ -565,8 +589,10 @@ __global__ void k_gather(const double* __restrict__ pos, const double* __restric
   py[i] = pos[3 * j + 1];
   pz[i] = pos[3 * j + 2];
   pm[i] = mass[j];
-  ph[i] = h[j];
+  const double hj = h[j];
+  ph[i] = hj;
   perm[i] = (int)j;
+  phh[i] = softening_record(hj);
 }
 
 // ---------------------------------------------------------------------------
@@ -1245,9 +1271,7 @@ __global__ void k_finalize_nodes(const uint32_t* __restrict__ counts, const unsi
 __global__ void k_particles_hh(int n, const double* __restrict__ ph, float4* __restrict__ phh) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double h = ph[i];
-  phh[i] = make_float4(__double2float_rn(recip_pos(h)), __double2float_rn(4.0 * h * h), __double2float_ru(2.0 * h),
-                       0.0f);
+  phh[i] = softening_record(ph[i]);
 }
 
 // Node depths, and counts[2]: the walkable internal nodes whose children are
@@ -1482,7 +1506,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
   ENS(n_exti, sizeof(int) * 6 * nn_max);
   ENS(size_cand, sizeof(unsigned long long) * 2 * nn_max);
   const int nbb = 2 * num_sms(c->device);
-  ENS(bbox_part, sizeof(double) * 6 * nbb);
+  ENS(bbox_part, sizeof(long long) * 6 * nbb + 16);
 #undef ENS
   const int nsys = c->nsys;
   double* bbox = c->misc.as<double>();             // 8 doubles per system
@@ -1502,9 +1526,9 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
 
   // S1: bounding box (per system), validation, Morton keys
   if (nsys == 1) {
-    k_bbox_partial<<<nbb, BB_NT, 0, st>>>(pos, mass, h, n, c->bbox_part.as<double>(), c->d_status);
-    ++c->nlaunch;
-    k_bbox_final<<<1, 32, 0, st>>>(c->bbox_part.as<double>(), nbb, bbox);
+    unsigned* done = reinterpret_cast<unsigned*>(c->bbox_part.as<long long>() + 6 * (size_t)nbb);
+    SFMM_CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(unsigned), st));
+    k_bbox_partial<<<nbb, BB_NT, 0, st>>>(pos, mass, h, n, c->bbox_part.as<long long>(), done, bbox, c->d_status);
     ++c->nlaunch;
   } else {
     k_bbox_seg<<<nsys, BB_NT, 0, st>>>(pos, mass, h, c->sys_off.as<int>(), bbox, c->d_status);
@@ -1575,7 +1599,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     ka_final = ka;
     k_gather<<<nblk(n, 256), 256, 0, st>>>(pos, mass, h, va, n, c->px.as<double>(), c->py.as<double>(),
                                            c->pz.as<double>(), c->pm.as<double>(), c->ph.as<double>(),
-                                           c->perm.as<int>());
+                                           c->perm.as<int>(), c->phh.as<float4>());
     ++c->nlaunch;
     SFMM_CUDA_TRY(cudaGetLastError());
 
@@ -1657,7 +1681,10 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
                                           c->pnode.as<int>(), c->ncx.as<double>(), c->ncy.as<double>(),
                                           c->ncz.as<double>(), c->prel.as<float4>(), c->geo_hi.as<float4>(),
                                           c->geo_lo.as<float4>());
-  k_particles_hh<<<nblk(n, 256), 256, 0, st>>>(n, c->ph.as<double>(), c->phh.as<float4>());
+  if (c->tree_kind == 1) {  // (the Morton build's gather wrote them)
+    k_particles_hh<<<nblk(n, 256), 256, 0, st>>>(n, c->ph.as<double>(), c->phh.as<float4>());
+    ++c->nlaunch;
+  }
   k_size_leaf<<<leaf_grid(c), 128, 0, st>>>(c->d_counts, c->leaf_node.as<int>(), c->nfirst.as<int>(),
                                             c->ncount.as<int>(), c->wparent.as<int>(), c->px.as<double>(),
                                             c->py.as<double>(), c->pz.as<double>(), c->ncx.as<double>(),
@@ -1670,7 +1697,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
                                        c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
                                        c->geo_hi.as<float4>(), c->geo_lo.as<float4>(), c->prel.as<float4>(),
                                        c->l2bits.as<unsigned long long>());
-  c->nlaunch += 4;
+  c->nlaunch += 3;  // node_lb, size_leaf, size
   k_finalize_nodes<<<node_grid(c), 256, 0, st>>>(c->d_counts, c->l2bits.as<unsigned long long>(),
                                                  c->nhmax.as<double>(), c->nsize.as<double>(), c->geo_hi.as<float4>(),
                                                  c->geo_lo.as<float4>());
