@@ -1550,7 +1550,7 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
 
     // S2: radix sort, 8 passes of 8 bits (the top pass holds 7 key bits)
     const int ntiles = (n + RS_TILE - 1) / RS_TILE;
-    if ((rc = c->sort_counts.ensure(sizeof(uint32_t) * 256 * (size_t)ntiles)) != SFMM_OK) return rc;
+    const int otiles = (n + OS_TILE - 1) / OS_TILE;
     uint64_t *ka = c->keys_a.as<uint64_t>(), *kb = c->keys_b.as<uint64_t>();
     uint32_t *va = c->idx_a.as<uint32_t>(), *vb = c->idx_b.as<uint32_t>();
     // Morton passes, then (batches) the system id as the most significant digits:
@@ -1562,6 +1562,11 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
     // digit histograms of all passes at once, then one launch per pass (the
     // published counts have 30 bits; larger sets take the three-step passes)
     const bool onesweep = n < (1 << 30);
+    // tile counts: one region per onesweep pass, all zeroed by one memset
+    const size_t tstat = sizeof(uint32_t) * 256 * (size_t)otiles;
+    if ((rc = c->sort_counts.ensure(onesweep ? tstat * npass : sizeof(uint32_t) * 256 * (size_t)ntiles)) != SFMM_OK)
+      return rc;
+    if (onesweep) SFMM_CUDA_TRY(cudaMemsetAsync(c->sort_counts.p, 0, tstat * npass, st));
     const size_t aux = sizeof(uint32_t) * 256 * (size_t)npass + sizeof(int) * (size_t)npass;
     if ((rc = c->sort_aux.ensure(aux))) return rc;
     uint32_t* gh = c->sort_aux.as<uint32_t>();
@@ -1577,10 +1582,9 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
       const int shift = by_sys ? 8 * (pass - 8) : 8 * pass;
       const int* dsys = by_sys ? psys : nullptr;
       if (onesweep) {
-        const int otiles = (n + OS_TILE - 1) / OS_TILE;
-        SFMM_CUDA_TRY(cudaMemsetAsync(c->sort_counts.p, 0, sizeof(uint32_t) * 256 * (size_t)otiles, st));
         k_rs_onesweep<<<otiles, RS_NT, 0, st>>>(ka, va, kb, vb, dsys, n, shift, gh + 256 * (size_t)pass,
-                                                c->sort_counts.as<uint32_t>(), tctr + pass, c->d_status);
+                                                c->sort_counts.as<uint32_t>() + 256 * (size_t)otiles * pass,
+                                                tctr + pass, c->d_status);
         ++c->nlaunch;
       } else {
         k_rs_hist<<<ntiles, RS_NT, 0, st>>>(ka, va, dsys, n, shift, c->sort_counts.as<uint32_t>(), ntiles);
