@@ -1104,9 +1104,9 @@ __global__ void k_node_lb(const uint32_t* __restrict__ counts, const int* __rest
   }
 }
 
-// Thread per leaf: the leaf's exact size, and which ancestors it is a
-// candidate for (bit k: the ancestor k levels up; beyond 127 levels every
-// ancestor counts as a candidate).
+// Thread per leaf: the leaf's exact size, and the ancestors it is a
+// candidate for (a short list; a leaf with more tries every ancestor).
+#define SIZE_LIST 8
 __global__ void k_size_leaf(const uint32_t* __restrict__ counts, const int* __restrict__ leaf_node, const int* __restrict__ nfirst,
                             const int* __restrict__ ncount, const int* __restrict__ wparent,
                             const double* __restrict__ px, const double* __restrict__ py,
@@ -1114,7 +1114,7 @@ __global__ void k_size_leaf(const uint32_t* __restrict__ counts, const int* __re
                             const double* __restrict__ ncy, const double* __restrict__ ncz,
                             const float4* __restrict__ geo_hi, const float4* __restrict__ geo_lo,
                             const float4* __restrict__ prel, unsigned long long* __restrict__ l2bits,
-                            unsigned long long* __restrict__ cand) {
+                            int* __restrict__ cand) {
   const int nleaves = (int)counts[1];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
     const int L = leaf_node[q];
@@ -1147,22 +1147,22 @@ __global__ void k_size_leaf(const uint32_t* __restrict__ counts, const int* __re
     // an ancestor v is skipped when every particle of the leaf is certainly
     // closer to s_v than LB(v) (a real particle's distance): |s_L - s_v| + l_L,
     // with its error bound and one more relative margin for the FP32 sums,
-    // below LB(v) rounded down
-    unsigned long long m0 = 0ull, m1 = 0ull;
-    int k = 1;
-    for (int v = (wparent[L] >= 0) ? wparent[L] : -1; v >= 0; v = wparent[v], ++k) {
+    // below LB(v) rounded down.  The others are listed (count, then ids);
+    // more than SIZE_LIST - 1 of them: count -1, and every ancestor is tried
+    int* const lst = cand + SIZE_LIST * (size_t)q;
+    int nc = 0;
+    for (int v = (wparent[L] >= 0) ? wparent[L] : -1; v >= 0; v = wparent[v]) {
       const float4 hv = geo_hi[v], ov = geo_lo[v];
       const float dx = df_diff(hL.x, oL.x, hv.x, ov.x), dy = df_diff(hL.y, oL.y, hv.y, ov.y),
                   dz = df_diff(hL.z, oL.z, hv.z, ov.z);
       const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
       const float reach = (d + df_dist_err(dx, dy, dz, hL, hv) + lL) * (1.0f + 1e-6f);
-      if (!(reach < hv.w)) {
-        if (k < 64) m0 |= 1ull << k;
-        else if (k < 128) m1 |= 1ull << (k - 64);
+      if (!(reach < hv.w) && nc >= 0) {
+        if (nc < SIZE_LIST - 1) lst[1 + nc++] = v;
+        else nc = -1;
       }
     }
-    cand[2 * (size_t)q] = m0;
-    cand[2 * (size_t)q + 1] = m1;
+    lst[0] = nc;
   }
 }
 
@@ -1194,7 +1194,7 @@ __device__ __forceinline__ void size_flush(const int2* q, int cnt, const double*
 
 __global__ void __launch_bounds__(SIZE_NT) k_size(int n, const double* __restrict__ px, const double* __restrict__ py,
                        const double* __restrict__ pz, const int* __restrict__ pnode,
-                       const uint32_t* __restrict__ leaf_index, const unsigned long long* __restrict__ cand,
+                       const uint32_t* __restrict__ leaf_index, const int* __restrict__ cand,
                        const int* __restrict__ wparent, const double* __restrict__ ncx,
                        const double* __restrict__ ncy, const double* __restrict__ ncz,
                        const float4* __restrict__ geo_hi, const float4* __restrict__ geo_lo,
@@ -1204,28 +1204,33 @@ __global__ void __launch_bounds__(SIZE_NT) k_size(int n, const double* __restric
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int2* const q = s_q[warp];
   int nq = 0;
-  int v = -1;
-  unsigned long long m0 = 0ull, m1 = 0ull;
+  const int* lst = nullptr;
+  int nc = 0, L = -1;
   float4 hL = make_float4(0.f, 0.f, 0.f, 0.f), oL = hL, r = hL;
   if (i < n) {
-    const int L = pnode[i];
-    v = wparent[L];  // the leaf itself was done by k_size_leaf
-    const uint32_t ql = leaf_index[L];
-    m0 = cand[2 * (size_t)ql];
-    m1 = cand[2 * (size_t)ql + 1];
+    L = pnode[i];  // the leaf itself was done by k_size_leaf
+    lst = cand + SIZE_LIST * (size_t)leaf_index[L];
+    nc = lst[0];
     hL = geo_hi[L];
     oL = geo_lo[L];
     r = prel[i];  // x - s_L in FP32
   }
   const float er = 2e-6f * (fabsf(r.x) + fabsf(r.y) + fabsf(r.z));
-  int k = 1;
-  while (true) {
-    const unsigned act = __ballot_sync(SFMM_FULL, v >= 0);
+  // candidate ancestor number k of this particle's leaf: from the list, or
+  // (count -1) every ancestor in turn
+  int v = (i < n && nc < 0) ? wparent[L] : -1;
+  for (int k = 0;; ++k) {
+    int u = -1;
+    if (i < n) {
+      if (nc >= 0) u = (k < nc) ? lst[1 + k] : -1;
+      else u = v;
+    }
+    const unsigned act = __ballot_sync(SFMM_FULL, u >= 0);
     if (act == 0u) break;
-    bool want = v >= 0 && (k >= 128 || ((k < 64 ? (m0 >> k) : (m1 >> (k - 64))) & 1ull));
-    if (want) {
-      // certainly closer than LB(v)? then not the maximum: skip the exact test
-      const float4 hv = geo_hi[v], ov = geo_lo[v];
+    bool want = false;
+    if (u >= 0) {
+      // certainly closer than LB(u)? then not the maximum: skip the exact test
+      const float4 hv = geo_hi[u], ov = geo_lo[u];
       const float ox = df_diff(hL.x, oL.x, hv.x, ov.x), oy = df_diff(hL.y, oL.y, hv.y, ov.y),
                   oz = df_diff(hL.z, oL.z, hv.z, ov.z);
       const float dx = r.x + ox, dy = r.y + oy, dz = r.z + oz;
@@ -1233,7 +1238,7 @@ __global__ void __launch_bounds__(SIZE_NT) k_size(int n, const double* __restric
       want = !((d + er + df_dist_err(ox, oy, oz, hL, hv)) * (1.0f + 1e-6f) < hv.w);
     }
     const unsigned bw = __ballot_sync(SFMM_FULL, want);
-    if (want) q[nq + __popc(bw & lanemask_lt())] = make_int2(i, v);
+    if (want) q[nq + __popc(bw & lanemask_lt())] = make_int2(i, u);
     nq += __popc(bw);
     __syncwarp();
     if (nq >= 32) {
@@ -1246,8 +1251,7 @@ __global__ void __launch_bounds__(SIZE_NT) k_size(int n, const double* __restric
       __syncwarp();
       nq = rest;
     }
-    if (v >= 0) v = wparent[v];  // stops after the system root (-1)
-    ++k;
+    if (nc < 0 && v >= 0) v = wparent[v];  // stops after the system root (-1)
   }
   if (nq > 0) size_flush(q, nq, px, py, pz, ncx, ncy, ncz, l2bits);
 }
@@ -1694,10 +1698,10 @@ int build_tree(sfmm_ctx* c, const double* pos, const double* mass, const double*
                                             c->py.as<double>(), c->pz.as<double>(), c->ncx.as<double>(),
                                             c->ncy.as<double>(), c->ncz.as<double>(), c->geo_hi.as<float4>(),
                                             c->geo_lo.as<float4>(), c->prel.as<float4>(),
-                                            c->l2bits.as<unsigned long long>(), c->size_cand.as<unsigned long long>());
+                                            c->l2bits.as<unsigned long long>(), c->size_cand.as<int>());
   k_size<<<nblk(n, SIZE_NT), SIZE_NT, 0, st>>>(n, c->px.as<double>(), c->py.as<double>(), c->pz.as<double>(),
                                        c->pnode.as<int>(), c->isleaf.as<uint32_t>(),
-                                       c->size_cand.as<unsigned long long>(), c->wparent.as<int>(),
+                                       c->size_cand.as<int>(), c->wparent.as<int>(),
                                        c->ncx.as<double>(), c->ncy.as<double>(), c->ncz.as<double>(),
                                        c->geo_hi.as<float4>(), c->geo_lo.as<float4>(), c->prel.as<float4>(),
                                        c->l2bits.as<unsigned long long>());

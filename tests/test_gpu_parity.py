@@ -195,6 +195,26 @@ def test_solve_host_equals_device_path():
         assert s.stats()["graph_replays"] == call
 
 
+@pytest.mark.parametrize("opts", [{"tree": 1}, {"walk": 0}])
+def test_solve_host_without_capture_equals_device_path(opts):
+    """Options the captured step does not run (kd tree, per-leaf replay walk):
+    the host-buffer solve takes the separate calls, with the same results."""
+    import torch
+
+    pos, m, h = workloads.uniform_sphere(3000, 6)
+    s = solver("fp32", **opts)
+    s.build(pos, m, h, 16)
+    acc_d, pot_d = s.gravity(0.5, 2)
+    acc_h = torch.empty((3000, 3), dtype=torch.float64).pin_memory()
+    pot_h = torch.empty(3000, dtype=torch.float64).pin_memory()
+    s.solve_host(torch.from_numpy(pos).pin_memory(), torch.from_numpy(m), torch.from_numpy(h), 16, 0.5, 2, acc_h,
+                 pot_h)
+    np.testing.assert_array_equal(acc_h.numpy(), acc_d.cpu().numpy())
+    np.testing.assert_array_equal(pot_h.numpy(), pot_d.cpu().numpy())
+    assert s.stats()["graph_replays"] == 0
+    s.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_deterministic_rerun(prec):
     pos, m, h = workloads.plummer(6000, 8)
