@@ -662,6 +662,56 @@ int sfmm_solve_graph(sfmm_ctx* c, int nsys, const int64_t* offsets, const double
   return rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Copies between host and device memory by a kernel when the host side is
+// device-accessible (pinned or registered): on GB300 the GPU reads and
+// writes host memory over the chip-to-chip link faster than a copy engine
+// moves it.  Otherwise (pageable memory) a stream copy.
+__global__ void k_copy_f64(const double2* __restrict__ src, double2* __restrict__ dst, int64_t n2,
+                           const double* __restrict__ src_tail, double* __restrict__ dst_tail, int tail) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+  if (tail && blockIdx.x == 0 && threadIdx.x == 0) *dst_tail = *src_tail;
+}
+
+const double* device_view(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return static_cast<const double*>(p);
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) return static_cast<const double*>(at.devicePointer);
+  return nullptr;
+}
+
+int copy_f64(sfmm_ctx* c, double* dst, const double* src, int64_t count, cudaMemcpyKind kind) {
+  const double* hs = (kind == cudaMemcpyHostToDevice) ? device_view(src) : nullptr;
+  double* hd = (kind == cudaMemcpyDeviceToHost) ? const_cast<double*>(device_view(dst)) : nullptr;
+  const double* s = (kind == cudaMemcpyHostToDevice) ? hs : src;
+  double* d = (kind == cudaMemcpyDeviceToHost) ? hd : dst;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
+  if (s && d && aligned) {
+    const int64_t n2 = count / 2;
+    const int blocks = (int)std::min<int64_t>((n2 + 255) / 256, 8 * (int64_t)num_sms(c->device));
+    k_copy_f64<<<std::max(blocks, 1), 256, 0, c->stream>>>(reinterpret_cast<const double2*>(s),
+                                                           reinterpret_cast<double2*>(d), n2, s + count - 1,
+                                                           d + count - 1, (int)(count & 1));
+    ++c->nlaunch;
+    SFMM_CUDA_TRY(cudaGetLastError());
+    return SFMM_OK;
+  }
+  SFMM_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double) * count, kind, c->stream));
+  return SFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int sfmm_solve_host(sfmm_ctx* c, int64_t n, const double* pos, const double* mass, const double* h, int leaf_size,
                     double theta, int order, double* acc, double* pot) {
   if (check_ctx(c)) return SFMM_EINVAL;
@@ -677,9 +727,10 @@ int sfmm_solve_host(sfmm_ctx* c, int64_t n, const double* pos, const double* mas
       (rc = c->out_pot.ensure(sizeof(double) * n)))
     return set_error(c, rc, "staging allocation failed");
   cudaStream_t st = c->stream;
-  SFMM_CUDA_TRY(cudaMemcpyAsync(c->in_pos.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-  SFMM_CUDA_TRY(cudaMemcpyAsync(c->in_mass.p, mass, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  SFMM_CUDA_TRY(cudaMemcpyAsync(c->in_h.p, h, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if ((rc = copy_f64(c, c->in_pos.as<double>(), pos, 3 * n, cudaMemcpyHostToDevice)) ||
+      (rc = copy_f64(c, c->in_mass.as<double>(), mass, n, cudaMemcpyHostToDevice)) ||
+      (rc = copy_f64(c, c->in_h.as<double>(), h, n, cudaMemcpyHostToDevice)))
+    return rc;
   if (c->tree_kind == 0 && c->walk_mode == 1 && n >= 2) {
     // build + gravity as the captured step (one host wait; bitwise the
     // results of the separate calls): the staging buffers keep their
@@ -695,8 +746,8 @@ int sfmm_solve_host(sfmm_ctx* c, int64_t n, const double* pos, const double* mas
     if ((rc = sfmm_gravity(c, theta, order, c->out_acc.as<double>(), pot ? c->out_pot.as<double>() : nullptr)))
       return rc;
   }
-  SFMM_CUDA_TRY(cudaMemcpyAsync(acc, c->out_acc.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
-  if (pot) SFMM_CUDA_TRY(cudaMemcpyAsync(pot, c->out_pot.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  if ((rc = copy_f64(c, acc, c->out_acc.as<double>(), 3 * n, cudaMemcpyDeviceToHost))) return rc;
+  if (pot && (rc = copy_f64(c, pot, c->out_pot.as<double>(), n, cudaMemcpyDeviceToHost))) return rc;
   SFMM_CUDA_TRY(cudaStreamSynchronize(st));
   return SFMM_OK;
 }
