@@ -255,7 +255,8 @@ int sfmm_batch_sums(const sfmm_ctx* ctx, int nsys, double* out);
 /* Whole solve from HOST buffers: copies the inputs to the device, builds,
  * runs the gravity and copies the results back, all on the context's stream.
  * Same arguments and errors as sfmm_build + sfmm_gravity, but every pointer
- * is a host pointer (pinned memory gives the fastest copies).  With the
+ * is a host pointer (pinned memory gives the fastest copies: the device
+ * then reads and writes it directly, by a copy kernel).  With the
  * Morton tree and the shared walk (the defaults) and n >= 2, build and
  * gravity run as sfmm_solve_graph's captured step on the context's staging
  * buffers (bitwise the same results; repeated calls of one shape replay
