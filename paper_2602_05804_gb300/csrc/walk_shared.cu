@@ -40,11 +40,12 @@ struct LevelArgs {
   const int* ndepth;
   double* Cown;
   double* Erecv;
-  // queue walk (mode 3): ready nodes in order of readiness (-1: not yet
-  // filled), slots handed out by q_head, filled through q_tail; q_total
-  // walkable nodes in all
-  int* queue;
-  long long* queue64;  // node queue: (walk parent + 1) << 32 | node, -1 while unfilled
+  // queue walks (schedules 2 and 3): items in order of readiness (-1: not
+  // yet filled), slots handed out by q_head, filled through q_tail; q_total
+  // items in all (an upper bound on the host: the kernels count them from
+  // the build's counts)
+  int* queue;          // pair queue: one int per item
+  long long* queue64;  // node queue: (walk parent + 1) << 32 | node
   int* q_head;
   int* q_tail;
   int q_total;
