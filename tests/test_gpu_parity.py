@@ -195,6 +195,28 @@ def test_solve_host_equals_device_path():
         assert s.stats()["graph_replays"] == call
 
 
+@pytest.mark.parametrize("n", [4001, 2])
+def test_solve_host_odd_sizes_and_pinned_buffers(n):
+    """All host buffers pinned (the device copies them by a kernel), odd
+    counts (the copies' last element) and the smallest captured step."""
+    import torch
+
+    pos, m, h = workloads.plummer(n, 7) if n > 2 else (np.array([[0.0, 0, 0], [1.0, 0, 0]]), np.ones(2), np.ones(2))
+    s = solver("fp64")
+    s.build(pos, m, h, 16)
+    acc_d, pot_d = s.gravity(0.5, 2)
+    pin = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (pos, m, h)]
+    acc_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    pot_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        acc_h.fill_(float("nan"))
+        pot_h.fill_(float("nan"))
+        s.solve_host(pin[0], pin[1], pin[2], 16, 0.5, 2, acc_h, pot_h)
+        np.testing.assert_array_equal(acc_h.numpy(), acc_d.cpu().numpy())
+        np.testing.assert_array_equal(pot_h.numpy(), pot_d.cpu().numpy())
+    s.close()
+
+
 @pytest.mark.parametrize("opts", [{"tree": 1}, {"walk": 0}])
 def test_solve_host_without_capture_equals_device_path(opts):
     """Options the captured step does not run (kd tree, per-leaf replay walk):
