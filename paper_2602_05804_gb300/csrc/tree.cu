@@ -568,11 +568,15 @@ __global__ void __launch_bounds__(RS_NT) k_rs_onesweep(const uint64_t* __restric
 // ---------------------------------------------------------------------------
 // Gather the sorted particles (float64 SoA)
 // ---------------------------------------------------------------------------
-// FP32 softening record of a particle: {1/h, (2h)^2, 2h rounded up, 0} (1/h
-// by the Newton reciprocal, within about one unit in the last place).
+// FP32 softening record of a particle: {1/h, (2h)^2, 2h rounded up, 0}.
+// The first two in FP32 from h rounded to FP32 (within an ulp or two of the
+// FP32 roundings of the exact values: the FP32 form's M4 kernels and its
+// inside-the-kernel test take them as they are); 2h rounded up from the
+// FP64 value, since the near-field candidate test needs a bound.
 __device__ __forceinline__ float4 softening_record(double h) {
-  return make_float4(__double2float_rn(recip_pos(h)), __double2float_rn(4.0 * h * h), __double2float_ru(2.0 * h),
-                     0.0f);
+  const float hf = __double2float_rn(h);
+  const float h2 = 2.0f * hf;
+  return make_float4(__frcp_rn(hf), h2 * h2, __double2float_ru(2.0 * h), 0.0f);
 }
 
 // Sorted particles (and their softening records, formed while the gather
