@@ -17,7 +17,7 @@ namespace sfmm {
 // FP64 instructions per particle than sums formed in the near-field kernel,
 // whose warps hold a leaf of ~11 particles.
 #define RED_NT 256
-#define RED_BLOCKS 608
+#define RED_BLOCKS 304
 
 __device__ __forceinline__ void block_merge(csum (&s)[5], double (&sh)[10][RED_NT]) {
 #pragma unroll
