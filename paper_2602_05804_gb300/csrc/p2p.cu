@@ -91,7 +91,7 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
 template <typename R> struct Vec4;
 template <> struct Vec4<float> { using T = float4; using T2 = float2; };
-template <> struct Vec4<double> { using T = double4; using T2 = double2; };
+template <> struct Vec4<double> { using T = double4_16a; using T2 = double2; };
 
 // Unsoftened pair: a -= m r^-3 d, phi -= m / r.
 template <typename R>
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(P2P_NT, F32 ? 3 : 1) k_p2p(const P2PArgs a) {
             h2j = hr.z;
           } else {
             const double h = a.ph[i];
-            v = make_double4(a.px[i], a.py[i], a.pz[i], a.pm[i]);
+            v = make_double4_16a(a.px[i], a.py[i], a.pz[i], a.pm[i]);
             hh = make_double2(1.0 / h, 4.0 * h * h);
             h2j = 2.0 * h;
           }
